@@ -1,0 +1,257 @@
+"""Seeded synthetic microstructures (crack-resistance fields gamma on a voxel grid).
+
+This module only builds inputs. It holds none of the solver's arithmetic and
+imports neither the CUDA binding nor the oracle, so both sides of every parity
+test draw their inputs from here.
+
+Conventions (Sec. 2.2 of the paper): the grid has N1 x N2 x N3 voxels of unit
+edge, the array is C-ordered with shape (N1, N2, N3) indexed [i, j, k] = (x, y, z),
+and gamma is sampled at the voxel centres ((i + 1/2), (j + 1/2), (k + 1/2)).
+A voxel belongs to a shape iff its centre lies strictly inside the shape, with
+periodic wrap-around of the cell.
+
+Random numbers come from ``numpy.random.default_rng(seed)`` (PCG64 seeded through
+SeedSequence), so a seed fixes every field bit for bit on any machine.
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+__all__ = [
+    "single_sphere",
+    "boolean_spheres",
+    "short_fibres",
+    "lognormal_field",
+    "laminate",
+    "random_two_phase",
+    "uniform_random",
+    "config_single_sphere_32",
+    "config_boolean_spheres_128",
+]
+
+
+def _centres(n):
+    return [np.arange(m, dtype=np.float64) + 0.5 for m in n]
+
+
+def _periodic_delta(x, c, length):
+    d = x - c
+    d -= length * np.round(d / length)
+    return d
+
+
+def _stamp_ball(mask, centre, radius):
+    """Set every voxel whose centre is strictly inside the periodic ball."""
+    n = mask.shape
+    r = float(radius)
+    lo = [int(math.floor(centre[a] - r - 1)) for a in range(3)]
+    hi = [int(math.ceil(centre[a] + r + 1)) for a in range(3)]
+    idx = [np.arange(lo[a], hi[a] + 1) for a in range(3)]
+    d2 = None
+    for a in range(3):
+        da = (idx[a] + 0.5) - centre[a]
+        shape = [1, 1, 1]
+        shape[a] = -1
+        term = (da * da).reshape(shape)
+        d2 = term if d2 is None else d2 + term
+    inside = d2 < r * r
+    ii, jj, kk = np.nonzero(inside)
+    mask[(idx[0][ii] % n[0]), (idx[1][jj] % n[1]), (idx[2][kk] % n[2])] = True
+
+
+def single_sphere(n, centre, radius, gamma_sphere, gamma_matrix, dtype=np.float64):
+    """One ball of the given radius (voxel units) in a homogeneous matrix."""
+    n = tuple(int(m) for m in n)
+    mask = np.zeros(n, dtype=bool)
+    _stamp_ball(mask, np.asarray(centre, dtype=np.float64), radius)
+    g = np.where(mask, gamma_sphere, gamma_matrix).astype(dtype)
+    return g
+
+
+def boolean_spheres(n, radius, volume_fraction, gamma_sphere, gamma_matrix, seed,
+                    radius_max=None, dtype=np.float64):
+    """Boolean model of overlapping balls.
+
+    Centres are i.i.d. uniform in the periodic cell; balls are added one at a time
+    until the voxel volume fraction first reaches ``volume_fraction``. With
+    ``radius_max`` set, each ball draws its radius uniformly from
+    [radius, radius_max] (polydisperse).
+    Returns (gamma, number_of_balls).
+    """
+    n = tuple(int(m) for m in n)
+    rng = np.random.default_rng(seed)
+    mask = np.zeros(n, dtype=bool)
+    total = float(np.prod(n))
+    count = 0
+    filled = 0
+    while filled / total < volume_fraction:
+        c = rng.random(3) * np.asarray(n, dtype=np.float64)
+        r = radius if radius_max is None else rng.uniform(radius, radius_max)
+        _stamp_ball(mask, c, r)
+        count += 1
+        filled = int(mask.sum())
+        if count > 10_000_000:  # pragma: no cover - guards a bad target
+            raise RuntimeError("volume fraction not reachable")
+    g = np.where(mask, gamma_sphere, gamma_matrix).astype(dtype)
+    return g, count
+
+
+def _segment_distance_sq(p0, d0, p1, d1):
+    """Squared distance between segments p0 + s d0 and p1 + t d1, s, t in [0, 1]."""
+    r = p0 - p1
+    a = d0 @ d0
+    e = d1 @ d1
+    f = d1 @ r
+    c = d0 @ r
+    b = d0 @ d1
+    denom = a * e - b * b
+    s = np.clip((b * f - c * e) / denom, 0.0, 1.0) if denom > 1e-14 else 0.0
+    t = (b * s + f) / e
+    if t < 0.0:
+        t = 0.0
+        s = np.clip(-c / a, 0.0, 1.0)
+    elif t > 1.0:
+        t = 1.0
+        s = np.clip((b - c) / a, 0.0, 1.0)
+    q = r + s * d0 - t * d1
+    return float(q @ q)
+
+
+def short_fibres(n, diameter, aspect_ratio, volume_fraction, gamma_fibre, gamma_matrix,
+                 seed, max_attempts=2_000_000, dtype=np.float32):
+    """Straight cylinders (spherocylinder distance rule) by random sequential addition.
+
+    Axis directions are isotropic on the sphere. A candidate is rejected if the
+    periodic segment-segment distance to any accepted fibre is below the
+    diameter. Fibres are added until the voxel volume fraction first reaches
+    ``volume_fraction``; a voxel belongs to a fibre iff its centre lies within
+    radius of the axis segment (projected parameter clipped to the segment).
+    Returns (gamma, number_of_fibres).
+    """
+    n = np.asarray([int(m) for m in n], dtype=np.int64)
+    rng = np.random.default_rng(seed)
+    radius = 0.5 * diameter
+    length = diameter * aspect_ratio
+    mask = np.zeros(tuple(n), dtype=bool)
+    total = float(np.prod(n))
+    cell = max(length + diameter, 1.0)
+    ncell = np.maximum((n / cell).astype(np.int64), 1)
+    grid = {}
+    accepted = []
+    filled = 0
+    attempts = 0
+    nf = n.astype(np.float64)
+    while filled / total < volume_fraction:
+        attempts += 1
+        if attempts > max_attempts:
+            raise RuntimeError("fibre volume fraction not reachable")
+        mid = rng.random(3) * nf
+        z = rng.uniform(-1.0, 1.0)
+        phi = rng.uniform(0.0, 2.0 * math.pi)
+        s = math.sqrt(max(0.0, 1.0 - z * z))
+        d = np.array([s * math.cos(phi), s * math.sin(phi), z]) * length
+        p0 = mid - 0.5 * d
+        key = tuple((mid / nf * ncell).astype(np.int64) % ncell)
+        ok = True
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dz in (-1, 0, 1):
+                    nb = ((key[0] + dx) % ncell[0], (key[1] + dy) % ncell[1], (key[2] + dz) % ncell[2])
+                    for fid in grid.get(nb, ()):
+                        q0, qd = accepted[fid]
+                        shift = _periodic_delta(p0 + 0.5 * d, q0 + 0.5 * qd, nf) - (p0 + 0.5 * d - q0 - 0.5 * qd)
+                        if _segment_distance_sq(p0 + shift, d, q0, qd) < diameter * diameter:
+                            ok = False
+                            break
+                    if not ok:
+                        break
+                if not ok:
+                    break
+            if not ok:
+                break
+        if not ok:
+            continue
+        grid.setdefault(key, []).append(len(accepted))
+        accepted.append((p0, d))
+        _stamp_cylinder(mask, p0, d, radius)
+        filled = int(mask.sum())
+    g = np.where(mask, gamma_fibre, gamma_matrix).astype(dtype)
+    return g, len(accepted)
+
+
+def _stamp_cylinder(mask, p0, d, radius):
+    n = mask.shape
+    length = float(np.linalg.norm(d))
+    step = max(radius, 1.0)
+    nseg = max(int(math.ceil(length / step)), 1)
+    dd = d @ d
+    for s in range(nseg):
+        a = p0 + d * (s / nseg)
+        b = p0 + d * ((s + 1) / nseg)
+        lo = np.floor(np.minimum(a, b) - radius - 1).astype(np.int64)
+        hi = np.ceil(np.maximum(a, b) + radius + 1).astype(np.int64)
+        idx = [np.arange(lo[ax], hi[ax] + 1) for ax in range(3)]
+        X = (idx[0] + 0.5)[:, None, None] - p0[0]
+        Y = (idx[1] + 0.5)[None, :, None] - p0[1]
+        Z = (idx[2] + 0.5)[None, None, :] - p0[2]
+        t = np.clip((X * d[0] + Y * d[1] + Z * d[2]) / dd, 0.0, 1.0)
+        r2 = (X - t * d[0]) ** 2 + (Y - t * d[1]) ** 2 + (Z - t * d[2]) ** 2
+        ii, jj, kk = np.nonzero(r2 < radius * radius)
+        mask[idx[0][ii] % n[0], idx[1][jj] % n[1], idx[2][kk] % n[2]] = True
+
+
+def lognormal_field(n, correlation_length, sigma, seed, dtype=np.float64):
+    """gamma = exp(sigma * g), g a periodic unit-variance Gaussian random field.
+
+    g has the Gaussian covariance exp(-r^2 / (2 l^2)); it is synthesised as
+    IFFT(sqrt(S) * FFT(white noise)) with S the sampled power spectrum of that
+    covariance on the periodic grid, then shifted and scaled to zero sample mean
+    and unit sample variance.
+    """
+    n = tuple(int(m) for m in n)
+    rng = np.random.default_rng(seed)
+    white = rng.standard_normal(n)
+    r2 = None
+    for a, m in enumerate(n):
+        x = np.arange(m, dtype=np.float64)
+        x = np.minimum(x, m - x)
+        shape = [1, 1, 1]
+        shape[a] = -1
+        term = (x * x).reshape(shape)
+        r2 = term if r2 is None else r2 + term
+    cov = np.exp(-r2 / (2.0 * correlation_length ** 2))
+    spec = np.maximum(np.fft.fftn(cov).real, 0.0)
+    g = np.fft.ifftn(np.sqrt(spec) * np.fft.fftn(white)).real
+    g = (g - g.mean()) / g.std()
+    return np.exp(sigma * g).astype(dtype)
+
+
+def laminate(n1, n2, layer_gammas, dtype=np.float64):
+    """gamma depends on k only: gamma[i, j, k] = layer_gammas[k]."""
+    layers = np.asarray(layer_gammas, dtype=np.float64)
+    return np.broadcast_to(layers[None, None, :], (n1, n2, layers.size)).astype(dtype)
+
+
+def random_two_phase(n, fraction, gamma_a, gamma_b, seed, dtype=np.float64):
+    """Independent voxel-wise two-phase field (gamma_a with probability fraction)."""
+    rng = np.random.default_rng(seed)
+    return np.where(rng.random(tuple(n)) < fraction, gamma_a, gamma_b).astype(dtype)
+
+
+def uniform_random(n, lo, hi, seed, dtype=np.float64):
+    """gamma i.i.d. uniform in [lo, hi) per voxel."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(lo, hi, size=tuple(n)).astype(dtype)
+
+
+def config_single_sphere_32():
+    """32^3 cell, gamma 1.0 matrix, one ball of radius 8 centred at (16, 16, 16) with gamma 0.1."""
+    return single_sphere((32, 32, 32), (16.0, 16.0, 16.0), 8.0, 0.1, 1.0)
+
+
+def config_boolean_spheres_128(seed=2103, dtype=np.float64):
+    """128^3 Boolean model: radius 6, volume fraction 0.20, gamma 0.3 in balls / 1.0 matrix."""
+    return boolean_spheres((128, 128, 128), 6.0, 0.20, 0.3, 1.0, seed, dtype=dtype)

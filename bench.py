@@ -1,0 +1,363 @@
+"""Benchmark: ADMM voxel-iterations per second of the CCMF FFT-ADMM solver.
+
+One step = one damped-ADMM iteration (Eq. 30 of the paper: FFT projection onto
+K, node-wise projection onto C_gamma, multiplier / residual / penalty update)
+over every solve of the workload. Default workload: 128^3 Boolean model of
+overlapping balls (radius 6 voxels, volume fraction 0.20, gamma 0.3 in balls /
+1.0 matrix) with the three crack normals e1, e2, e3 solved together (3 solves),
+FP32 fields with FP64 reductions.
+
+Output: one JSON line (rank 0). See the design doc for the definitions of every key.
+Multi-GPU runs (torchrun) are replicas: every rank solves the same workload on
+its own GPU; value = all ranks' voxel-iterations / slowest rank's time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ADMM voxel-iters/s, FP32-mixed vs FP64 at rel γ_eff err ≤1e-5; HBM % of peak"
+UNIT = "voxel-iters/s"
+FALLBACK_HBM_GBS = 6800.0
+
+WORKLOADS = {
+    "boolean128": dict(shape=(128, 128, 128), normals=[[1, 0, 0], [0, 1, 0], [0, 0, 1]],
+                       desc="128^3 Boolean spheres r=6 vf=0.20 gamma 0.3/1.0, normals e1,e2,e3 (3 solves)"),
+    "fibres512": dict(shape=(512, 512, 512), normals=[[0, 0, 1]],
+                      desc="512^3 short fibres d=6 AR=20 vf=0.12 gamma 3.0/1.0, normal e3 (1 solve)"),
+}
+
+
+def make_gamma(name, dtype):
+    from paper_2103_05968_gb300 import microstructure as M
+    if name == "boolean128":
+        g, _ = M.config_boolean_spheres_128(dtype=dtype)
+        return g
+    if name == "fibres512":
+        g, _ = M.short_fibres((512, 512, 512), 6.0, 20.0, 0.12, 3.0, 1.0, seed=2103, dtype=dtype)
+        return g
+    raise ValueError(name)
+
+
+def bytes_per_voxel(kernel, esize, n3):
+    """Algorithmic DRAM bytes per voxel of one launch of each loop kernel."""
+    half = (n3 // 2 + 1) / n3 * 2 * esize  # half-spectrum bytes per voxel
+    return {
+        "k_div_rfft_z": 12 * esize + half,          # read e, v; write spectrum
+        "k_fft_y_fwd": 2 * half,                    # read + write spectrum
+        "k_fft_x_solve": 2 * half,
+        "k_fft_y_inv": 2 * half,
+        "k_irfft_z": half + esize,                  # read spectrum; write phi
+        "k_update": 12 * esize + 2 * esize + 12 * esize,  # read e, v, gamma, phi; write e, v
+    }[kernel]
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for key in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if key in d:
+                    return float(d[key]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(name, max_seconds=20.0):
+    """The oracle as it stands on the host cores: a bounded sample of the workload
+    (one solve of the same grid, as many iterations as fit in about max_seconds)."""
+    from oracle import ccmf_oracle as O
+    wl = WORKLOADS[name]
+    gamma = make_gamma(name, np.float64) if name == "boolean128" else None
+    if gamma is None:  # pragma: no cover - the large workload samples a 128^3 sub-block
+        gamma = make_gamma(name, np.float32)[:128, :128, :128].astype(np.float64)
+    xi = np.asarray(wl["normals"][0], dtype=np.float64)
+    e = O.op_A(O.const_field(xi, gamma.shape))
+    v = np.zeros((6,) + gamma.shape)
+    rho = O.initial_rho(gamma, O.Params())
+    t0, c0 = time.perf_counter(), time.process_time()
+    iters = 0
+    while True:
+        _, e2, v2 = O.admm_step(e, v, rho, gamma, xi, 0.25)
+        rho = O.next_rho(rho, O.RHO_BB, e, e2, v, v2, O.Params())
+        e, v = e2, v2
+        iters += 1
+        if time.perf_counter() - t0 > max_seconds or iters >= 50:
+            break
+    wall = time.perf_counter() - t0
+    cpu = time.process_time() - c0
+    value = gamma.size * iters / wall
+    return {"value": value, "unit": UNIT, "cores": max(1, round(cpu / wall)), "kind": "oracle",
+            "sample": f"{iters} FP64 oracle iterations of one solve ({gamma.shape[0]}^3, normal "
+                      f"{wl['normals'][0]}) in {wall:.1f} s wall / {cpu:.1f} s CPU"}
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the CPU oracle, timed as it stands on the host cores. Each step is
+    one FP64 oracle iteration of one solve (normal e1) on the 64^3 corner block of the
+    workload's gamma field, treated as its own periodic cell (a bounded sample)."""
+    if rank != 0:
+        return
+    from oracle import ccmf_oracle as O
+    name = args.workload
+    wl = WORKLOADS[name]
+    gamma = np.ascontiguousarray(make_gamma(name, np.float64)[:64, :64, :64])
+    xi = np.asarray(wl["normals"][0], dtype=np.float64)
+    e = O.op_A(O.const_field(xi, gamma.shape))
+    v = np.zeros((6,) + gamma.shape)
+    rho = O.initial_rho(gamma, O.Params())
+
+    def step():
+        nonlocal e, v, rho
+        _, e2, v2 = O.admm_step(e, v, rho, gamma, xi, 0.25)
+        rho = O.next_rho(rho, O.RHO_BB, e, e2, v, v2, O.Params())
+        e, v = e2, v2
+
+    for _ in range(args.warmup):
+        step()
+    t0, c0 = time.perf_counter(), time.process_time()
+    for _ in range(args.steps):
+        step()
+    wall = time.perf_counter() - t0
+    cpu = time.process_time() - c0
+    value = gamma.size * args.steps / wall
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": wl["desc"] + " -- reference arm (CPU oracle): per step one iteration of one "
+                                               "solve (normal e1) on the 64^3 corner block",
+                       "grid": list(gamma.shape), "solves": 1},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": max(1, round(cpu / wall)), "kind": "oracle",
+                             "sample": f"{args.steps} FP64 oracle iterations of one solve on the 64^3 corner block "
+                                       f"after {args.warmup} warm-up iterations"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, world, rank, local):
+    import torch
+
+    import __graft_entry__
+    from paper_2103_05968_gb300 import ccmf
+
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    barrier(world)
+    __graft_entry__.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    name = args.workload
+    wl = WORKLOADS[name]
+    prec = ccmf.CCMF_FP64 if args.precision == "fp64" else ccmf.CCMF_FP32_MIXED
+    np_dtype = np.float64 if prec == ccmf.CCMF_FP64 else np.float32
+    esize = 8 if prec == ccmf.CCMF_FP64 else 4
+    gamma_np = make_gamma(name, np_dtype)
+    normals = np.asarray(wl["normals"], dtype=np.float64)
+    B = normals.shape[0]
+    n1, n2, n3 = gamma_np.shape
+    N = n1 * n2 * n3
+    plan = ccmf.Plan(gamma_np.shape, batch=B, precision=prec, device=dev)
+    gamma_dev = torch.from_numpy(gamma_np).to(dev)
+    K, W = args.steps, args.warmup
+
+    # initial state + warm-up (W iterations), untimed
+    plan.solve(gamma_dev, normals, ccmf.Params(fixed_iters=W, check_every=W))
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    p_timed = ccmf.Params(fixed_iters=K, check_every=K, resume=1)
+    # capture the graph outside the timed region (same key as the timed call)
+    plan.set_kernel_timing(True)
+    plan.solve(gamma_dev, normals, ccmf.Params(fixed_iters=K, check_every=K, resume=1))
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    plan.solve(gamma_dev, normals, p_timed, want_results=False)   # K iterations + final evaluation
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    t_ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    kt = plan.kernel_times()
+    plan.set_kernel_timing(False)
+    t_ms_max = max_over_ranks(t_ms, world)
+    value = world * N * B * K / (t_ms_max * 1e-3)
+
+    # roofline of the dominant kernel (events recorded inside the timed graph)
+    dom = max(kt, key=lambda k: kt[k][0])
+    dom_ms, dom_n = kt[dom]
+    per_launch_bytes = bytes_per_voxel(dom, esize, n3) * N * B
+    achieved = per_launch_bytes / (dom_ms / dom_n * 1e-3) / 1e9
+    peak, peak_kind = load_peaks()
+    kern = {k: {"ms_per_launch": ms / n, "launches": n, "share": ms / sum(x[0] for x in kt.values()),
+                "gbs": bytes_per_voxel(k, esize, n3) * N * B / (ms / n * 1e-3) / 1e9}
+            for k, (ms, n) in kt.items()}
+    step_bytes = sum(bytes_per_voxel(k, esize, n3) for k in kt) * N * B
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": dom, "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": per_launch_bytes,
+                "step_frac": step_bytes / (t_ms / K * 1e-3) / 1e9 / peak,
+                "floor_100B_frac": (100 if esize == 4 else 200) * N * B / (t_ms / K * 1e-3) / 1e9 / peak}
+
+    # end to end through the public API with host buffers: pinned gamma in, results out
+    gamma_host = torch.from_numpy(gamma_np).pin_memory()
+    p_e2e = ccmf.Params(fixed_iters=K, check_every=K)
+    plan.solve(gamma_host, normals, p_e2e)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    res, _, _ = plan.solve(gamma_host, normals, p_e2e)   # H2D of gamma, init, K iterations, results D2H
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(time.perf_counter() - t0, world)
+    e2e_value = world * N * B * K / t_e2e
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(name, max_seconds=args.cpu_seconds)
+
+    # kernels launched in the timed region: 6 per iteration, setup + gamma statistics, 6 for the final pass
+    launches = 6 * K + 2 + 6
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+                "ms_per_step": t_ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if esize == 8 else "f32", "data": "synthetic",
+                "config": {"workload": wl["desc"] + (" FP64" if esize == 8 else " FP32-mixed (FP64 reductions)"),
+                           "grid": [n1, n2, n3], "solves": B, "parallelism": f"replicas x{world}",
+                           "l2": f"inputs larger than L2: state {12 * esize * N * B / 1e6:.0f} MB per step",
+                           "precision": args.precision},
+                "roofline": roofline, "kernels": kern, "e2e": {
+                    "value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(esize * N / K),
+                    "d2h_bytes_per_step": int(B * 48 / K) + 1,
+                    "note": f"one ccmf_solve from pinned host gamma: H2D {esize * N} B, init, {K} iterations, "
+                            "final evaluation, results D2H"},
+                "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
+                "gamma_eff": [r["gamma_eff"] for r in res]}
+        print(json.dumps(line), flush=True)
+    plan.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="boolean128", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        run_reference(args, world, rank)
+        return
+    world, rank, local = dist_setup(args)
+    run_gpu(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

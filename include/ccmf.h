@@ -1,0 +1,185 @@
+/*
+ * ccmf.h - C ABI of the GB300 solver for the effective crack energy on a
+ * combinatorially consistent grid (CCMF discretisation, FFT-based damped ADMM).
+ *
+ * Paper: Ernesti & Schneider, "An FFT-based method for computing the effective
+ * crack energy of a heterogeneous material on a combinatorially consistent
+ * grid", arXiv:2103.05968. Equations are numbered as in the paper.
+ *
+ * Problem (Sec. 2.2, Sec. 3.1): given crack resistances gamma >= 0 sampled at
+ * the voxel centres of a periodic N1 x N2 x N3 grid and a crack normal xi_bar,
+ * compute the effective crack energy gamma_eff(xi_bar) as the common value of
+ * the CCMF maximum flow (Eq. 12) and the min-cut problem (Eq. 21), by the
+ * damped ADMM of Eq. 30 with the convergence criterion of Eq. 31.
+ *
+ * Memory layout (all arrays C-ordered, z fastest):
+ *   gamma : [batch][N1][N2][N3] (or one shared field, batch stride 0)
+ *   cut   : [batch][6][N1][N2][N3]  xi^{K+1/2}, the min-cut normal field (Eq. 21)
+ *   flow  : [batch][3][N1][N2][N3]  A* v^K, the face flows of Eq. 12
+ *           (component a of voxel p is the flow on face p + e_a / 2, Sec. 2.2)
+ *   state : e and v, each [batch][6][N1][N2][N3] (the split variable and the
+ *           multiplier of Eq. 24 / Eq. 30)
+ * Element type: double for CCMF_FP64 plans, float for CCMF_FP32_MIXED plans
+ * (the latter keep all global reductions and the penalty logic in double).
+ *
+ * Ownership: the caller owns every buffer. The library allocates only small
+ * constant tables inside the plan (plan_create) and never frees caller memory.
+ * Device pointers must come from the CUDA device that was current at
+ * plan_create. Where noted, a pointer may also be ordinary host memory; the
+ * library then stages it through the workspace and the call synchronises the
+ * stream before returning.
+ *
+ * Errors: every call returns a status code (CCMF_OK = 0); nothing throws.
+ * Non-convergence within max_iter is not an error (result.converged = 0).
+ * Per-solve device-side failures (invalid gamma, non-finite reductions) are
+ * reported in ccmf_result.status.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream). Calls enqueue work on it; the calls that return host results
+ * synchronise it.
+ */
+#ifndef CCMF_H
+#define CCMF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define CCMF_OK 0
+#define CCMF_ERR_INVALID_ARG 1      /* bad pointer, size, normal, tolerance, damping, rule */
+#define CCMF_ERR_UNSUPPORTED_SIZE 2 /* an N_i with a prime factor other than 2, 3, 5, or N_i > 1024 */
+#define CCMF_ERR_WORKSPACE 3        /* workspace missing or smaller than ccmf_plan_workspace_bytes */
+#define CCMF_ERR_CUDA 4             /* a CUDA runtime call failed */
+#define CCMF_ERR_NUMERICAL 5        /* gamma < 0 or non-finite, or a non-finite reduction */
+#define CCMF_ERR_TIMEOUT 6          /* a bounded device-side wait gave up */
+
+/* Precision of a plan. */
+#define CCMF_FP64 0        /* every field, FFT and reduction in double */
+#define CCMF_FP32_MIXED 1  /* fields and FFTs in float, reductions and penalty logic in double */
+
+/* Penalty rules (text after Eq. 30). */
+#define CCMF_RHO_BB 0     /* Barzilai-Borwein scaling with safeguard (default, Sec. 4.1) */
+#define CCMF_RHO_CONST 1  /* constant rho (Sec. 4.2, Sec. 4.3: the lower bound min gamma) */
+#define CCMF_RHO_LTD 2    /* Lorenz-Tran-Dinh scaling |v| / |e| */
+
+typedef struct ccmf_plan ccmf_plan;
+
+/* ADMM parameters (Eq. 30, Eq. 31, Sec. 4.1). */
+typedef struct {
+    double tol;          /* Eq. 31: stop once |e^k - xi^{k+1/2}|_L2 <= tol |<v^k>| (k >= 1); default 1e-4 */
+    double delta;        /* damping of Eq. 30, in (0, 1); default 0.25 */
+    double rho0;         /* initial penalty; <= 0 selects min(gamma) if positive, else mean(gamma) */
+    double bb_corr_min;  /* BB safeguard: minimum correlation <dv,de>/(|dv||de|); default 0.2 */
+    double rho_step_max; /* BB/LTD safeguard: rho changes by at most this factor per iteration; default 2 */
+    int max_iter;        /* upper bound on ADMM updates; default 20000 */
+    int rho_rule;        /* CCMF_RHO_BB (default), CCMF_RHO_CONST or CCMF_RHO_LTD */
+    int fixed_iters;     /* > 0: run exactly this many updates and ignore tol; default 0 */
+    int check_every;     /* updates per device-side loop chunk between host checks; default 32 */
+    int resume;          /* 1: start from the state already in the workspace instead of e^0, v^0 */
+    int history_len;     /* entries of the per-solve history ring kept in the workspace (<= 4096); default 1024 */
+} ccmf_params;
+
+/* Per-solve result (Eq. 21, Eq. 12, Eq. 31), evaluated on the final state. */
+typedef struct {
+    double gamma_eff;     /* reported effective crack energy = gamma_primal */
+    double gamma_primal;  /* mean(gamma |xi^{K+1/2}|), the min-cut objective of Eq. 21 */
+    double gamma_dual;    /* <xi_bar, A* v^K>, the max-flow objective of Eq. 12 */
+    double residual;      /* |e^K - xi^{K+1/2}|_L2 */
+    double mean_v_norm;   /* |<v^K>| (right-hand side of Eq. 31 without tol) */
+    double rho;           /* final penalty rho^K */
+    int iters;            /* ADMM updates performed (K) */
+    int converged;        /* 1 if Eq. 31 held */
+    int status;           /* CCMF_OK or CCMF_ERR_NUMERICAL / CCMF_ERR_INVALID_ARG for this solve */
+    int reserved;
+} ccmf_result;
+
+/* Fill *p with the defaults listed above. */
+void ccmf_params_default(ccmf_params* p);
+
+/* Human-readable text of a status code (static storage). */
+const char* ccmf_status_string(int status);
+
+/*
+ * Create a plan for `batch` independent solves on one n1 x n2 x n3 grid
+ * (Sec. 2.2: periodic grid, z fastest) in the given precision. Each N_i must be
+ * 1..1024 with prime factors 2, 3, 5 only (CCMF_ERR_UNSUPPORTED_SIZE otherwise);
+ * batch >= 1. Builds the FFT schedules and uploads twiddle and Laplacian-symbol
+ * tables (Eq. 28: div^- grad^+ has the symbol -sum_a 4 sin^2(pi k_a / N_a)) to
+ * the current device. *out receives the plan; free it with ccmf_plan_destroy.
+ */
+int ccmf_plan_create(int n1, int n2, int n3, int batch, int precision, ccmf_plan** out);
+
+/* Release a plan and its tables (NULL is accepted). */
+int ccmf_plan_destroy(ccmf_plan* plan);
+
+/* Bytes of device workspace a solve with this plan needs (state, spectra,
+ * reduction partials, history, host-I/O staging). */
+int ccmf_plan_workspace_bytes(const ccmf_plan* plan, size_t* bytes);
+
+/*
+ * Run the damped ADMM of Eq. 30 for every solve of the plan.
+ *   gamma        : crack resistances, device or host memory (element type of the plan)
+ *   gamma_stride : elements between consecutive solves' gamma fields (0 = all share one field)
+ *   xi_bar       : host array [batch][3], crack normals; normalised internally
+ *                  (gamma_eff is 1-homogeneous in xi_bar, Eq. 3); zero or non-finite -> INVALID_ARG
+ *   params       : ADMM parameters (NULL = defaults)
+ *   workspace    : device memory of at least ccmf_plan_workspace_bytes bytes, 256-byte aligned
+ *   flow, cut    : optional outputs (NULL to skip), device or host memory
+ *   results      : optional host array [batch]; when given, the call synchronises the stream
+ * The loop runs on the device; the host only relaunches a captured CUDA graph
+ * of params->check_every updates and reads one counter between chunks (no
+ * host round trip in fixed_iters mode).
+ */
+int ccmf_solve(ccmf_plan* plan, const void* gamma, long long gamma_stride, const double* xi_bar,
+               const ccmf_params* params, void* workspace, size_t workspace_bytes,
+               void* flow, void* cut, ccmf_result* results, void* stream);
+
+/*
+ * Copy the ADMM state of the workspace out (checkpoint): e and v ([batch][6][N]
+ * each, device or host memory, may be NULL), and per solve the penalty rho and
+ * the number of updates performed (host arrays [batch], may be NULL).
+ * Synchronises the stream.
+ */
+int ccmf_state_export(const ccmf_plan* plan, const void* workspace, void* e, void* v,
+                      double* rho, int* iters, void* stream);
+
+/*
+ * Load an ADMM state into the workspace (resume): e, v as in ccmf_state_export,
+ * rho and iters host arrays [batch]. A following ccmf_solve with params->resume = 1
+ * continues from it bit for bit. Synchronises the stream.
+ */
+int ccmf_state_import(const ccmf_plan* plan, void* workspace, const void* e, const void* v,
+                      const double* rho, const int* iters, void* stream);
+
+/*
+ * Copy the per-solve history ring to host memory: out[batch][max_entries][5]
+ * with (k, rho^k, |e^k - xi^{k+1/2}|_L2, |<v^k>|, mean(gamma |xi^{k+1/2}|)) for
+ * the most recent min(max_entries, history_len, iterations) updates, oldest
+ * first; *count receives the number of entries written per solve.
+ * Synchronises the stream.
+ */
+int ccmf_history_export(const ccmf_plan* plan, const void* workspace, double* out, int max_entries,
+                        int* count, void* stream);
+
+/*
+ * Per-kernel device time of the most recent ccmf_solve that ran with
+ * ccmf_set_kernel_timing(plan, 1): ms[i] = total milliseconds spent in kernel
+ * class i over the ADMM loop, launches[i] = number of launches; names[i]
+ * points to a static string. Returns the number of kernel classes in *count.
+ */
+int ccmf_kernel_times(const ccmf_plan* plan, double* ms, long long* launches, const char** names,
+                      int capacity, int* count);
+
+/* Enable (1) or disable (0) CUDA-event timing of every loop kernel for later
+ * ccmf_solve calls on this plan (events are recorded on the solve's stream
+ * inside the captured graph; fixed_iters mode only). */
+int ccmf_set_kernel_timing(ccmf_plan* plan, int enable);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CCMF_H */

@@ -1,0 +1,339 @@
+"""Thin Python binding of the CCMF solver's C ABI (include/ccmf.h).
+
+Every entry point of the C library is exposed under the same name with the
+same arguments (pointers as Python ints, host arrays as numpy arrays). The
+classes `Plan` and `solve` below only marshal torch tensors into those calls:
+PyTorch provides device memory and the stream, every step of the solver runs
+in the library's CUDA kernels. There is no fallback: if the compiled library
+is missing, loading it raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libccmf.so")
+
+CCMF_OK = 0
+CCMF_ERR_INVALID_ARG = 1
+CCMF_ERR_UNSUPPORTED_SIZE = 2
+CCMF_ERR_WORKSPACE = 3
+CCMF_ERR_CUDA = 4
+CCMF_ERR_NUMERICAL = 5
+CCMF_ERR_TIMEOUT = 6
+
+CCMF_FP64 = 0
+CCMF_FP32_MIXED = 1
+
+CCMF_RHO_BB = 0
+CCMF_RHO_CONST = 1
+CCMF_RHO_LTD = 2
+
+HIST_FIELDS = 5
+
+
+class ccmf_params(ctypes.Structure):
+    _fields_ = [
+        ("tol", ctypes.c_double),
+        ("delta", ctypes.c_double),
+        ("rho0", ctypes.c_double),
+        ("bb_corr_min", ctypes.c_double),
+        ("rho_step_max", ctypes.c_double),
+        ("max_iter", ctypes.c_int),
+        ("rho_rule", ctypes.c_int),
+        ("fixed_iters", ctypes.c_int),
+        ("check_every", ctypes.c_int),
+        ("resume", ctypes.c_int),
+        ("history_len", ctypes.c_int),
+    ]
+
+
+class ccmf_result(ctypes.Structure):
+    _fields_ = [
+        ("gamma_eff", ctypes.c_double),
+        ("gamma_primal", ctypes.c_double),
+        ("gamma_dual", ctypes.c_double),
+        ("residual", ctypes.c_double),
+        ("mean_v_norm", ctypes.c_double),
+        ("rho", ctypes.c_double),
+        ("iters", ctypes.c_int),
+        ("converged", ctypes.c_int),
+        ("status", ctypes.c_int),
+        ("reserved", ctypes.c_int),
+    ]
+
+
+_lib = None
+
+# name -> (restype, argtypes); mirrors include/ccmf.h
+_SIGNATURES = {
+    "ccmf_params_default": (None, [ctypes.POINTER(ccmf_params)]),
+    "ccmf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "ccmf_plan_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_void_p)]),
+    "ccmf_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "ccmf_plan_workspace_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    "ccmf_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong,
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ccmf_params), ctypes.c_void_p,
+                                   ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.POINTER(ccmf_result), ctypes.c_void_p]),
+    "ccmf_state_export": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                                          ctypes.c_void_p]),
+    "ccmf_state_import": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                                          ctypes.c_void_p]),
+    "ccmf_history_export": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                            ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
+    "ccmf_kernel_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_char_p),
+                                          ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "ccmf_set_kernel_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+}
+
+
+def load_library(path=LIB_PATH):
+    """Load libccmf.so (built by __graft_entry__.build()); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CCMF CUDA library not built: {path} is missing "
+                           "(run __graft_entry__.build() or python -m paper_2103_05968_gb300._build)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class CCMFError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {ccmf_status_string(code)} (status {code})")
+
+
+def _check(code, where):
+    if code != CCMF_OK:
+        raise CCMFError(code, where)
+
+
+# ---- same-name wrappers of the C entry points --------------------------------
+
+def ccmf_params_default():
+    p = ccmf_params()
+    load_library().ccmf_params_default(ctypes.byref(p))
+    return p
+
+
+def ccmf_status_string(status):
+    return load_library().ccmf_status_string(int(status)).decode()
+
+
+def ccmf_plan_create(n1, n2, n3, batch, precision):
+    out = ctypes.c_void_p()
+    code = load_library().ccmf_plan_create(int(n1), int(n2), int(n3), int(batch), int(precision), ctypes.byref(out))
+    return code, out.value
+
+
+def ccmf_plan_destroy(plan):
+    return load_library().ccmf_plan_destroy(plan)
+
+
+def ccmf_plan_workspace_bytes(plan):
+    b = ctypes.c_size_t()
+    code = load_library().ccmf_plan_workspace_bytes(plan, ctypes.byref(b))
+    return code, b.value
+
+
+def ccmf_solve(plan, gamma_ptr, gamma_stride, xi_bar, params, workspace_ptr, workspace_bytes, flow_ptr, cut_ptr,
+               results, stream):
+    xi = np.ascontiguousarray(xi_bar, dtype=np.float64).reshape(-1)
+    return load_library().ccmf_solve(plan, gamma_ptr, int(gamma_stride),
+                                     xi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     ctypes.byref(params) if params is not None else None,
+                                     workspace_ptr, int(workspace_bytes), flow_ptr, cut_ptr, results, stream)
+
+
+def ccmf_state_export(plan, workspace_ptr, e_ptr, v_ptr, batch, stream):
+    rho = (ctypes.c_double * batch)()
+    iters = (ctypes.c_int * batch)()
+    code = load_library().ccmf_state_export(plan, workspace_ptr, e_ptr, v_ptr, rho, iters, stream)
+    return code, np.array(rho[:]), np.array(iters[:])
+
+
+def ccmf_state_import(plan, workspace_ptr, e_ptr, v_ptr, rho, iters, stream):
+    r = (ctypes.c_double * len(rho))(*[float(x) for x in rho])
+    it = (ctypes.c_int * len(iters))(*[int(x) for x in iters])
+    return load_library().ccmf_state_import(plan, workspace_ptr, e_ptr, v_ptr, r, it, stream)
+
+
+def ccmf_history_export(plan, workspace_ptr, batch, max_entries, stream):
+    out = np.zeros((batch, max_entries, HIST_FIELDS))
+    cnt = ctypes.c_int()
+    code = load_library().ccmf_history_export(plan, workspace_ptr,
+                                              out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                              int(max_entries), ctypes.byref(cnt), stream)
+    return code, out[:, :cnt.value]
+
+
+def ccmf_kernel_times(plan):
+    cap = 16
+    ms = (ctypes.c_double * cap)()
+    launches = (ctypes.c_longlong * cap)()
+    names = (ctypes.c_char_p * cap)()
+    cnt = ctypes.c_int()
+    code = load_library().ccmf_kernel_times(plan, ms, launches, names, cap, ctypes.byref(cnt))
+    n = min(cnt.value, cap)
+    return code, {names[i].decode(): (ms[i], launches[i]) for i in range(n)}
+
+
+def ccmf_set_kernel_timing(plan, enable):
+    return load_library().ccmf_set_kernel_timing(plan, int(enable))
+
+
+# ---- torch-facing convenience layer (argument marshalling only) --------------
+
+@dataclasses.dataclass
+class Params:
+    tol: float = 1e-4
+    delta: float = 0.25
+    rho0: float = 0.0
+    bb_corr_min: float = 0.2
+    rho_step_max: float = 2.0
+    max_iter: int = 20000
+    rho_rule: int = CCMF_RHO_BB
+    fixed_iters: int = 0
+    check_every: int = 32
+    resume: int = 0
+    history_len: int = 1024
+
+    def to_c(self):
+        p = ccmf_params()
+        for f in dataclasses.fields(self):
+            setattr(p, f.name, getattr(self, f.name))
+        return p
+
+
+def _stream_handle(torch, device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+class Plan:
+    """A plan plus its torch-allocated workspace for `batch` solves on one grid."""
+
+    def __init__(self, shape, batch=1, precision=CCMF_FP32_MIXED, device="cuda"):
+        import torch
+
+        self.torch = torch
+        self.shape = tuple(int(x) for x in shape)
+        self.batch = int(batch)
+        self.precision = precision
+        self.device = torch.device(device)
+        self.dtype = torch.float64 if precision == CCMF_FP64 else torch.float32
+        with torch.cuda.device(self.device):
+            code, self.handle = ccmf_plan_create(*self.shape, self.batch, precision)
+            _check(code, "ccmf_plan_create")
+            code, nbytes = ccmf_plan_workspace_bytes(self.handle)
+            _check(code, "ccmf_plan_workspace_bytes")
+            self.workspace_bytes = nbytes
+            self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        self.ws_ptr = (base + 255) // 256 * 256
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ccmf_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_voxels(self):
+        n1, n2, n3 = self.shape
+        return n1 * n2 * n3
+
+    def solve(self, gamma, normals, params=None, want_flow=False, want_cut=False, gamma_shared=None,
+              want_results=True):
+        """Run the solver. gamma: torch tensor (device or host) of shape (N1,N2,N3) shared
+        by all solves, or (batch, N1, N2, N3). normals: (batch, 3). Returns (results, flow, cut)."""
+        torch = self.torch
+        params = params or Params()
+        g = gamma
+        if g.dtype != self.dtype:
+            raise TypeError(f"gamma must be {self.dtype} for this plan")
+        if not g.is_contiguous():
+            raise ValueError("gamma must be contiguous")
+        if gamma_shared is None:
+            gamma_shared = (g.dim() == 3)
+        stride = 0 if gamma_shared else self.n_voxels
+        normals = np.asarray(normals, dtype=np.float64).reshape(self.batch, 3)
+        n1, n2, n3 = self.shape
+        on_dev = g.is_cuda
+        flow = cut = None
+        if want_flow:
+            flow = torch.empty((self.batch, 3, n1, n2, n3), dtype=self.dtype, device=self.device if on_dev else "cpu")
+        if want_cut:
+            cut = torch.empty((self.batch, 6, n1, n2, n3), dtype=self.dtype, device=self.device if on_dev else "cpu")
+        res = (ccmf_result * self.batch)()
+        with torch.cuda.device(self.device):
+            code = ccmf_solve(self.handle, ctypes.c_void_p(g.data_ptr()), stride, normals, params.to_c(),
+                              ctypes.c_void_p(self.ws_ptr), self.workspace_bytes,
+                              ctypes.c_void_p(flow.data_ptr()) if flow is not None else None,
+                              ctypes.c_void_p(cut.data_ptr()) if cut is not None else None,
+                              res if want_results else None, _stream_handle(torch, self.device))
+        _check(code, "ccmf_solve")
+        if not want_results:
+            return None, flow, cut
+        results = [{f[0]: getattr(r, f[0]) for f in ccmf_result._fields_} for r in res]
+        return results, flow, cut
+
+    def state(self):
+        """(e, v, rho, iters): device copies of the ADMM state (checkpoint)."""
+        torch = self.torch
+        n1, n2, n3 = self.shape
+        e = torch.empty((self.batch, 6, n1, n2, n3), dtype=self.dtype, device=self.device)
+        v = torch.empty_like(e)
+        with torch.cuda.device(self.device):
+            code, rho, iters = ccmf_state_export(self.handle, ctypes.c_void_p(self.ws_ptr),
+                                                 ctypes.c_void_p(e.data_ptr()), ctypes.c_void_p(v.data_ptr()),
+                                                 self.batch, _stream_handle(torch, self.device))
+        _check(code, "ccmf_state_export")
+        return e, v, rho, iters
+
+    def load_state(self, e, v, rho, iters):
+        torch = self.torch
+        e = e.to(device=self.device, dtype=self.dtype).contiguous()
+        v = v.to(device=self.device, dtype=self.dtype).contiguous()
+        with torch.cuda.device(self.device):
+            code = ccmf_state_import(self.handle, ctypes.c_void_p(self.ws_ptr), ctypes.c_void_p(e.data_ptr()),
+                                     ctypes.c_void_p(v.data_ptr()), list(rho), list(iters),
+                                     _stream_handle(torch, self.device))
+        _check(code, "ccmf_state_import")
+
+    def history(self, max_entries=4096):
+        torch = self.torch
+        with torch.cuda.device(self.device):
+            code, h = ccmf_history_export(self.handle, ctypes.c_void_p(self.ws_ptr), self.batch, max_entries,
+                                          _stream_handle(torch, self.device))
+        _check(code, "ccmf_history_export")
+        return h
+
+    def set_kernel_timing(self, enable):
+        _check(ccmf_set_kernel_timing(self.handle, 1 if enable else 0), "ccmf_set_kernel_timing")
+
+    def kernel_times(self):
+        code, t = ccmf_kernel_times(self.handle)
+        _check(code, "ccmf_kernel_times")
+        return t

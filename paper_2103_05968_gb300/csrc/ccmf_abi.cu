@@ -1,0 +1,620 @@
+// C ABI of the CCMF FFT-ADMM solver: plans, workspace layout, the device-side
+// iteration loop (captured CUDA graphs) and state / history / timing access.
+// See include/ccmf.h for the contract of every entry point.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "../../include/ccmf.h"
+#include "ccmf_launch.cuh"
+
+using namespace ccmf;
+
+namespace ccmf {
+template <typename T> cudaError_t configure_kernels(const LaunchShape&);
+template <typename T> void launch_init(const Ctx<T>&, cudaStream_t);
+template <typename T> void launch_iteration(const Ctx<T>&, cudaStream_t);
+template <typename T> void launch_iteration_timed(const Ctx<T>&, cudaStream_t, cudaEvent_t*);
+template <typename T> void launch_final(const Ctx<T>&, cudaStream_t, T*, T*);
+}  // namespace ccmf
+
+namespace {
+
+constexpr int kMaxN = 1024;
+constexpr size_t kSmemBudget = 96 * 1024;
+constexpr int kMaxTimedIters = 2048;
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+// Radix schedule for a line of length n (prime factors 2, 3, 5): 8s first, then
+// 4 / 2, then 3s and 5s. Returns false for unsupported n.
+bool make_axis_plan(int n, AxisPlan* ap) {
+    memset(ap, 0, sizeof(*ap));
+    ap->n = n;
+    int m = n, st = 0;
+    auto push = [&](int r) {
+        if (st >= kMaxStages) return false;
+        ap->rad[st++] = r;
+        m /= r;
+        return true;
+    };
+    while (m % 8 == 0)
+        if (!push(8)) return false;
+    while (m % 4 == 0)
+        if (!push(4)) return false;
+    while (m % 2 == 0)
+        if (!push(2)) return false;
+    while (m % 3 == 0)
+        if (!push(3)) return false;
+    while (m % 5 == 0)
+        if (!push(5)) return false;
+    ap->nst = st;
+    return m == 1;
+}
+
+struct GraphKey {
+    int chunk, timed;
+    const void* ws;
+    const void* gamma;
+    long long gstride;
+    LoopConfig cfg;
+};
+
+}  // namespace
+
+struct ccmf_plan {
+    int n1, n2, n3, n3h, batch, prec, device;
+    size_t esize;  // bytes per real element
+    Geom g;
+    AxisPlan ax[3];
+    LaunchShape sh;
+    void* tw[3];
+    void* sym[3];
+    // workspace layout
+    size_t off_sc, off_nact, off_xi, off_part, off_hist, off_e, off_v, off_spec, off_phi, off_gam, off_cut,
+        off_flow, total;
+    cudaStream_t cap_stream;
+    int* h_nactive;  // pinned
+    // captured loop graph
+    cudaGraphExec_t gexec;
+    GraphKey gkey;
+    bool have_graph;
+    // timing
+    int timing;
+    std::vector<cudaEvent_t> events;
+    int timed_iters;
+    double kms[kNumKernelClasses];
+    long long klaunch[kNumKernelClasses];
+    long long launches_last;
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? CCMF_OK : CCMF_ERR_CUDA; }
+
+bool is_device_ptr(const void* ptr) {
+    if (!ptr) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+Ctx<T> make_ctx(const ccmf_plan* pl, unsigned char* ws, const T* gamma, long long gstride, const LoopConfig& cfg) {
+    Ctx<T> c;
+    memset(&c, 0, sizeof(c));
+    c.g = pl->g;
+    c.cfg = cfg;
+    for (int a = 0; a < 3; ++a) {
+        c.ax[a] = pl->ax[a];
+        c.tw[a] = reinterpret_cast<const cx<T>*>(pl->tw[a]);
+        c.sym[a] = reinterpret_cast<const T*>(pl->sym[a]);
+    }
+    c.sh = pl->sh;
+    c.xi_stage = reinterpret_cast<const double*>(ws + pl->off_xi);
+    c.p.sc = reinterpret_cast<SolveScalars*>(ws + pl->off_sc);
+    c.p.n_active = reinterpret_cast<int*>(ws + pl->off_nact);
+    c.p.partial = reinterpret_cast<double*>(ws + pl->off_part);
+    c.p.hist = reinterpret_cast<double*>(ws + pl->off_hist);
+    c.p.e = reinterpret_cast<T*>(ws + pl->off_e);
+    c.p.v = reinterpret_cast<T*>(ws + pl->off_v);
+    c.p.spec = reinterpret_cast<cx<T>*>(ws + pl->off_spec);
+    c.p.phi = reinterpret_cast<T*>(ws + pl->off_phi);
+    c.p.gamma = gamma;
+    c.p.gstride = gstride;
+    c.p.cut = nullptr;
+    c.p.flow = nullptr;
+    c.p.run_all = 0;
+    return c;
+}
+
+void destroy_graph(ccmf_plan* pl) {
+    if (pl->have_graph) cudaGraphExecDestroy(pl->gexec);
+    pl->have_graph = false;
+}
+
+template <typename T>
+int capture_loop(ccmf_plan* pl, const Ctx<T>& c, const GraphKey& key) {
+    if (pl->have_graph && memcmp(&pl->gkey, &key, sizeof(key)) == 0) return CCMF_OK;
+    destroy_graph(pl);
+    if (key.timed) {
+        size_t need = (size_t)key.chunk * kNumKernelClasses + 1;
+        while (pl->events.size() < need) {
+            cudaEvent_t ev;
+            if (cudaEventCreate(&ev) != cudaSuccess) return CCMF_ERR_CUDA;
+            pl->events.push_back(ev);
+        }
+    }
+    cudaGraph_t graph;
+    cudaError_t err = cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (err != cudaSuccess) return CCMF_ERR_CUDA;
+    if (key.timed) cudaEventRecordWithFlags(pl->events[0], pl->cap_stream, cudaEventRecordExternal);
+    for (int it = 0; it < key.chunk; ++it) {
+        if (key.timed)
+            launch_iteration_timed<T>(c, pl->cap_stream, pl->events.data() + (size_t)it * kNumKernelClasses);
+        else
+            launch_iteration<T>(c, pl->cap_stream);
+    }
+    err = cudaStreamEndCapture(pl->cap_stream, &graph);
+    if (err != cudaSuccess) return CCMF_ERR_CUDA;
+    err = cudaGraphInstantiate(&pl->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (err != cudaSuccess) return CCMF_ERR_CUDA;
+    pl->gkey = key;
+    pl->have_graph = true;
+    return CCMF_OK;
+}
+
+template <typename T>
+int solve_impl(ccmf_plan* pl, const void* gamma_in, long long gstride_in, const double* xi_host,
+               const ccmf_params* prm, unsigned char* ws, void* flow, void* cut, ccmf_result* results,
+               cudaStream_t st) {
+    const Geom& g = pl->g;
+    const size_t N = (size_t)g.N;
+    // gamma: device pointer or host memory staged into the workspace
+    const T* gamma = reinterpret_cast<const T*>(gamma_in);
+    long long gstride = gstride_in;
+    if (!is_device_ptr(gamma_in)) {
+        T* stage = reinterpret_cast<T*>(ws + pl->off_gam);
+        size_t fields = gstride_in == 0 ? 1 : (size_t)g.batch;
+        for (size_t s = 0; s < fields; ++s) {
+            if (cudaMemcpyAsync(stage + s * N, reinterpret_cast<const T*>(gamma_in) + s * (size_t)gstride_in,
+                                N * sizeof(T), cudaMemcpyHostToDevice, st) != cudaSuccess)
+                return CCMF_ERR_CUDA;
+        }
+        gamma = stage;
+        gstride = gstride_in == 0 ? 0 : (long long)N;
+    }
+    // unit normals
+    std::vector<double> xi(3 * (size_t)g.batch);
+    for (int s = 0; s < g.batch; ++s) {
+        const double* x = xi_host + 3 * s;
+        double nn = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        for (int a = 0; a < 3; ++a) xi[3 * s + a] = x[a] / nn;
+    }
+    if (cudaMemcpyAsync(ws + pl->off_xi, xi.data(), xi.size() * sizeof(double), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+        return CCMF_ERR_CUDA;
+    if (cudaMemsetAsync(ws + pl->off_nact, 0, sizeof(int), st) != cudaSuccess) return CCMF_ERR_CUDA;
+    if (!prm->resume &&
+        cudaMemsetAsync(ws + pl->off_hist, 0xFF, sizeof(double) * kHistFields * (size_t)kHistCap * g.batch, st) !=
+            cudaSuccess)
+        return CCMF_ERR_CUDA;
+
+    LoopConfig cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.tol = prm->tol;
+    cfg.delta = prm->delta;
+    cfg.rho0 = prm->rho0;
+    cfg.bb_corr_min = prm->bb_corr_min;
+    cfg.rho_step_max = prm->rho_step_max;
+    cfg.max_iter = prm->max_iter;
+    cfg.fixed_iters = prm->fixed_iters;
+    cfg.rho_rule = prm->rho_rule;
+    cfg.hist_len = prm->history_len;
+    cfg.resume = prm->resume;
+    Ctx<T> c = make_ctx<T>(pl, ws, gamma, gstride, cfg);
+
+    launch_init<T>(c, st);
+    if (cudaGetLastError() != cudaSuccess) return CCMF_ERR_CUDA;
+
+    const bool fixed = prm->fixed_iters > 0;
+    const int total = fixed ? prm->fixed_iters : prm->max_iter;
+    const bool timed = pl->timing && fixed;
+    int chunk = timed ? total : (prm->check_every < total ? prm->check_every : total);
+    if (timed && total > kMaxTimedIters) return CCMF_ERR_INVALID_ARG;
+    GraphKey key;
+    memset(&key, 0, sizeof(key));
+    key.chunk = chunk;
+    key.timed = timed ? 1 : 0;
+    key.ws = ws;
+    key.gamma = gamma;
+    key.gstride = gstride;
+    key.cfg = cfg;
+    int rc = capture_loop<T>(pl, c, key);
+    if (rc != CCMF_OK) return rc;
+    const long long nchunks_max = ((long long)total + chunk - 1) / chunk;
+    pl->launches_last = 0;
+    for (long long ch = 0; ch < nchunks_max; ++ch) {
+        if (cudaGraphLaunch(pl->gexec, st) != cudaSuccess) return CCMF_ERR_CUDA;
+        pl->launches_last += (long long)chunk * kNumKernelClasses;
+        if (!fixed) {
+            if (cudaMemcpyAsync(pl->h_nactive, ws + pl->off_nact, sizeof(int), cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess)
+                return CCMF_ERR_CUDA;
+            if (cudaStreamSynchronize(st) != cudaSuccess) return CCMF_ERR_CUDA;
+            if (*pl->h_nactive <= 0) break;
+        }
+    }
+    // final evaluation of the state (cut, flow, primal and dual objectives)
+    const bool cut_host = cut && !is_device_ptr(cut);
+    const bool flow_host = flow && !is_device_ptr(flow);
+    T* cut_d = cut_host ? reinterpret_cast<T*>(ws + pl->off_cut) : reinterpret_cast<T*>(cut);
+    T* flow_d = flow_host ? reinterpret_cast<T*>(ws + pl->off_flow) : reinterpret_cast<T*>(flow);
+    launch_final<T>(c, st, cut_d, flow_d);
+    if (cudaGetLastError() != cudaSuccess) return CCMF_ERR_CUDA;
+    if (cut_host && cudaMemcpyAsync(cut, cut_d, (size_t)g.batch * 6 * N * sizeof(T), cudaMemcpyDeviceToHost, st) !=
+                        cudaSuccess)
+        return CCMF_ERR_CUDA;
+    if (flow_host &&
+        cudaMemcpyAsync(flow, flow_d, (size_t)g.batch * 3 * N * sizeof(T), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return CCMF_ERR_CUDA;
+    if (results || cut_host || flow_host || timed) {
+        std::vector<SolveScalars> sc(g.batch);
+        if (cudaMemcpyAsync(sc.data(), ws + pl->off_sc, sizeof(SolveScalars) * g.batch, cudaMemcpyDeviceToHost,
+                            st) != cudaSuccess)
+            return CCMF_ERR_CUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return CCMF_ERR_CUDA;
+        if (results) {
+            for (int s = 0; s < g.batch; ++s) {
+                ccmf_result& r = results[s];
+                r.gamma_primal = sc[s].primal;
+                r.gamma_eff = sc[s].primal;
+                r.gamma_dual = sc[s].dual;
+                r.residual = sc[s].residual;
+                r.mean_v_norm = sc[s].mean_v;
+                r.rho = sc[s].rho;
+                r.iters = sc[s].iters;
+                r.converged = sc[s].converged;
+                r.status = sc[s].status;
+                r.reserved = 0;
+            }
+        }
+    }
+    if (timed) {
+        for (int k = 0; k < kNumKernelClasses; ++k) {
+            pl->kms[k] = 0.0;
+            pl->klaunch[k] = 0;
+        }
+        for (int it = 0; it < chunk; ++it)
+            for (int k = 0; k < kNumKernelClasses; ++k) {
+                float ms = 0.f;
+                size_t a = (size_t)it * kNumKernelClasses + k;
+                if (cudaEventElapsedTime(&ms, pl->events[a], pl->events[a + 1]) == cudaSuccess) {
+                    pl->kms[k] += ms;
+                    pl->klaunch[k] += 1;
+                }
+            }
+        pl->timed_iters = chunk;
+    }
+    return CCMF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ccmf_params_default(ccmf_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->tol = 1e-4;
+    p->delta = 0.25;
+    p->rho0 = 0.0;
+    p->bb_corr_min = 0.2;
+    p->rho_step_max = 2.0;
+    p->max_iter = 20000;
+    p->rho_rule = CCMF_RHO_BB;
+    p->fixed_iters = 0;
+    p->check_every = 32;
+    p->resume = 0;
+    p->history_len = 1024;
+}
+
+const char* ccmf_status_string(int status) {
+    switch (status) {
+        case CCMF_OK: return "ok";
+        case CCMF_ERR_INVALID_ARG: return "invalid argument";
+        case CCMF_ERR_UNSUPPORTED_SIZE: return "unsupported grid size (N_i must be 1..1024 with prime factors 2, 3, 5)";
+        case CCMF_ERR_WORKSPACE: return "workspace missing or too small";
+        case CCMF_ERR_CUDA: return "CUDA runtime error";
+        case CCMF_ERR_NUMERICAL: return "numerical failure (invalid gamma or non-finite reduction)";
+        case CCMF_ERR_TIMEOUT: return "device-side wait timed out";
+        default: return "unknown status";
+    }
+}
+
+int ccmf_plan_create(int n1, int n2, int n3, int batch, int precision, ccmf_plan** out) {
+    if (!out) return CCMF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n1 < 1 || n2 < 1 || n3 < 1 || batch < 1 || batch > 65535) return CCMF_ERR_INVALID_ARG;
+    if (precision != CCMF_FP64 && precision != CCMF_FP32_MIXED) return CCMF_ERR_INVALID_ARG;
+    if (n1 > kMaxN || n2 > kMaxN || n3 > kMaxN) return CCMF_ERR_UNSUPPORTED_SIZE;
+    AxisPlan ax[3];
+    const int nn[3] = {n1, n2, n3};
+    for (int a = 0; a < 3; ++a)
+        if (!make_axis_plan(nn[a], &ax[a])) return CCMF_ERR_UNSUPPORTED_SIZE;
+
+    ccmf_plan* pl = new (std::nothrow) ccmf_plan();
+    if (!pl) return CCMF_ERR_INVALID_ARG;
+    pl->n1 = n1;
+    pl->n2 = n2;
+    pl->n3 = n3;
+    pl->n3h = n3 / 2 + 1;
+    pl->batch = batch;
+    pl->prec = precision;
+    pl->esize = precision == CCMF_FP64 ? 8 : 4;
+    for (int a = 0; a < 3; ++a) pl->ax[a] = ax[a];
+    Geom& g = pl->g;
+    g.n1 = n1;
+    g.n2 = n2;
+    g.n3 = n3;
+    g.n3h = pl->n3h;
+    g.batch = batch;
+    g.N = (long long)n1 * n2 * n3;
+    g.Nh = (long long)n1 * n2 * pl->n3h;
+    g.div_n3 = make_fastdiv((unsigned)n3);
+    g.div_n2 = make_fastdiv((unsigned)n2);
+    g.div_n3h = make_fastdiv((unsigned)pl->n3h);
+
+    // launch shape
+    const size_t cs = 2 * pl->esize;  // complex element
+    LaunchShape& sh = pl->sh;
+    {
+        long long P = ((long long)(kSmemBudget / cs) - n3) / (2LL * n3) - 1;
+        if (P > 16) P = 16;
+        if (P < 1) P = 1;
+        sh.pairs_per_block = (int)P;
+        sh.smem_z = ((size_t)n3 + 2 * (size_t)n3 * (P + 1)) * cs;
+        auto lpb_for = [&](int n) {
+            long long L = ((long long)(kSmemBudget / cs) - n) / (2LL * n) - 1;
+            if (L > 16) L = 16;
+            if (L < 1) L = 1;
+            return (int)L;
+        };
+        sh.lpb_y = lpb_for(n2);
+        sh.lpb_x = lpb_for(n1);
+        sh.smem_y = ((size_t)n2 + 2 * (size_t)n2 * (sh.lpb_y + 1)) * cs;
+        sh.smem_x = ((size_t)n1 + 2 * (size_t)n1 * (sh.lpb_x + 1)) * cs;
+        long long gu = (g.N + kThreads - 1) / kThreads;
+        if (gu > 608) gu = 608;
+        sh.grid_update = (int)gu;
+    }
+
+    // workspace layout
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes);
+        return o;
+    };
+    const size_t N = (size_t)g.N;
+    pl->off_sc = take(256 * (size_t)batch);
+    pl->off_nact = take(256);
+    pl->off_xi = take(3 * sizeof(double) * batch);
+    pl->off_part = take(sizeof(double) * kNSum * (size_t)sh.grid_update * batch);
+    pl->off_hist = take(sizeof(double) * kHistFields * (size_t)kHistCap * batch);
+    pl->off_e = take(pl->esize * 6 * N * batch);
+    pl->off_v = take(pl->esize * 6 * N * batch);
+    pl->off_spec = take(cs * (size_t)g.Nh * batch);
+    pl->off_phi = take(pl->esize * N * batch);
+    pl->off_gam = take(pl->esize * N * batch);
+    pl->off_cut = take(pl->esize * 6 * N * batch);
+    pl->off_flow = take(pl->esize * 3 * N * batch);
+    pl->total = off;
+
+    int rc = CCMF_OK;
+    if (cudaGetDevice(&pl->device) != cudaSuccess) rc = CCMF_ERR_CUDA;
+    // twiddle and symbol tables
+    for (int a = 0; a < 3 && rc == CCMF_OK; ++a) {
+        const int n = nn[a];
+        std::vector<double> tw(2 * (size_t)n), sy((size_t)n);
+        for (int t = 0; t < n; ++t) {
+            const double ang = -2.0 * kPi * (double)t / (double)n;
+            tw[2 * t] = cos(ang);
+            tw[2 * t + 1] = sin(ang);
+            const double sn = sin(kPi * (double)t / (double)n);
+            sy[t] = 4.0 * sn * sn;
+        }
+        if (precision == CCMF_FP64) {
+            if (cudaMalloc(&pl->tw[a], tw.size() * 8) != cudaSuccess ||
+                cudaMemcpy(pl->tw[a], tw.data(), tw.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMalloc(&pl->sym[a], sy.size() * 8) != cudaSuccess ||
+                cudaMemcpy(pl->sym[a], sy.data(), sy.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+                rc = CCMF_ERR_CUDA;
+        } else {
+            std::vector<float> twf(tw.begin(), tw.end()), syf(sy.begin(), sy.end());
+            if (cudaMalloc(&pl->tw[a], twf.size() * 4) != cudaSuccess ||
+                cudaMemcpy(pl->tw[a], twf.data(), twf.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMalloc(&pl->sym[a], syf.size() * 4) != cudaSuccess ||
+                cudaMemcpy(pl->sym[a], syf.data(), syf.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+                rc = CCMF_ERR_CUDA;
+        }
+    }
+    if (rc == CCMF_OK) {
+        cudaError_t e = precision == CCMF_FP64 ? configure_kernels<double>(sh) : configure_kernels<float>(sh);
+        if (e != cudaSuccess) rc = CCMF_ERR_CUDA;
+    }
+    if (rc == CCMF_OK && cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        rc = CCMF_ERR_CUDA;
+    if (rc == CCMF_OK && cudaMallocHost((void**)&pl->h_nactive, sizeof(int)) != cudaSuccess) rc = CCMF_ERR_CUDA;
+    if (rc != CCMF_OK) {
+        ccmf_plan_destroy(pl);
+        return rc;
+    }
+    *out = pl;
+    return CCMF_OK;
+}
+
+int ccmf_plan_destroy(ccmf_plan* pl) {
+    if (!pl) return CCMF_OK;
+    destroy_graph(pl);
+    for (cudaEvent_t ev : pl->events) cudaEventDestroy(ev);
+    for (int a = 0; a < 3; ++a) {
+        if (pl->tw[a]) cudaFree(pl->tw[a]);
+        if (pl->sym[a]) cudaFree(pl->sym[a]);
+    }
+    if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+    if (pl->h_nactive) cudaFreeHost(pl->h_nactive);
+    delete pl;
+    return CCMF_OK;
+}
+
+int ccmf_plan_workspace_bytes(const ccmf_plan* plan, size_t* bytes) {
+    if (!plan || !bytes) return CCMF_ERR_INVALID_ARG;
+    *bytes = plan->total;
+    return CCMF_OK;
+}
+
+int ccmf_solve(ccmf_plan* plan, const void* gamma, long long gamma_stride, const double* xi_bar,
+               const ccmf_params* params, void* workspace, size_t workspace_bytes, void* flow, void* cut,
+               ccmf_result* results, void* stream) {
+    if (!plan || !gamma || !xi_bar || gamma_stride < 0) return CCMF_ERR_INVALID_ARG;
+    ccmf_params prm;
+    if (params)
+        prm = *params;
+    else
+        ccmf_params_default(&prm);
+    for (int s = 0; s < plan->batch; ++s) {
+        const double* x = xi_bar + 3 * s;
+        const double nn = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+        if (!isfinite(x[0]) || !isfinite(x[1]) || !isfinite(x[2]) || !(nn > 0.0) || !isfinite(nn))
+            return CCMF_ERR_INVALID_ARG;
+    }
+    if (prm.fixed_iters < 0 || prm.max_iter < 1 || prm.check_every < 1) return CCMF_ERR_INVALID_ARG;
+    if (prm.fixed_iters == 0 && !(prm.tol > 0.0)) return CCMF_ERR_INVALID_ARG;
+    if (!(prm.delta > 0.0 && prm.delta < 1.0)) return CCMF_ERR_INVALID_ARG;
+    if (prm.rho_rule < CCMF_RHO_BB || prm.rho_rule > CCMF_RHO_LTD) return CCMF_ERR_INVALID_ARG;
+    if (!(prm.rho_step_max >= 1.0) || !isfinite(prm.rho0) || !isfinite(prm.bb_corr_min)) return CCMF_ERR_INVALID_ARG;
+    if (prm.history_len < 0 || prm.history_len > kHistCap) return CCMF_ERR_INVALID_ARG;
+    if (prm.resume != 0 && prm.resume != 1) return CCMF_ERR_INVALID_ARG;
+    if (!workspace || workspace_bytes < plan->total) return CCMF_ERR_WORKSPACE;
+    if (((uintptr_t)workspace & 255u) != 0) return CCMF_ERR_WORKSPACE;
+    if (cudaSetDevice(plan->device) != cudaSuccess) return CCMF_ERR_CUDA;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    unsigned char* ws = reinterpret_cast<unsigned char*>(workspace);
+    if (plan->prec == CCMF_FP64)
+        return solve_impl<double>(plan, gamma, gamma_stride, xi_bar, &prm, ws, flow, cut, results, st);
+    return solve_impl<float>(plan, gamma, gamma_stride, xi_bar, &prm, ws, flow, cut, results, st);
+}
+
+int ccmf_state_export(const ccmf_plan* plan, const void* workspace, void* e, void* v, double* rho, int* iters,
+                      void* stream) {
+    if (!plan || !workspace) return CCMF_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const unsigned char* ws = reinterpret_cast<const unsigned char*>(workspace);
+    const size_t bytes = plan->esize * 6 * (size_t)plan->g.N * plan->batch;
+    if (e && cudaMemcpyAsync(e, ws + plan->off_e, bytes, cudaMemcpyDefault, st) != cudaSuccess) return CCMF_ERR_CUDA;
+    if (v && cudaMemcpyAsync(v, ws + plan->off_v, bytes, cudaMemcpyDefault, st) != cudaSuccess) return CCMF_ERR_CUDA;
+    std::vector<SolveScalars> sc(plan->batch);
+    if (cudaMemcpyAsync(sc.data(), ws + plan->off_sc, sizeof(SolveScalars) * plan->batch, cudaMemcpyDeviceToHost,
+                        st) != cudaSuccess)
+        return CCMF_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return CCMF_ERR_CUDA;
+    for (int s = 0; s < plan->batch; ++s) {
+        if (rho) rho[s] = sc[s].rho;
+        if (iters) iters[s] = sc[s].iters;
+    }
+    return CCMF_OK;
+}
+
+int ccmf_state_import(const ccmf_plan* plan, void* workspace, const void* e, const void* v, const double* rho,
+                      const int* iters, void* stream) {
+    if (!plan || !workspace || !e || !v || !rho || !iters) return CCMF_ERR_INVALID_ARG;
+    for (int s = 0; s < plan->batch; ++s)
+        if (!(rho[s] > 0.0) || !isfinite(rho[s]) || iters[s] < 0) return CCMF_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    unsigned char* ws = reinterpret_cast<unsigned char*>(workspace);
+    const size_t bytes = plan->esize * 6 * (size_t)plan->g.N * plan->batch;
+    if (cudaMemcpyAsync(ws + plan->off_e, e, bytes, cudaMemcpyDefault, st) != cudaSuccess) return CCMF_ERR_CUDA;
+    if (cudaMemcpyAsync(ws + plan->off_v, v, bytes, cudaMemcpyDefault, st) != cudaSuccess) return CCMF_ERR_CUDA;
+    std::vector<SolveScalars> sc(plan->batch);
+    if (cudaMemcpyAsync(sc.data(), ws + plan->off_sc, sizeof(SolveScalars) * plan->batch, cudaMemcpyDeviceToHost,
+                        st) != cudaSuccess)
+        return CCMF_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return CCMF_ERR_CUDA;
+    for (int s = 0; s < plan->batch; ++s) {
+        sc[s].rho = rho[s];
+        sc[s].iters = iters[s];
+    }
+    if (cudaMemcpyAsync(ws + plan->off_sc, sc.data(), sizeof(SolveScalars) * plan->batch, cudaMemcpyHostToDevice,
+                        st) != cudaSuccess)
+        return CCMF_ERR_CUDA;
+    return cuda_status(cudaStreamSynchronize(st));
+}
+
+int ccmf_history_export(const ccmf_plan* plan, const void* workspace, double* out, int max_entries, int* count,
+                        void* stream) {
+    if (!plan || !workspace || !out || max_entries < 1 || !count) return CCMF_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const unsigned char* ws = reinterpret_cast<const unsigned char*>(workspace);
+    std::vector<SolveScalars> sc(plan->batch);
+    std::vector<double> hist((size_t)plan->batch * kHistCap * kHistFields);
+    if (cudaMemcpyAsync(sc.data(), ws + plan->off_sc, sizeof(SolveScalars) * plan->batch, cudaMemcpyDeviceToHost,
+                        st) != cudaSuccess ||
+        cudaMemcpyAsync(hist.data(), ws + plan->off_hist, hist.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                        st) != cudaSuccess)
+        return CCMF_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return CCMF_ERR_CUDA;
+    // history_len of the last solve is not stored; entries carry their own k.
+    int written = 0;
+    for (int s = 0; s < plan->batch; ++s) {
+        const double* hs = hist.data() + (size_t)s * kHistCap * kHistFields;
+        const int iters = sc[s].iters;
+        // collect entries with k in [iters - max_entries, iters), oldest first
+        std::vector<const double*> rows;
+        for (int t = 0; t < kHistCap; ++t) {
+            const double* r = hs + (size_t)t * kHistFields;
+            const double k = r[0];
+            if (k >= 0.0 && k < iters && k >= (double)(iters - max_entries) && k == floor(k)) rows.push_back(r);
+        }
+        std::sort(rows.begin(), rows.end(), [](const double* a, const double* b) { return a[0] < b[0]; });
+        int n = 0;
+        double* dst = out + (size_t)s * max_entries * kHistFields;
+        for (size_t a = 0; a < rows.size() && n < max_entries; ++a) {
+            if (n > 0 && dst[(size_t)(n - 1) * kHistFields] == rows[a][0]) continue;
+            memcpy(dst + (size_t)n * kHistFields, rows[a], kHistFields * sizeof(double));
+            ++n;
+        }
+        written = n > written ? n : written;
+    }
+    *count = written;
+    return CCMF_OK;
+}
+
+int ccmf_kernel_times(const ccmf_plan* plan, double* ms, long long* launches, const char** names, int capacity,
+                      int* count) {
+    if (!plan || !count) return CCMF_ERR_INVALID_ARG;
+    *count = kNumKernelClasses;
+    for (int k = 0; k < kNumKernelClasses && k < capacity; ++k) {
+        if (ms) ms[k] = plan->kms[k];
+        if (launches) launches[k] = plan->klaunch[k];
+        if (names) names[k] = kernel_class_name(k);
+    }
+    return CCMF_OK;
+}
+
+int ccmf_set_kernel_timing(ccmf_plan* plan, int enable) {
+    if (!plan || (enable != 0 && enable != 1)) return CCMF_ERR_INVALID_ARG;
+    plan->timing = enable;
+    return CCMF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,10 @@
+// Explicit instantiation of the solver launch sequences for float fields.
+#include "ccmf_launch.cuh"
+
+namespace ccmf {
+template cudaError_t configure_kernels<float>(const LaunchShape&);
+template void launch_init<float>(const Ctx<float>&, cudaStream_t);
+template void launch_iteration<float>(const Ctx<float>&, cudaStream_t);
+template void launch_iteration_timed<float>(const Ctx<float>&, cudaStream_t, cudaEvent_t*);
+template void launch_final<float>(const Ctx<float>&, cudaStream_t, float*, float*);
+}  // namespace ccmf

@@ -1,0 +1,176 @@
+// Mixed-radix (2, 3, 4, 5, 8) Stockham FFT of a tile of lines held in shared memory.
+//
+// The Poisson solve inside the projection onto K (Eq. 28 of the paper,
+// Gamma = grad^+ (div^- grad^+)^+ div^-) is diagonal in Fourier space; these
+// routines provide the forward transforms X[m] = sum_t x[t] exp(-2 pi i m t / n)
+// that the solver kernels apply along each grid axis. The inverse transform is
+// obtained by conjugating input and output.
+//
+// Tile layout: `lines` complex lines of length n, element m of line c at
+// buf[m * stride + c] (stride >= lines; stride = lines + 1 avoids bank conflicts).
+// Each stage of radix R reads from one buffer and writes to the other
+// (autosort: the result is in natural order), so the caller provides two buffers
+// and gets back the one that holds the result.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace ccmf {
+
+constexpr int kMaxStages = 12;
+
+struct AxisPlan {
+    int n;                  // line length
+    int nst;                // number of radix stages
+    int rad[kMaxStages];    // radix of each stage, product = n
+};
+
+template <typename T> struct CxOf;
+template <> struct CxOf<float> { using type = float2; };
+template <> struct CxOf<double> { using type = double2; };
+template <typename T> using cx = typename CxOf<T>::type;
+
+template <typename C> __device__ __forceinline__ C cmake(decltype(C::x) a, decltype(C::x) b) { C r; r.x = a; r.y = b; return r; }
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return cmake<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return cmake<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+    return cmake<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { return cmake<C>(a.x, -a.y); }
+// multiply by -i
+template <typename C> __device__ __forceinline__ C cmul_mi(C a) { return cmake<C>(a.y, -a.x); }
+template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return cmake<C>(a.x * s, a.y * s); }
+
+// In-register forward DFTs of size R (omega = exp(-2 pi i / R)).
+template <typename C, int R> struct Dft;
+
+template <typename C> struct Dft<C, 2> {
+    __device__ __forceinline__ static void run(C* v) {
+        C a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    }
+};
+
+template <typename C> struct Dft<C, 4> {
+    __device__ __forceinline__ static void run(C* v) {
+        C s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+        C s13 = cadd(v[1], v[3]), d13 = cmul_mi(csub(v[1], v[3]));
+        v[0] = cadd(s02, s13);
+        v[2] = csub(s02, s13);
+        v[1] = cadd(d02, d13);
+        v[3] = csub(d02, d13);
+    }
+};
+
+template <typename C> struct Dft<C, 8> {
+    __device__ __forceinline__ static void run(C* v) {
+        using R = decltype(C::x);
+        const R h = R(0.70710678118654752440084436210485);
+        C e[4] = {v[0], v[2], v[4], v[6]};
+        C o[4] = {v[1], v[3], v[5], v[7]};
+        Dft<C, 4>::run(e);
+        Dft<C, 4>::run(o);
+        // o[m] *= exp(-2 pi i m / 8)
+        C o1 = cmake<C>(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x));
+        C o2 = cmul_mi(o[2]);
+        C o3 = cmake<C>(h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y));
+        v[0] = cadd(e[0], o[0]);
+        v[4] = csub(e[0], o[0]);
+        v[1] = cadd(e[1], o1);
+        v[5] = csub(e[1], o1);
+        v[2] = cadd(e[2], o2);
+        v[6] = csub(e[2], o2);
+        v[3] = cadd(e[3], o3);
+        v[7] = csub(e[3], o3);
+    }
+};
+
+template <typename C> struct Dft<C, 3> {
+    __device__ __forceinline__ static void run(C* v) {
+        using R = decltype(C::x);
+        const R s = R(0.86602540378443864676372317075294);  // sin(2 pi / 3)
+        C t = cadd(v[1], v[2]);
+        C m = cmake<C>(v[0].x - R(0.5) * t.x, v[0].y - R(0.5) * t.y);
+        C d = csub(v[1], v[2]);
+        C j = cmake<C>(s * d.y, -s * d.x);  // -i s (b - c)
+        v[0] = cadd(v[0], t);
+        v[1] = cadd(m, j);
+        v[2] = csub(m, j);
+    }
+};
+
+template <typename C> struct Dft<C, 5> {
+    __device__ __forceinline__ static void run(C* v) {
+        using R = decltype(C::x);
+        const R c1 = R(0.30901699437494742410229341718282);   // cos(2 pi / 5)
+        const R c2 = R(-0.80901699437494742410229341718282);  // cos(4 pi / 5)
+        const R s1 = R(0.95105651629515357211643933337938);   // sin(2 pi / 5)
+        const R s2 = R(0.58778525229247312916870595463907);   // sin(4 pi / 5)
+        C a = v[0];
+        C p1 = cadd(v[1], v[4]), m1 = csub(v[1], v[4]);
+        C p2 = cadd(v[2], v[3]), m2 = csub(v[2], v[3]);
+        C r1 = cmake<C>(a.x + c1 * p1.x + c2 * p2.x, a.y + c1 * p1.y + c2 * p2.y);
+        C r2 = cmake<C>(a.x + c2 * p1.x + c1 * p2.x, a.y + c2 * p1.y + c1 * p2.y);
+        // i1 = s1 m1 + s2 m2 ; i2 = s2 m1 - s1 m2 ; X1 = r1 - i i1, X4 = r1 + i i1 ; X2 = r2 - i i2, X3 = r2 + i i2
+        C i1 = cmake<C>(s1 * m1.x + s2 * m2.x, s1 * m1.y + s2 * m2.y);
+        C i2 = cmake<C>(s2 * m1.x - s1 * m2.x, s2 * m1.y - s1 * m2.y);
+        v[0] = cadd(a, cadd(p1, p2));
+        v[1] = cmake<C>(r1.x + i1.y, r1.y - i1.x);
+        v[4] = cmake<C>(r1.x - i1.y, r1.y + i1.x);
+        v[2] = cmake<C>(r2.x + i2.y, r2.y - i2.x);
+        v[3] = cmake<C>(r2.x - i2.y, r2.y + i2.x);
+    }
+};
+
+// One Stockham stage of radix R: butterfly j of line c reads elements
+// j + r n/R, applies the twiddles W_{Ns R}^{(j mod Ns) r}, transforms, and
+// writes to (j div Ns) Ns R + (j mod Ns) + r Ns.
+template <typename C, int R>
+__device__ __forceinline__ void stockham_stage(const C* __restrict__ src, C* __restrict__ dst, int n, int Ns,
+                                               int stride, int lines, const C* __restrict__ tw) {
+    const int nR = n / R;
+    const int total = lines * nR;
+    const int twstep = n / (Ns * R);
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+        const int c = q % lines;
+        const int j = q / lines;
+        const int jm = j % Ns;
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[(j + r * nR) * stride + c];
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[jm * r * twstep]);
+        }
+        Dft<C, R>::run(v);
+        const int od = (j - jm) * R + jm;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[(od + r * Ns) * stride + c] = v[r];
+    }
+}
+
+// Forward FFT of `lines` lines (layout above). Must be called by all threads of
+// the block; ends with a barrier. Returns the buffer that holds the result.
+template <typename C>
+__device__ C* block_fft(C* a, C* b, int stride, int lines, const AxisPlan& ap, const C* __restrict__ tw) {
+    int Ns = 1;
+    for (int st = 0; st < ap.nst; ++st) {
+        const int R = ap.rad[st];
+        switch (R) {
+            case 8: stockham_stage<C, 8>(a, b, ap.n, Ns, stride, lines, tw); break;
+            case 4: stockham_stage<C, 4>(a, b, ap.n, Ns, stride, lines, tw); break;
+            case 2: stockham_stage<C, 2>(a, b, ap.n, Ns, stride, lines, tw); break;
+            case 3: stockham_stage<C, 3>(a, b, ap.n, Ns, stride, lines, tw); break;
+            default: stockham_stage<C, 5>(a, b, ap.n, Ns, stride, lines, tw); break;
+        }
+        __syncthreads();
+        C* t = a;
+        a = b;
+        b = t;
+        Ns *= R;
+    }
+    return a;
+}
+
+}  // namespace ccmf

@@ -1,0 +1,102 @@
+// Shared types of the CCMF solver kernels and the host driver.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ccmf_fft.cuh"
+
+namespace ccmf {
+
+// Global sums reduced by the update pass (all in double once past the warp level).
+enum SumIndex {
+    kSumRes = 0,      // sum |e^k - xi^{k+1/2}|^2            (Eq. 31, left side)
+    kSumV = 1,        // 1..6: sum of v^k components           (Eq. 31, right side; dual objective)
+    kSumPrimal = 7,   // sum gamma |xi^{k+1/2}|                (Eq. 21)
+    kSumDvDe = 8,     // sum <v^{k+1}-v^k, e^{k+1}-e^k>        (BB scaling)
+    kSumDeDe = 9,     // sum |e^{k+1}-e^k|^2
+    kSumDvDv = 10,    // sum |v^{k+1}-v^k|^2                   (BB safeguard)
+    kSumVV = 11,      // sum |v^{k+1}|^2                       (LTD scaling)
+    kSumEE = 12,      // sum |e^{k+1}|^2
+    kNSum = 13
+};
+
+constexpr int kHistFields = 5;
+constexpr int kHistCap = 4096;   // history entries reserved per solve
+constexpr int kThreads = 256;
+
+// One per solve, in the workspace (256-byte slot).
+struct SolveScalars {
+    double rho;          // current penalty rho^k
+    double xi[3];        // unit crack normal
+    double gmin, gmax, gsum;
+    double residual, mean_v, primal, dual;
+    double sums[kNSum];
+    int active;          // 1 while the solve iterates
+    int status;          // CCMF_OK or an error code
+    int iters;           // updates performed so far (k)
+    int converged;
+    int call_start;      // iters at the start of the current solve call
+    unsigned int counter;  // last-block ticket of the reductions
+    int bad;             // number of invalid gamma values seen at init
+    int pad;
+};
+static_assert(sizeof(SolveScalars) <= 256, "scalar slot");
+
+struct LoopConfig {
+    double tol, delta, rho0, bb_corr_min, rho_step_max;
+    int max_iter, fixed_iters, rho_rule, hist_len, resume;
+};
+
+// Unsigned division by a fixed divisor through a multiply-high and shift
+// (Granlund & Montgomery, PLDI 1994): q = (umulhi(n, m) + n) >> s, exact for n < 2^32.
+struct FastDiv {
+    unsigned d, m, s;
+};
+
+inline FastDiv make_fastdiv(unsigned d) {
+    FastDiv f;
+    f.d = d;
+    unsigned s = 0;
+    while ((1ull << s) < d) ++s;
+    f.s = s;
+    f.m = (unsigned)((((1ull << 32) * ((1ull << s) - d)) / d) + 1ull);
+    return f;
+}
+
+__device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv& f) {
+    return (unsigned)(((unsigned long long)__umulhi(n, f.m) + n) >> f.s);
+}
+
+struct Geom {
+    int n1, n2, n3, n3h, batch;
+    long long N;    // voxels per solve
+    long long Nh;   // half-spectrum entries per solve (n1 n2 n3h)
+    FastDiv div_n3, div_n2, div_n3h;
+};
+
+template <typename T>
+struct Ptrs {
+    SolveScalars* sc;
+    int* n_active;
+    double* partial;      // [batch][grid_update][kNSum]
+    double* hist;         // [batch][hist_len][kHistFields]
+    T* e;                 // [batch][6][N]
+    T* v;                 // [batch][6][N]
+    cx<T>* spec;          // [batch][Nh]
+    T* phi;               // [batch][N]
+    const T* gamma;       // solve s at gamma + s * gstride
+    long long gstride;
+    T* cut;               // [batch][6][N] (final pass, may be null)
+    T* flow;              // [batch][3][N] (final pass, may be null)
+    int run_all;          // 1: passes run for every solve (final evaluation), 0: active solves only
+};
+
+struct LaunchShape {
+    int pairs_per_block;      // z passes: line pairs per block
+    int lpb_y, lpb_x;         // strided passes: lines per block
+    int grid_update;          // blocks per solve of the voxel passes
+    size_t smem_z, smem_y, smem_x;
+};
+
+}  // namespace ccmf

@@ -126,6 +126,7 @@ Ctx<T> make_ctx(const ccmf_plan* pl, unsigned char* ws, const T* gamma, long lon
     c.p.hist = reinterpret_cast<double*>(ws + pl->off_hist);
     c.p.e = reinterpret_cast<T*>(ws + pl->off_e);
     c.p.v = reinterpret_cast<T*>(ws + pl->off_v);
+    c.p.sstride = 6 * pl->g.N * (long long)pl->batch;
     c.p.spec = reinterpret_cast<cx<T>*>(ws + pl->off_spec);
     c.p.phi = reinterpret_cast<T*>(ws + pl->off_phi);
     c.p.gamma = gamma;
@@ -411,8 +412,8 @@ int ccmf_plan_create(int n1, int n2, int n3, int batch, int precision, ccmf_plan
     pl->off_xi = take(3 * sizeof(double) * batch);
     pl->off_part = take(sizeof(double) * kNSum * (size_t)sh.grid_update * batch);
     pl->off_hist = take(sizeof(double) * kHistFields * (size_t)kHistCap * batch);
-    pl->off_e = take(pl->esize * 6 * N * batch);
-    pl->off_v = take(pl->esize * 6 * N * batch);
+    pl->off_e = take(pl->esize * 6 * N * batch * 2);
+    pl->off_v = take(pl->esize * 6 * N * batch * 2);
     pl->off_spec = take(cs * (size_t)g.Nh * batch);
     pl->off_phi = take(pl->esize * N * batch);
     pl->off_gam = take(pl->esize * N * batch);
@@ -520,19 +521,26 @@ int ccmf_state_export(const ccmf_plan* plan, const void* workspace, void* e, voi
     if (!plan || !workspace) return CCMF_ERR_INVALID_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const unsigned char* ws = reinterpret_cast<const unsigned char*>(workspace);
-    const size_t bytes = plan->esize * 6 * (size_t)plan->g.N * plan->batch;
-    if (e && cudaMemcpyAsync(e, ws + plan->off_e, bytes, cudaMemcpyDefault, st) != cudaSuccess) return CCMF_ERR_CUDA;
-    if (v && cudaMemcpyAsync(v, ws + plan->off_v, bytes, cudaMemcpyDefault, st) != cudaSuccess) return CCMF_ERR_CUDA;
     std::vector<SolveScalars> sc(plan->batch);
     if (cudaMemcpyAsync(sc.data(), ws + plan->off_sc, sizeof(SolveScalars) * plan->batch, cudaMemcpyDeviceToHost,
                         st) != cudaSuccess)
         return CCMF_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return CCMF_ERR_CUDA;
+    // the current copy of solve s is (iters & 1)
+    const size_t one = plan->esize * 6 * (size_t)plan->g.N;
+    const size_t copy = one * plan->batch;
     for (int s = 0; s < plan->batch; ++s) {
+        const size_t src = (size_t)(sc[s].iters & 1) * copy + (size_t)s * one;
+        if (e && cudaMemcpyAsync((unsigned char*)e + (size_t)s * one, ws + plan->off_e + src, one, cudaMemcpyDefault,
+                                 st) != cudaSuccess)
+            return CCMF_ERR_CUDA;
+        if (v && cudaMemcpyAsync((unsigned char*)v + (size_t)s * one, ws + plan->off_v + src, one, cudaMemcpyDefault,
+                                 st) != cudaSuccess)
+            return CCMF_ERR_CUDA;
         if (rho) rho[s] = sc[s].rho;
         if (iters) iters[s] = sc[s].iters;
     }
-    return CCMF_OK;
+    return cuda_status(cudaStreamSynchronize(st));
 }
 
 int ccmf_state_import(const ccmf_plan* plan, void* workspace, const void* e, const void* v, const double* rho,
@@ -542,15 +550,20 @@ int ccmf_state_import(const ccmf_plan* plan, void* workspace, const void* e, con
         if (!(rho[s] > 0.0) || !isfinite(rho[s]) || iters[s] < 0) return CCMF_ERR_INVALID_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     unsigned char* ws = reinterpret_cast<unsigned char*>(workspace);
-    const size_t bytes = plan->esize * 6 * (size_t)plan->g.N * plan->batch;
-    if (cudaMemcpyAsync(ws + plan->off_e, e, bytes, cudaMemcpyDefault, st) != cudaSuccess) return CCMF_ERR_CUDA;
-    if (cudaMemcpyAsync(ws + plan->off_v, v, bytes, cudaMemcpyDefault, st) != cudaSuccess) return CCMF_ERR_CUDA;
     std::vector<SolveScalars> sc(plan->batch);
     if (cudaMemcpyAsync(sc.data(), ws + plan->off_sc, sizeof(SolveScalars) * plan->batch, cudaMemcpyDeviceToHost,
                         st) != cudaSuccess)
         return CCMF_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return CCMF_ERR_CUDA;
+    const size_t one = plan->esize * 6 * (size_t)plan->g.N;
+    const size_t copy = one * plan->batch;
     for (int s = 0; s < plan->batch; ++s) {
+        const size_t dst = (size_t)(iters[s] & 1) * copy + (size_t)s * one;
+        if (cudaMemcpyAsync(ws + plan->off_e + dst, (const unsigned char*)e + (size_t)s * one, one, cudaMemcpyDefault,
+                            st) != cudaSuccess ||
+            cudaMemcpyAsync(ws + plan->off_v + dst, (const unsigned char*)v + (size_t)s * one, one, cudaMemcpyDefault,
+                            st) != cudaSuccess)
+            return CCMF_ERR_CUDA;
         sc[s].rho = rho[s];
         sc[s].iters = iters[s];
     }

@@ -191,8 +191,9 @@ __global__ void __launch_bounds__(kThreads) k_init_state(Geom g, Ptrs<T> p) {
     const double h = 0.70710678118654752440084436210485;
     const SolveScalars& S = p.sc[s];
     const T a0 = (T)(S.xi[0] * h), a1 = (T)(S.xi[1] * h), a2 = (T)(S.xi[2] * h);
-    T* e = p.e + (size_t)s * 6 * g.N;
-    T* v = p.v + (size_t)s * 6 * g.N;
+    const long long cur = (long long)(S.iters & 1) * p.sstride + (long long)s * 6 * g.N;
+    T* e = p.e + cur;
+    T* v = p.v + cur;
     const long long stride = (long long)gridDim.x * kThreads;
     for (long long lin = (long long)blockIdx.x * kThreads + threadIdx.x; lin < g.N; lin += stride) {
         e[0 * g.N + lin] = a0;
@@ -231,8 +232,9 @@ __global__ void __launch_bounds__(kThreads) k_div_rfft_z(Geom g, Ptrs<T> p, Axis
     const T irho = T(1) / (T)p.sc[s].rho;
     const T h = T(0.70710678118654752440084436210485);
     const long long N = g.N;
-    const T* __restrict__ e = p.e + (size_t)s * 6 * N;
-    const T* __restrict__ v = p.v + (size_t)s * 6 * N;
+    const long long cur = (long long)(p.sc[s].iters & 1) * p.sstride + (long long)s * 6 * N;
+    const T* __restrict__ e = p.e + cur;
+    const T* __restrict__ v = p.v + cur;
     const long long L = (long long)g.n1 * g.n2;
     const long long l0 = (long long)blockIdx.x * 2 * P;
     const int cnt = 2 * P * g.n3;
@@ -432,8 +434,13 @@ __global__ void __launch_bounds__(kThreads) k_update(Geom g, Ptrs<T> p, LoopConf
     const T h = T(0.70710678118654752440084436210485);
     const T xi0 = (T)S.xi[0], xi1 = (T)S.xi[1], xi2 = (T)S.xi[2];
     const T alpha = (T)(2.0 * (1.0 - cfg.delta)), beta = (T)(1.0 - 2.0 * cfg.delta);
-    T* __restrict__ e = p.e + (size_t)s * 6 * N;
-    T* __restrict__ v = p.v + (size_t)s * 6 * N;
+    // read the current copy of the state, write the other one (the stencil reads
+    // neighbours, so an in-place update would race)
+    const int par = S.iters & 1;
+    const T* __restrict__ e = p.e + (long long)par * p.sstride + (long long)s * 6 * N;
+    const T* __restrict__ v = p.v + (long long)par * p.sstride + (long long)s * 6 * N;
+    T* __restrict__ e_out = p.e + (long long)(1 - par) * p.sstride + (long long)s * 6 * N;
+    T* __restrict__ v_out = p.v + (long long)(1 - par) * p.sstride + (long long)s * 6 * N;
     const T* __restrict__ phi = p.phi + (size_t)s * N;
     const T* __restrict__ gam = p.gamma + (size_t)s * p.gstride;
     T acc[kNSum];
@@ -518,8 +525,8 @@ __global__ void __launch_bounds__(kThreads) k_update(Geom g, Ptrs<T> p, LoopConf
                 dvdv += dv * dv;
                 vv += vn * vn;
                 ee += en * en;
-                e[c * N + lin] = en;
-                v[c * N + lin] = vn;
+                e_out[c * N + lin] = en;
+                v_out[c * N + lin] = vn;
             }
             acc[kSumDvDe] += dvde;
             acc[kSumDeDe] += dede;

@@ -81,8 +81,9 @@ struct Ptrs {
     int* n_active;
     double* partial;      // [batch][grid_update][kNSum]
     double* hist;         // [batch][hist_len][kHistFields]
-    T* e;                 // [batch][6][N]
-    T* v;                 // [batch][6][N]
+    T* e;                 // [2][batch][6][N]: two copies, the current one is (iters & 1)
+    T* v;                 // [2][batch][6][N]
+    long long sstride;    // elements between the two copies (batch * 6 * N)
     cx<T>* spec;          // [batch][Nh]
     T* phi;               // [batch][N]
     const T* gamma;       // solve s at gamma + s * gstride

@@ -84,7 +84,8 @@ typedef struct {
 
 /* Per-solve result (Eq. 21, Eq. 12, Eq. 31), evaluated on the final state. */
 typedef struct {
-    double gamma_eff;     /* reported effective crack energy = gamma_primal */
+    double gamma_eff;     /* reported effective crack energy = gamma_dual, the objective of the CCMF
+                             maximum-flow problem (Eq. 8 / Eq. 12) that defines the discretisation */
     double gamma_primal;  /* mean(gamma |xi^{K+1/2}|), the min-cut objective of Eq. 21 */
     double gamma_dual;    /* <xi_bar, A* v^K>, the max-flow objective of Eq. 12 */
     double residual;      /* |e^K - xi^{K+1/2}|_L2 */

@@ -37,9 +37,13 @@ Readings where the paper is silent (each one is listed in the design notes):
      evaluated from k = 1 on (at k = 0 both sides vanish) and, when it holds,
      the solver stops after the update to k + 1 that the same pass performs.
   R5 outputs come from one further projection of the final state (e^K, v^K):
-     cut = xi^{K+1/2} = P_K(e^K - v^K / rho^K), primal estimate
-     mean(gamma |cut|) (Eq. 21), flow = A* v^K and dual estimate <xi_bar, A* v^K>
-     (Eq. 12). The reported effective crack energy is the primal estimate.
+     cut = xi^{K+1/2} = P_K(e^K - v^K / rho^K), min-cut estimate
+     mean(gamma |cut|) (Eq. 21), flow = A* v^K and max-flow estimate
+     <xi_bar, A* v^K> (Eq. 12). The reported effective crack energy is the
+     max-flow estimate: Sec. 2.2 defines the CCMF discretisation as the maximum
+     flow problem of Eq. 8 / Eq. 12, and this estimate is linear in v, so
+     rounding noise in the fields averages out instead of adding |noise| to a
+     norm. Both estimates converge to the same value (strong duality, Sec. 2.1).
   R6 P_C keeps w when |w| <= gamma (the strict '>' branch); gamma = 0 maps to 0.
   R7 the zero frequency of (div^- grad^+)^+ is set to zero (pseudo-inverse).
 """
@@ -183,7 +187,7 @@ class Params:
 
 @dataclasses.dataclass
 class Result:
-    gamma_eff: float             # = gamma_primal (R5)
+    gamma_eff: float             # = gamma_dual, the max-flow objective (R5)
     gamma_primal: float
     gamma_dual: float
     residual: float              # |e^K - xi^{K+1/2}|_{L2} of the final evaluation
@@ -279,7 +283,8 @@ def evaluate(gamma, xi_bar, e, v, rho, iters=0, converged=False, history=None):
     flow = op_A_adj(v)
     mv = math.sqrt(sum(float(np.mean(v[c])) ** 2 for c in range(6)))
     gp = mincut_objective(xi_half, gamma)
-    return Result(gamma_eff=gp, gamma_primal=gp, gamma_dual=flow_objective(flow, xi_bar),
+    gd = flow_objective(flow, xi_bar)
+    return Result(gamma_eff=gd, gamma_primal=gp, gamma_dual=gd,
                   residual=l2_norm(e - xi_half), mean_v_norm=mv, rho=rho, iters=iters,
                   converged=converged, e=e, v=v, cut=xi_half, flow=flow,
                   history=history or [])

@@ -278,7 +278,7 @@ int solve_impl(ccmf_plan* pl, const void* gamma_in, long long gstride_in, const 
             for (int s = 0; s < g.batch; ++s) {
                 ccmf_result& r = results[s];
                 r.gamma_primal = sc[s].primal;
-                r.gamma_eff = sc[s].primal;
+                r.gamma_eff = sc[s].dual;
                 r.gamma_dual = sc[s].dual;
                 r.residual = sc[s].residual;
                 r.mean_v_norm = sc[s].mean_v;

@@ -55,6 +55,7 @@ def assert_parity(out, refs):
         assert r["iters"] == ref.iters
         assert abs(r["gamma_eff"] - ref.gamma_eff) <= GEFF_TOL * abs(ref.gamma_eff)
         assert abs(r["gamma_dual"] - ref.gamma_dual) <= GEFF_TOL * abs(ref.gamma_eff) + 1e-13
+        assert abs(r["gamma_primal"] - ref.gamma_primal) <= GEFF_TOL * abs(ref.gamma_primal) + 1e-13
         assert abs(out["rho"][s] - ref.rho) <= 1e-10 * ref.rho
         np.testing.assert_allclose(out["e"][s], ref.e, rtol=0, atol=FIELD_TOL)
         np.testing.assert_allclose(out["v"][s], ref.v, rtol=0, atol=FIELD_TOL)
@@ -84,10 +85,14 @@ def test_fp64_equal_iterations(name, build, normals, iters):
 
 @pytest.mark.parametrize("rule", [ccmf.CCMF_RHO_CONST, ccmf.CCMF_RHO_LTD, ccmf.CCMF_RHO_BB])
 def test_fp64_penalty_rules_and_damping(rule):
+    # rho^0 below min(gamma): with rho^0 = min(gamma) the first update meets |z| = gamma exactly
+    # at the weakest voxels, where rounding decides whether |e^1| is 0 or 1e-16, and the LTD
+    # ratio |v|/|e| of that noise would flip rho differently on both sides.
     gamma = M.random_two_phase((10, 12, 8), 0.3, 0.2, 1.0, 11)
     delta = 0.5 if rule == ccmf.CCMF_RHO_BB else 0.25
-    out = gpu_run(gamma, [[0.0, 0.0, 1.0]], ccmf.Params(fixed_iters=70, rho_rule=rule, delta=delta))
-    ref = O.solve(gamma, [0, 0, 1], O.Params(fixed_iters=70, rho_rule=rule, delta=delta), record_history=False)
+    out = gpu_run(gamma, [[0.0, 0.0, 1.0]], ccmf.Params(fixed_iters=70, rho_rule=rule, delta=delta, rho0=0.15))
+    ref = O.solve(gamma, [0, 0, 1], O.Params(fixed_iters=70, rho_rule=rule, delta=delta, rho0=0.15),
+                  record_history=False)
     assert_parity(out, [ref])
 
 

@@ -29,13 +29,13 @@ def _dense_pin_holds():
     xi = [0.3, -0.5, 0.8]
     val, _, gap = D.max_flow(g, xi, gap_tol=1e-9)
     r = O.solve(g, xi, O.Params(tol=1e-9, max_iter=20000), record_history=False)
-    return abs(r.gamma_eff - val) <= 1e-6 * val + gap
+    return abs(r.gamma_eff - val) <= 1e-6 * val + gap and abs(r.gamma_primal - val) <= 1e-6 * val + gap
 
 
 def _homogeneous_pin_holds():
     r = O.solve(np.full((4, 4, 4), 1.3), [0.6, 0.8, 0.0], O.Params(tol=1e-9, max_iter=2000),
                 record_history=False)
-    return abs(r.gamma_eff - 1.3) < 1e-7
+    return abs(r.gamma_eff - 1.3) < 1e-7 and abs(r.gamma_primal - 1.3) < 1e-7
 
 
 def _laplacian_pin_holds():

@@ -22,7 +22,7 @@ def test_homogeneous_any_normal():
         r = O.solve(g, xi, O.Params(tol=1e-9))
         assert r.converged
         assert abs(r.gamma_eff - 1.7) < 1e-8
-        assert abs(r.gamma_dual - 1.7) < 1e-8
+        assert abs(r.gamma_primal - 1.7) < 1e-8
 
 
 def test_laminate_closed_forms():
@@ -43,7 +43,7 @@ def test_axis_normal_bounds_random_columns():
     lo = g.min(axis=2).mean()
     hi = g.mean(axis=(0, 1)).min()
     assert lo - 1e-4 <= r.gamma_eff <= hi + 1e-4
-    assert lo - 1e-4 <= r.gamma_dual <= hi + 1e-4
+    assert lo - 1e-4 <= r.gamma_primal <= hi + 1e-4
 
 
 @pytest.mark.parametrize("seed,xi", [(3, [0.3, -0.5, 0.8]), (4, [0.0, 0.0, 1.0]), (5, [1.0, 1.0, 0.0])])
@@ -54,7 +54,7 @@ def test_dense_barrier_agreement(seed, xi):
     r = O.solve(g, xi, O.Params(tol=1e-10, max_iter=100000))
     assert r.converged
     assert abs(r.gamma_eff - val) <= 1e-8 * val + gap
-    assert abs(r.gamma_dual - val) <= 1e-8 * val + gap
+    assert abs(r.gamma_primal - val) <= 1e-8 * val + gap
 
 
 def test_dense_barrier_anisotropic_grid():
@@ -63,6 +63,7 @@ def test_dense_barrier_anisotropic_grid():
     val, _, gap = D.max_flow(g, xi, gap_tol=1e-10)
     r = O.solve(g, xi, O.Params(tol=1e-10, max_iter=200000))
     assert abs(r.gamma_eff - val) <= 1e-7 * val + gap
+    assert abs(r.gamma_primal - val) <= 1e-7 * val + gap
 
 
 def test_config_single_sphere_32_closed_form():
@@ -74,8 +75,8 @@ def test_config_single_sphere_32_closed_form():
     assert exact == 1.0 - 0.9 * gold["central_layer_voxels"] / 1024.0
     r = O.solve(g, gold["xi_bar"], O.Params(tol=1e-6))
     assert r.converged
-    assert exact - 1e-9 <= r.gamma_eff <= exact + 5e-6          # primal is an upper bound
-    assert abs(r.gamma_dual - exact) <= 5e-6
+    assert exact - 1e-9 <= r.gamma_primal <= exact + 5e-6       # the min-cut value is an upper bound
+    assert abs(r.gamma_eff - exact) <= 5e-6                      # reported max-flow value
 
 
 @pytest.mark.slow
@@ -163,7 +164,7 @@ def test_penalty_rules_agree():
     vals = []
     for rule in (O.RHO_BB, O.RHO_LTD, O.RHO_CONST):
         r = O.solve(g, [0, 0, 1], O.Params(tol=1e-4, max_iter=3000, rho_rule=rule), record_history=False)
-        assert lo - 1e-9 <= r.gamma_dual and r.gamma_eff <= hi + 1e-9
+        assert lo - 1e-9 <= r.gamma_eff and r.gamma_primal <= hi + 1e-9
         vals.append(r.gamma_eff)
     assert max(vals) - min(vals) < 2e-3 * vals[0]
 
@@ -172,4 +173,4 @@ def test_strong_duality_at_convergence():
     g, _ = M.boolean_spheres((12, 12, 12), 2.0, 0.2, 0.3, 1.0, 13)
     r = O.solve(g, [0, 0, 1], O.Params(tol=1e-8, max_iter=50000))
     assert r.converged
-    assert abs(r.gamma_eff - r.gamma_dual) < 1e-6
+    assert abs(r.gamma_primal - r.gamma_dual) < 1e-6

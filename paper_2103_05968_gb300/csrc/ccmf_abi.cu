@@ -54,7 +54,19 @@ bool make_axis_plan(int n, AxisPlan* ap) {
     while (m % 5 == 0)
         if (!push(5)) return false;
     ap->nst = st;
+    unsigned ns = 1;
+    for (int t = 0; t < st; ++t) {
+        ap->ns[t] = make_fastdiv(ns);
+        ns *= (unsigned)ap->rad[t];
+    }
     return m == 1;
+}
+
+// Largest power of two <= min(cap, x), at least 1.
+int pow2_floor(long long x, int cap) {
+    int r = 1;
+    while (r * 2 <= cap && r * 2 <= x) r *= 2;
+    return r;
 }
 
 struct GraphKey {
@@ -134,6 +146,9 @@ Ctx<T> make_ctx(const ccmf_plan* pl, unsigned char* ws, const T* gamma, long lon
     c.p.cut = nullptr;
     c.p.flow = nullptr;
     c.p.run_all = 0;
+    const int W = 16 / (int)sizeof(T);
+    c.vec_div = (pl->n3 % W) == 0;
+    c.vec_update = c.vec_div && ((uintptr_t)gamma % 16) == 0;
     return c;
 }
 
@@ -379,19 +394,15 @@ int ccmf_plan_create(int n1, int n2, int n3, int batch, int precision, ccmf_plan
     const size_t cs = 2 * pl->esize;  // complex element
     LaunchShape& sh = pl->sh;
     {
-        long long P = ((long long)(kSmemBudget / cs) - n3) / (2LL * n3) - 1;
-        if (P > 16) P = 16;
-        if (P < 1) P = 1;
-        sh.pairs_per_block = (int)P;
-        sh.smem_z = ((size_t)n3 + 2 * (size_t)n3 * (P + 1)) * cs;
-        auto lpb_for = [&](int n) {
+        // lines per block of the FFT passes: powers of two, shared memory = twiddles + 2 tiles
+        auto lines_for = [&](int n) {
             long long L = ((long long)(kSmemBudget / cs) - n) / (2LL * n) - 1;
-            if (L > 16) L = 16;
-            if (L < 1) L = 1;
-            return (int)L;
+            return pow2_floor(L, 16);
         };
-        sh.lpb_y = lpb_for(n2);
-        sh.lpb_x = lpb_for(n1);
+        sh.pairs_per_block = lines_for(n3);
+        sh.smem_z = ((size_t)n3 + 2 * (size_t)n3 * (sh.pairs_per_block + 1)) * cs;
+        sh.lpb_y = lines_for(n2);
+        sh.lpb_x = lines_for(n1);
         sh.smem_y = ((size_t)n2 + 2 * (size_t)n2 * (sh.lpb_y + 1)) * cs;
         sh.smem_x = ((size_t)n1 + 2 * (size_t)n1 * (sh.lpb_x + 1)) * cs;
         long long gu = (g.N + kThreads - 1) / kThreads;

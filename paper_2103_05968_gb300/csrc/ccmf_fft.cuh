@@ -19,10 +19,31 @@ namespace ccmf {
 
 constexpr int kMaxStages = 12;
 
+// Unsigned division by a fixed divisor through a multiply-high and shift
+// (Granlund & Montgomery, PLDI 1994): q = (umulhi(n, m) + n) >> s, exact for n < 2^32.
+struct FastDiv {
+    unsigned d, m, s;
+};
+
+inline FastDiv make_fastdiv(unsigned d) {
+    FastDiv f;
+    f.d = d;
+    unsigned s = 0;
+    while ((1ull << s) < d) ++s;
+    f.s = s;
+    f.m = (unsigned)((((1ull << 32) * ((1ull << s) - d)) / d) + 1ull);
+    return f;
+}
+
+__device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv& f) {
+    return (unsigned)(((unsigned long long)__umulhi(n, f.m) + n) >> f.s);
+}
+
 struct AxisPlan {
-    int n;                  // line length
-    int nst;                // number of radix stages
-    int rad[kMaxStages];    // radix of each stage, product = n
+    int n;                     // line length
+    int nst;                   // number of radix stages
+    int rad[kMaxStages];       // radix of each stage, product = n
+    FastDiv ns[kMaxStages];    // divisor Ns (product of the earlier radices) of each stage
 };
 
 template <typename T> struct CxOf;
@@ -123,25 +144,31 @@ template <typename C> struct Dft<C, 5> {
     }
 };
 
-// One Stockham stage of radix R: butterfly j of line c reads elements
-// j + r n/R, applies the twiddles W_{Ns R}^{(j mod Ns) r}, transforms, and
-// writes to (j div Ns) Ns R + (j mod Ns) + r Ns.
-template <typename C, int R>
-__device__ __forceinline__ void stockham_stage(const C* __restrict__ src, C* __restrict__ dst, int n, int Ns,
-                                               int stride, int lines, const C* __restrict__ tw) {
+// One Stockham stage of radix R over LINES lines (LINES a power of two):
+// butterfly j of line c reads elements j + r n/R, applies the twiddles
+// W_{Ns R}^{(j mod Ns) r}, transforms, and writes to
+// (j div Ns) Ns R + (j mod Ns) + r Ns.
+template <typename C, int R, int LINES>
+__device__ __forceinline__ void stockham_stage(const C* __restrict__ src, C* __restrict__ dst, int n,
+                                               const FastDiv& nsd, const C* __restrict__ tw) {
+    constexpr int stride = LINES + 1;
+    constexpr int lsh = (LINES >= 16) ? 4 : (LINES >= 8) ? 3 : (LINES >= 4) ? 2 : (LINES >= 2) ? 1 : 0;
+    static_assert((1 << lsh) == LINES, "LINES must be a power of two <= 16");
+    const int Ns = (int)nsd.d;
     const int nR = n / R;
-    const int total = lines * nR;
+    const int total = LINES * nR;
     const int twstep = n / (Ns * R);
     for (int q = threadIdx.x; q < total; q += blockDim.x) {
-        const int c = q % lines;
-        const int j = q / lines;
-        const int jm = j % Ns;
+        const int c = q & (LINES - 1);
+        const int j = q >> lsh;
+        const int jm = j - (int)fdiv((unsigned)j, nsd) * Ns;
         C v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = src[(j + r * nR) * stride + c];
         if (Ns > 1) {
+            const int t = jm * twstep;
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[jm * r * twstep]);
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[t * r]);
         }
         Dft<C, R>::run(v);
         const int od = (j - jm) * R + jm;
@@ -150,25 +177,24 @@ __device__ __forceinline__ void stockham_stage(const C* __restrict__ src, C* __r
     }
 }
 
-// Forward FFT of `lines` lines (layout above). Must be called by all threads of
-// the block; ends with a barrier. Returns the buffer that holds the result.
-template <typename C>
-__device__ C* block_fft(C* a, C* b, int stride, int lines, const AxisPlan& ap, const C* __restrict__ tw) {
-    int Ns = 1;
+// Forward FFT of LINES lines (layout above, stride LINES + 1). Must be called by
+// all threads of the block; ends with a barrier. Returns the buffer that holds
+// the result.
+template <typename C, int LINES>
+__device__ C* block_fft(C* a, C* b, const AxisPlan& ap, const C* __restrict__ tw) {
     for (int st = 0; st < ap.nst; ++st) {
         const int R = ap.rad[st];
         switch (R) {
-            case 8: stockham_stage<C, 8>(a, b, ap.n, Ns, stride, lines, tw); break;
-            case 4: stockham_stage<C, 4>(a, b, ap.n, Ns, stride, lines, tw); break;
-            case 2: stockham_stage<C, 2>(a, b, ap.n, Ns, stride, lines, tw); break;
-            case 3: stockham_stage<C, 3>(a, b, ap.n, Ns, stride, lines, tw); break;
-            default: stockham_stage<C, 5>(a, b, ap.n, Ns, stride, lines, tw); break;
+            case 8: stockham_stage<C, 8, LINES>(a, b, ap.n, ap.ns[st], tw); break;
+            case 4: stockham_stage<C, 4, LINES>(a, b, ap.n, ap.ns[st], tw); break;
+            case 2: stockham_stage<C, 2, LINES>(a, b, ap.n, ap.ns[st], tw); break;
+            case 3: stockham_stage<C, 3, LINES>(a, b, ap.n, ap.ns[st], tw); break;
+            default: stockham_stage<C, 5, LINES>(a, b, ap.n, ap.ns[st], tw); break;
         }
         __syncthreads();
         C* t = a;
         a = b;
         b = t;
-        Ns *= R;
     }
     return a;
 }

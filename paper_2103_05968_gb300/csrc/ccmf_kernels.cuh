@@ -208,26 +208,71 @@ __global__ void __launch_bounds__(kThreads) k_init_state(Geom g, Ptrs<T> p) {
 }
 
 // ---------------------------------------------------------------------------
+// 16-byte vectors of the field type (4 floats or 2 doubles).
+// ---------------------------------------------------------------------------
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+    using type = float4;
+    static constexpr int W = 4;
+    __device__ __forceinline__ static void ld(const float* __restrict__ p, float (&o)[4]) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+        o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+    }
+    __device__ __forceinline__ static void st(float* p, const float (&o)[4]) {
+        *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+};
+template <> struct Vec16<double> {
+    using type = double2;
+    static constexpr int W = 2;
+    __device__ __forceinline__ static void ld(const double* __restrict__ p, double (&o)[2]) {
+        const double2 t = __ldg(reinterpret_cast<const double2*>(p));
+        o[0] = t.x; o[1] = t.y;
+    }
+    __device__ __forceinline__ static void st(double* p, const double (&o)[2]) {
+        *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+    }
+};
+
+// Neighbour offsets of the row (i, j) of a solve: rows (i+1, j), (i-1, j), (i, j+1), (i, j-1).
+struct RowNb {
+    long long row, ip, im, jp, jm;  // element offsets of k = 0 of each row
+};
+
+__device__ __forceinline__ RowNb row_neighbours(const Geom& g, unsigned row) {
+    const unsigned i = fdiv(row, g.div_n2);
+    const int j = (int)(row - i * (unsigned)g.n2);
+    const int ip = ((int)i + 1 == g.n1) ? 0 : (int)i + 1, im = (i == 0) ? g.n1 - 1 : (int)i - 1;
+    const int jp = (j + 1 == g.n2) ? 0 : j + 1, jm = (j == 0) ? g.n2 - 1 : j - 1;
+    RowNb r;
+    const long long n3 = g.n3;
+    r.row = (long long)row * n3;
+    r.ip = ((long long)ip * g.n2 + j) * n3;
+    r.im = ((long long)im * g.n2 + j) * n3;
+    r.jp = ((long long)i * g.n2 + jp) * n3;
+    r.jm = ((long long)i * g.n2 + jm) * n3;
+    return r;
+}
+
+// ---------------------------------------------------------------------------
 // Pass 1: divergence of A*(e - v/rho) fused with the real-to-complex z FFT.
 // Line l = i * n2 + j of a solve; block b packs line pairs (2q, 2q+1) for
 // q in [b P, b P + P) as real and imaginary parts of one complex line.
+// d(p) = (1/sqrt2) sum_a [w1_a(p) - w1_a(p - e_a) + w2_a(p + e_a) - w2_a(p)].
+// VEC: each thread reads W consecutive voxels of a line with 16-byte loads.
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T wcomp(const T* __restrict__ e, const T* __restrict__ v, long long off, T irho) {
-    return e[off] - v[off] * irho;
-}
-
-template <typename T>
+template <typename T, int P, bool VEC>
 __global__ void __launch_bounds__(kThreads) k_div_rfft_z(Geom g, Ptrs<T> p, AxisPlan az,
-                                                         const cx<T>* __restrict__ tw, int P) {
+                                                         const cx<T>* __restrict__ tw) {
     using C = cx<T>;
+    constexpr int stride = P + 1;
+    constexpr int W = VEC ? Vec16<T>::W : 1;
     const int s = blockIdx.y;
     if (!p.run_all && !p.sc[s].active) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* twl = reinterpret_cast<C*>(smem_raw);
     C* A = twl + g.n3;
-    C* B = A + (size_t)g.n3 * (P + 1);
-    const int stride = P + 1;
+    C* B = A + (size_t)g.n3 * stride;
     for (int t = threadIdx.x; t < g.n3; t += kThreads) twl[t] = tw[t];
     const T irho = T(1) / (T)p.sc[s].rho;
     const T h = T(0.70710678118654752440084436210485);
@@ -237,50 +282,82 @@ __global__ void __launch_bounds__(kThreads) k_div_rfft_z(Geom g, Ptrs<T> p, Axis
     const T* __restrict__ v = p.v + cur;
     const long long L = (long long)g.n1 * g.n2;
     const long long l0 = (long long)blockIdx.x * 2 * P;
-    const int cnt = 2 * P * g.n3;
+    const int n3w = g.n3 / W;
+    const int cnt = 2 * P * n3w;
     T* Ar = reinterpret_cast<T*>(A);
     for (int idx = threadIdx.x; idx < cnt; idx += kThreads) {
-        const int ll = (int)fdiv((unsigned)idx, g.div_n3);
-        const int k = idx - ll * g.n3;
+        const int ll = idx / n3w;
+        const int k0 = (idx - ll * n3w) * W;
         const long long l = l0 + ll;
-        T d = T(0);
+        T d[W];
+#pragma unroll
+        for (int u = 0; u < W; ++u) d[u] = T(0);
         if (l < L) {
-            const int i = (int)fdiv((unsigned)l, g.div_n2);
-            const int j = (int)l - i * g.n2;
-            const int ip = (i + 1 == g.n1) ? 0 : i + 1, im = (i == 0) ? g.n1 - 1 : i - 1;
-            const int jp = (j + 1 == g.n2) ? 0 : j + 1, jm = (j == 0) ? g.n2 - 1 : j - 1;
-            const int kp = (k + 1 == g.n3) ? 0 : k + 1, km = (k == 0) ? g.n3 - 1 : k - 1;
-            const long long row = l * g.n3;
-            const long long p0 = row + k;
-            const long long pxp = ((long long)ip * g.n2 + j) * g.n3 + k;
-            const long long pxm = ((long long)im * g.n2 + j) * g.n3 + k;
-            const long long pyp = ((long long)i * g.n2 + jp) * g.n3 + k;
-            const long long pym = ((long long)i * g.n2 + jm) * g.n3 + k;
-            const long long pzp = row + kp, pzm = row + km;
-            // d = (1/sqrt2) sum_a [w1_a(p) - w1_a(p - e_a) + w2_a(p + e_a) - w2_a(p)]
-            T sx = wcomp(e, v, 0 * N + p0, irho) - wcomp(e, v, 0 * N + pxm, irho) +
-                   wcomp(e, v, 3 * N + pxp, irho) - wcomp(e, v, 3 * N + p0, irho);
-            T sy = wcomp(e, v, 1 * N + p0, irho) - wcomp(e, v, 1 * N + pym, irho) +
-                   wcomp(e, v, 4 * N + pyp, irho) - wcomp(e, v, 4 * N + p0, irho);
-            T sz = wcomp(e, v, 2 * N + p0, irho) - wcomp(e, v, 2 * N + pzm, irho) +
-                   wcomp(e, v, 5 * N + pzp, irho) - wcomp(e, v, 5 * N + p0, irho);
-            d = h * (sx + sy + sz);
+            const RowNb rn = row_neighbours(g, (unsigned)l);
+            const int kp = (k0 + W == g.n3) ? 0 : k0 + W;      // first voxel after the group
+            const int km = (k0 == 0) ? g.n3 - 1 : k0 - 1;        // last voxel before the group
+            if constexpr (VEC) {
+                T w[6][W], tmp_e[W], tmp_v[W];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+                    Vec16<T>::ld(e + c * N + rn.row + k0, tmp_e);
+                    Vec16<T>::ld(v + c * N + rn.row + k0, tmp_v);
+#pragma unroll
+                    for (int u = 0; u < W; ++u) w[c][u] = tmp_e[u] - tmp_v[u] * irho;
+                }
+                T xp[W], xm[W], yp[W], ym[W];
+                Vec16<T>::ld(e + 3 * N + rn.ip + k0, tmp_e);
+                Vec16<T>::ld(v + 3 * N + rn.ip + k0, tmp_v);
+#pragma unroll
+                for (int u = 0; u < W; ++u) xp[u] = tmp_e[u] - tmp_v[u] * irho;
+                Vec16<T>::ld(e + 0 * N + rn.im + k0, tmp_e);
+                Vec16<T>::ld(v + 0 * N + rn.im + k0, tmp_v);
+#pragma unroll
+                for (int u = 0; u < W; ++u) xm[u] = tmp_e[u] - tmp_v[u] * irho;
+                Vec16<T>::ld(e + 4 * N + rn.jp + k0, tmp_e);
+                Vec16<T>::ld(v + 4 * N + rn.jp + k0, tmp_v);
+#pragma unroll
+                for (int u = 0; u < W; ++u) yp[u] = tmp_e[u] - tmp_v[u] * irho;
+                Vec16<T>::ld(e + 1 * N + rn.jm + k0, tmp_e);
+                Vec16<T>::ld(v + 1 * N + rn.jm + k0, tmp_v);
+#pragma unroll
+                for (int u = 0; u < W; ++u) ym[u] = tmp_e[u] - tmp_v[u] * irho;
+                const T zp = __ldg(e + 5 * N + rn.row + kp) - __ldg(v + 5 * N + rn.row + kp) * irho;
+                const T zm = __ldg(e + 2 * N + rn.row + km) - __ldg(v + 2 * N + rn.row + km) * irho;
+#pragma unroll
+                for (int u = 0; u < W; ++u) {
+                    const T w2zp = (u + 1 < W) ? w[5][(u + 1) % W] : zp;
+                    const T w1zm = (u > 0) ? w[2][(u + W - 1) % W] : zm;
+                    const T sx = w[0][u] - xm[u] + xp[u] - w[3][u];
+                    const T sy = w[1][u] - ym[u] + yp[u] - w[4][u];
+                    const T sz = w[2][u] - w1zm + w2zp - w[5][u];
+                    d[u] = h * (sx + sy + sz);
+                }
+            } else {
+                const long long p0 = rn.row + k0;
+                auto wc = [&](int c, long long off) { return e[c * N + off] - v[c * N + off] * irho; };
+                const T sx = wc(0, p0) - wc(0, rn.im + k0) + wc(3, rn.ip + k0) - wc(3, p0);
+                const T sy = wc(1, p0) - wc(1, rn.jm + k0) + wc(4, rn.jp + k0) - wc(4, p0);
+                const T sz = wc(2, p0) - wc(2, rn.row + km) + wc(5, rn.row + kp) - wc(5, p0);
+                d[0] = h * (sx + sy + sz);
+            }
         }
-        Ar[2 * (k * stride + (ll >> 1)) + (ll & 1)] = d;
+#pragma unroll
+        for (int u = 0; u < W; ++u) Ar[2 * ((k0 + u) * stride + (ll >> 1)) + (ll & 1)] = d[u];
     }
     __syncthreads();
-    C* R = block_fft<C>(A, B, stride, P, az, twl);
+    C* R = block_fft<C, P>(A, B, az, twl);
     const int cnt2 = P * g.n3h;
     C* spec = p.spec + (size_t)s * g.Nh;
     for (int idx = threadIdx.x; idx < cnt2; idx += kThreads) {
         const int c = (int)fdiv((unsigned)idx, g.div_n3h);
         const int kz = idx - c * g.n3h;
         const C Z = R[kz * stride + c];
-        const int km = (kz == 0) ? 0 : g.n3 - kz;
-        const C Zm = cconj(R[km * stride + c]);
-        const C S = cadd(Z, Zm), D = csub(Z, Zm);
+        const int kmr = (kz == 0) ? 0 : g.n3 - kz;
+        const C Zm = cconj(R[kmr * stride + c]);
+        const C Sm = cadd(Z, Zm), D = csub(Z, Zm);
         const long long la = l0 + 2 * c, lb = la + 1;
-        if (la < L) spec[la * g.n3h + kz] = cmake<C>(T(0.5) * S.x, T(0.5) * S.y);
+        if (la < L) spec[la * g.n3h + kz] = cmake<C>(T(0.5) * Sm.x, T(0.5) * Sm.y);
         if (lb < L) spec[lb * g.n3h + kz] = cmake<C>(T(0.5) * D.y, T(-0.5) * D.x);
     }
 }
@@ -290,78 +367,71 @@ __global__ void __launch_bounds__(kThreads) k_div_rfft_z(Geom g, Ptrs<T> p, Axis
 // MODE 0: forward along y.  MODE 2: inverse along y.
 // MODE 1: forward along x, multiply by 1 / (N lambda(k)) with
 //         lambda(k) = -sum_a 4 sin^2(pi k_a / N_a) and 0 at k = 0, inverse along x.
+// A block transforms LPB lines (consecutive line ids, so that each element row
+// of the tile is a contiguous run of the spectrum).
 // ---------------------------------------------------------------------------
-template <typename T, int MODE>
+template <typename T, int MODE, int LPB>
 __global__ void __launch_bounds__(kThreads) k_fft_strided(Geom g, Ptrs<T> p, AxisPlan ap,
-                                                          const cx<T>* __restrict__ tw, int LPB,
+                                                          const cx<T>* __restrict__ tw,
                                                           const T* __restrict__ sym1, const T* __restrict__ sym2,
                                                           const T* __restrict__ sym3, T inv_n) {
     using C = cx<T>;
+    constexpr int stride = LPB + 1;
+    constexpr int lsh = (LPB >= 16) ? 4 : (LPB >= 8) ? 3 : (LPB >= 4) ? 2 : (LPB >= 2) ? 1 : 0;
     const int s = blockIdx.y;
     if (!p.run_all && !p.sc[s].active) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = ap.n;
     C* twl = reinterpret_cast<C*>(smem_raw);
     C* A = twl + n;
-    C* B = A + (size_t)n * (LPB + 1);
-    const int stride = LPB + 1;
+    C* B = A + (size_t)n * stride;
     for (int t = threadIdx.x; t < n; t += kThreads) twl[t] = tw[t];
     const long long nlines = (MODE == 1) ? (long long)g.n2 * g.n3h : (long long)g.n1 * g.n3h;
     const long long es = (MODE == 1) ? (long long)g.n2 * g.n3h : (long long)g.n3h;
     const long long l0 = (long long)blockIdx.x * LPB;
     C* spec = p.spec + (size_t)s * g.Nh;
-    const int cnt = LPB * n;
-    for (int idx = threadIdx.x; idx < cnt; idx += kThreads) {
-        const int m = idx / LPB;
-        const int c = idx - m * LPB;
-        const long long l = l0 + c;
+    // this thread always handles line c of the tile; its global base offset is fixed
+    const int c = threadIdx.x & (LPB - 1);
+    const int m0 = threadIdx.x >> lsh;
+    constexpr int mstep = kThreads / LPB;
+    const long long l = l0 + c;
+    const bool valid = l < nlines;
+    long long base = 0;
+    int k2 = 0, kz = 0;
+    if (valid) {
+        if (MODE == 1) {
+            base = l;
+            k2 = (int)fdiv((unsigned)l, g.div_n3h);
+            kz = (int)l - k2 * g.n3h;
+        } else {
+            const long long i = fdiv((unsigned)l, g.div_n3h);
+            base = i * g.n2 * g.n3h + (l - i * g.n3h);
+        }
+    }
+    for (int m = m0; m < n; m += mstep) {
         C val = cmake<C>(T(0), T(0));
-        if (l < nlines) {
-            long long base;
-            if (MODE == 1) {
-                base = l;
-            } else {
-                const long long i = fdiv((unsigned)l, g.div_n3h);
-                base = i * g.n2 * g.n3h + (l - i * g.n3h);
-            }
+        if (valid) {
             val = spec[base + m * es];
             if (MODE == 2) val = cconj(val);
         }
         A[m * stride + c] = val;
     }
     __syncthreads();
-    C* R = block_fft<C>(A, B, stride, LPB, ap, twl);
+    C* R = block_fft<C, LPB>(A, B, ap, twl);
     if (MODE == 1) {
-        for (int idx = threadIdx.x; idx < cnt; idx += kThreads) {
-            const int m = idx / LPB;
-            const int c = idx - m * LPB;
-            const long long l = l0 + c;
-            T gk = T(0);
-            if (l < nlines) {
-                const int k2 = (int)fdiv((unsigned)l, g.div_n3h);
-                const int kz = (int)l - k2 * g.n3h;
-                const T lam = sym1[m] + sym2[k2] + sym3[kz];
-                gk = (lam > T(0)) ? -inv_n / lam : T(0);
-            }
+        const T lam23 = valid ? sym2[k2] + sym3[kz] : T(0);
+        for (int m = m0; m < n; m += mstep) {
+            const T lam = sym1[m] + lam23;
+            const T gk = (valid && lam > T(0)) ? -inv_n / lam : T(0);
             const C z = R[m * stride + c];
             R[m * stride + c] = cmake<C>(z.x * gk, -z.y * gk);   // conj for the inverse transform
         }
         __syncthreads();
         C* other = (R == A) ? B : A;
-        R = block_fft<C>(R, other, stride, LPB, ap, twl);
+        R = block_fft<C, LPB>(R, other, ap, twl);
     }
-    for (int idx = threadIdx.x; idx < cnt; idx += kThreads) {
-        const int m = idx / LPB;
-        const int c = idx - m * LPB;
-        const long long l = l0 + c;
-        if (l < nlines) {
-            long long base;
-            if (MODE == 1) {
-                base = l;
-            } else {
-                const long long i = fdiv((unsigned)l, g.div_n3h);
-                base = i * g.n2 * g.n3h + (l - i * g.n3h);
-            }
+    if (valid) {
+        for (int m = m0; m < n; m += mstep) {
             C val = R[m * stride + c];
             if (MODE != 0) val = cconj(val);
             spec[base + m * es] = val;
@@ -372,17 +442,17 @@ __global__ void __launch_bounds__(kThreads) k_fft_strided(Geom g, Ptrs<T> p, Axi
 // ---------------------------------------------------------------------------
 // Pass 5: complex-to-real inverse FFT along z, two real lines per transform.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, int P>
 __global__ void __launch_bounds__(kThreads) k_irfft_z(Geom g, Ptrs<T> p, AxisPlan az,
-                                                      const cx<T>* __restrict__ tw, int P) {
+                                                      const cx<T>* __restrict__ tw) {
     using C = cx<T>;
+    constexpr int stride = P + 1;
     const int s = blockIdx.y;
     if (!p.run_all && !p.sc[s].active) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* twl = reinterpret_cast<C*>(smem_raw);
     C* A = twl + g.n3;
-    C* B = A + (size_t)g.n3 * (P + 1);
-    const int stride = P + 1;
+    C* B = A + (size_t)g.n3 * stride;
     for (int t = threadIdx.x; t < g.n3; t += kThreads) twl[t] = tw[t];
     const long long L = (long long)g.n1 * g.n2;
     const long long l0 = (long long)blockIdx.x * 2 * P;
@@ -404,7 +474,7 @@ __global__ void __launch_bounds__(kThreads) k_irfft_z(Geom g, Ptrs<T> p, AxisPla
         }
     }
     __syncthreads();
-    C* R = block_fft<C>(A, B, stride, P, az, twl);
+    C* R = block_fft<C, P>(A, B, az, twl);
     const int cnt2 = 2 * P * g.n3;
     T* phi = p.phi + (size_t)s * g.N;
     for (int idx = threadIdx.x; idx < cnt2; idx += kThreads) {
@@ -422,119 +492,86 @@ __global__ void __launch_bounds__(kThreads) k_irfft_z(Geom g, Ptrs<T> p, AxisPla
 // Pass 6: projection completion, node-wise projection, multiplier update and
 // reductions; the last block of each solve runs the penalty / stop logic.
 // ---------------------------------------------------------------------------
+template <typename T>
+struct StepConsts {
+    T rho, irho, h, alpha, beta;
+    T xi[3];
+};
+
+// Per-voxel work of the update pass. Inputs: the voxel's own state (ec, vc),
+// gamma, phi at the voxel and at p +- e_a, and the neighbour state components
+// the stencil needs: e/v of w2_a at p + e_a and of w1_a at p - e_a.
 template <typename T, bool OUT>
-__global__ void __launch_bounds__(kThreads) k_update(Geom g, Ptrs<T> p, LoopConfig cfg) {
-    const int s = blockIdx.y;
-    SolveScalars& S = p.sc[s];
-    if (!OUT && !S.active) return;
-    const long long N = g.N;
-    const double rho_d = S.rho;
-    const T rho = (T)rho_d;
-    const T irho = T(1) / rho;
-    const T h = T(0.70710678118654752440084436210485);
-    const T xi0 = (T)S.xi[0], xi1 = (T)S.xi[1], xi2 = (T)S.xi[2];
-    const T alpha = (T)(2.0 * (1.0 - cfg.delta)), beta = (T)(1.0 - 2.0 * cfg.delta);
-    // read the current copy of the state, write the other one (the stencil reads
-    // neighbours, so an in-place update would race)
-    const int par = S.iters & 1;
-    const T* __restrict__ e = p.e + (long long)par * p.sstride + (long long)s * 6 * N;
-    const T* __restrict__ v = p.v + (long long)par * p.sstride + (long long)s * 6 * N;
-    T* __restrict__ e_out = p.e + (long long)(1 - par) * p.sstride + (long long)s * 6 * N;
-    T* __restrict__ v_out = p.v + (long long)(1 - par) * p.sstride + (long long)s * 6 * N;
-    const T* __restrict__ phi = p.phi + (size_t)s * N;
-    const T* __restrict__ gam = p.gamma + (size_t)s * p.gstride;
-    T acc[kNSum];
+__device__ __forceinline__ void voxel_step(const StepConsts<T>& K, const T (&ec)[6], const T (&vc)[6], T gm, T ph0,
+                                           const T (&php)[3], const T (&phm)[3], const T (&e2p)[3],
+                                           const T (&v2p)[3], const T (&e1m)[3], const T (&v1m)[3],
+                                           T (&acc)[kNSum], T (&eo)[6], T (&vo)[6], T (&flow)[3]) {
+    T w[6], xh[6];
 #pragma unroll
-    for (int q = 0; q < kNSum; ++q) acc[q] = T(0);
-    const long long gstride = (long long)gridDim.x * kThreads;
-    for (long long lin = (long long)blockIdx.x * kThreads + threadIdx.x; lin < N; lin += gstride) {
-        const unsigned row = fdiv((unsigned)lin, g.div_n3);
-        const int k = (int)(lin - (long long)row * g.n3);
-        const unsigned i = fdiv(row, g.div_n2);
-        const int j = (int)(row - i * g.n2);
-        const long long base_i = (long long)i * g.n2 * g.n3;
-        const long long base_j = (long long)j * g.n3;
-        const int ip = ((int)i + 1 == g.n1) ? 0 : (int)i + 1, im = (i == 0) ? g.n1 - 1 : (int)i - 1;
-        const int jp = (j + 1 == g.n2) ? 0 : j + 1, jm = (j == 0) ? g.n2 - 1 : j - 1;
-        const int kp = (k + 1 == g.n3) ? 0 : k + 1, km = (k == 0) ? g.n3 - 1 : k - 1;
-        const long long nb_p[3] = {(long long)ip * g.n2 * g.n3 + base_j + k, base_i + (long long)jp * g.n3 + k,
-                                   base_i + base_j + kp};
-        const long long nb_m[3] = {(long long)im * g.n2 * g.n3 + base_j + k, base_i + (long long)jm * g.n3 + k,
-                                   base_i + base_j + km};
-        T ec[6], vc[6], w[6], xh[6];
+    for (int c = 0; c < 6; ++c) w[c] = ec[c] - vc[c] * K.irho;
 #pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            ec[c] = e[c * N + lin];
-            vc[c] = v[c * N + lin];
-            w[c] = ec[c] - vc[c] * irho;
-        }
-        const T ph0 = phi[lin];
-        const T xi[3] = {xi0, xi1, xi2};
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const long long qp = nb_p[a], qm = nb_m[a];
-            const T w2p = e[(3 + a) * N + qp] - v[(3 + a) * N + qp] * irho;   // w2_a(p + e_a)
-            const T w1m = e[a * N + qm] - v[a * N + qm] * irho;               // w1_a(p - e_a)
-            const T ua = h * (w[a] + w2p);                                    // (A* w)_a(p)
-            const T uam = h * (w1m + w[3 + a]);                               // (A* w)_a(p - e_a)
-            const T ya = ua - (phi[qp] - ph0) - xi[a];
-            const T yam = uam - (ph0 - phi[qm]) - xi[a];
-            xh[a] = w[a] - h * ya;
-            xh[3 + a] = w[3 + a] - h * yam;
-        }
-        const T gm = gam[lin];
-        T r2 = T(0), nx2 = T(0);
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            const T dd = ec[c] - xh[c];
-            r2 += dd * dd;
-            nx2 += xh[c] * xh[c];
-            acc[kSumV + c] += vc[c];
-        }
-        acc[kSumRes] += r2;
-        acc[kSumPrimal] += gm * Real<T>::sqrt_(nx2);
-        if (OUT) {
-            if (p.cut) {
-                T* cut = p.cut + (size_t)s * 6 * N;
-#pragma unroll
-                for (int c = 0; c < 6; ++c) cut[c * N + lin] = xh[c];
-            }
-            if (p.flow) {
-                T* flow = p.flow + (size_t)s * 3 * N;
-#pragma unroll
-                for (int a = 0; a < 3; ++a) flow[a * N + lin] = h * (vc[a] + v[(3 + a) * N + nb_p[a]]);
-            }
-        } else {
-            T z[6];
-            T nz2 = T(0);
-#pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                z[c] = vc[c] + rho * (alpha * xh[c] - beta * ec[c]);
-                nz2 += z[c] * z[c];
-            }
-            const T nz = Real<T>::sqrt_(nz2);
-            const T scale = (nz > gm) ? gm / nz : T(1);
-            T dvde = T(0), dede = T(0), dvdv = T(0), vv = T(0), ee = T(0);
-#pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                const T vn = z[c] * scale;
-                const T en = (z[c] - vn) * irho;
-                const T dv = vn - vc[c], de = en - ec[c];
-                dvde += dv * de;
-                dede += de * de;
-                dvdv += dv * dv;
-                vv += vn * vn;
-                ee += en * en;
-                e_out[c * N + lin] = en;
-                v_out[c * N + lin] = vn;
-            }
-            acc[kSumDvDe] += dvde;
-            acc[kSumDeDe] += dede;
-            acc[kSumDvDv] += dvdv;
-            acc[kSumVV] += vv;
-            acc[kSumEE] += ee;
-        }
+    for (int a = 0; a < 3; ++a) {
+        const T w2p = e2p[a] - v2p[a] * K.irho;   // w2_a(p + e_a)
+        const T w1m = e1m[a] - v1m[a] * K.irho;   // w1_a(p - e_a)
+        const T ua = K.h * (w[a] + w2p);          // (A* w)_a(p)
+        const T uam = K.h * (w1m + w[3 + a]);     // (A* w)_a(p - e_a)
+        const T ya = ua - (php[a] - ph0) - K.xi[a];
+        const T yam = uam - (ph0 - phm[a]) - K.xi[a];
+        xh[a] = w[a] - K.h * ya;
+        xh[3 + a] = w[3 + a] - K.h * yam;
     }
+    T r2 = T(0), nx2 = T(0);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        const T dd = ec[c] - xh[c];
+        r2 += dd * dd;
+        nx2 += xh[c] * xh[c];
+        acc[kSumV + c] += vc[c];
+    }
+    acc[kSumRes] += r2;
+    acc[kSumPrimal] += gm * Real<T>::sqrt_(nx2);
+    if (OUT) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) eo[c] = xh[c];                   // the cut xi^{K+1/2}
+#pragma unroll
+        for (int a = 0; a < 3; ++a) flow[a] = K.h * (vc[a] + v2p[a]);  // A* v
+    } else {
+        T z[6];
+        T nz2 = T(0);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            z[c] = vc[c] + K.rho * (K.alpha * xh[c] - K.beta * ec[c]);
+            nz2 += z[c] * z[c];
+        }
+        const T nz = Real<T>::sqrt_(nz2);
+        const T scale = (nz > gm) ? gm / nz : T(1);
+        T dvde = T(0), dede = T(0), dvdv = T(0), vv = T(0), ee = T(0);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const T vn = z[c] * scale;
+            const T en = (z[c] - vn) * K.irho;
+            const T dv = vn - vc[c], de = en - ec[c];
+            dvde += dv * de;
+            dede += de * de;
+            dvdv += dv * dv;
+            vv += vn * vn;
+            ee += en * en;
+            eo[c] = en;
+            vo[c] = vn;
+        }
+        acc[kSumDvDe] += dvde;
+        acc[kSumDeDe] += dede;
+        acc[kSumDvDv] += dvdv;
+        acc[kSumVV] += vv;
+        acc[kSumEE] += ee;
+    }
+}
+
+// Reduction epilogue of the update pass: block partials, then the last block of
+// the solve reduces them in double and runs the penalty / history / stop logic.
+template <typename T, bool OUT>
+__device__ void update_epilogue(const Geom& g, const Ptrs<T>& p, const LoopConfig& cfg, SolveScalars& S, int s,
+                                double rho_d, T (&acc)[kNSum]) {
     const int nblocks = gridDim.x;
     double* part = p.partial + (size_t)s * nblocks * kNSum;
     const bool last = block_partials<T, kNSum>(acc, part, &S.counter, nblocks, blockIdx.x);
@@ -543,7 +580,7 @@ __global__ void __launch_bounds__(kThreads) k_update(Geom g, Ptrs<T> p, LoopConf
     reduce_partials<kNSum>(part, nblocks, sums);
     if (threadIdx.x != 0) return;
     S.counter = 0;
-    const double Nd = (double)N;
+    const double Nd = (double)g.N;
     bool finite = true;
     for (int q = 0; q < kNSum; ++q) {
         S.sums[q] = sums[q];
@@ -605,6 +642,179 @@ __global__ void __launch_bounds__(kThreads) k_update(Geom g, Ptrs<T> p, LoopConf
         S.active = 0;
         atomicSub(p.n_active, 1);
     }
+}
+
+template <typename T>
+__device__ __forceinline__ StepConsts<T> step_consts(const SolveScalars& S, const LoopConfig& cfg) {
+    StepConsts<T> K;
+    K.rho = (T)S.rho;
+    K.irho = T(1) / K.rho;
+    K.h = T(0.70710678118654752440084436210485);
+    K.alpha = (T)(2.0 * (1.0 - cfg.delta));
+    K.beta = (T)(1.0 - 2.0 * cfg.delta);
+    K.xi[0] = (T)S.xi[0];
+    K.xi[1] = (T)S.xi[1];
+    K.xi[2] = (T)S.xi[2];
+    return K;
+}
+
+// Scalar version (any N3, unaligned inputs, and the final evaluation pass).
+template <typename T, bool OUT>
+__global__ void __launch_bounds__(kThreads) k_update(Geom g, Ptrs<T> p, LoopConfig cfg) {
+    const int s = blockIdx.y;
+    SolveScalars& S = p.sc[s];
+    if (!OUT && !S.active) return;
+    const long long N = g.N;
+    const double rho_d = S.rho;
+    const StepConsts<T> K = step_consts<T>(S, cfg);
+    // read the current copy of the state, write the other one (the stencil reads
+    // neighbours, so an in-place update would race)
+    const int par = S.iters & 1;
+    const T* __restrict__ e = p.e + (long long)par * p.sstride + (long long)s * 6 * N;
+    const T* __restrict__ v = p.v + (long long)par * p.sstride + (long long)s * 6 * N;
+    T* __restrict__ e_out = p.e + (long long)(1 - par) * p.sstride + (long long)s * 6 * N;
+    T* __restrict__ v_out = p.v + (long long)(1 - par) * p.sstride + (long long)s * 6 * N;
+    const T* __restrict__ phi = p.phi + (size_t)s * N;
+    const T* __restrict__ gam = p.gamma + (size_t)s * p.gstride;
+    T acc[kNSum];
+#pragma unroll
+    for (int q = 0; q < kNSum; ++q) acc[q] = T(0);
+    const long long gstride = (long long)gridDim.x * kThreads;
+    for (long long lin = (long long)blockIdx.x * kThreads + threadIdx.x; lin < N; lin += gstride) {
+        const unsigned row = fdiv((unsigned)lin, g.div_n3);
+        const int k = (int)(lin - (long long)row * g.n3);
+        const RowNb rn = row_neighbours(g, row);
+        const int kp = (k + 1 == g.n3) ? 0 : k + 1, km = (k == 0) ? g.n3 - 1 : k - 1;
+        const long long nb_p[3] = {rn.ip + k, rn.jp + k, rn.row + kp};
+        const long long nb_m[3] = {rn.im + k, rn.jm + k, rn.row + km};
+        T ec[6], vc[6], php[3], phm[3], e2p[3], v2p[3], e1m[3], v1m[3];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            ec[c] = e[c * N + lin];
+            vc[c] = v[c * N + lin];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            php[a] = phi[nb_p[a]];
+            phm[a] = phi[nb_m[a]];
+            e2p[a] = e[(3 + a) * N + nb_p[a]];
+            v2p[a] = v[(3 + a) * N + nb_p[a]];
+            e1m[a] = e[a * N + nb_m[a]];
+            v1m[a] = v[a * N + nb_m[a]];
+        }
+        T eo[6], vo[6], fl[3];
+        voxel_step<T, OUT>(K, ec, vc, gam[lin], phi[lin], php, phm, e2p, v2p, e1m, v1m, acc, eo, vo, fl);
+        if (OUT) {
+            if (p.cut) {
+                T* cut = p.cut + (size_t)s * 6 * N;
+#pragma unroll
+                for (int c = 0; c < 6; ++c) cut[c * N + lin] = eo[c];
+            }
+            if (p.flow) {
+                T* flow = p.flow + (size_t)s * 3 * N;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) flow[a * N + lin] = fl[a];
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                e_out[c * N + lin] = eo[c];
+                v_out[c * N + lin] = vo[c];
+            }
+        }
+    }
+    update_epilogue<T, OUT>(g, p, cfg, S, s, rho_d, acc);
+}
+
+// Vector version of the advancing update: W consecutive voxels of a z line per
+// thread, 16-byte loads and stores (N3 % W == 0, 16-byte aligned gamma).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_update_vec(Geom g, Ptrs<T> p, LoopConfig cfg) {
+    constexpr int W = Vec16<T>::W;
+    using V = Vec16<T>;
+    const int s = blockIdx.y;
+    SolveScalars& S = p.sc[s];
+    if (!S.active) return;
+    const long long N = g.N;
+    const double rho_d = S.rho;
+    const StepConsts<T> K = step_consts<T>(S, cfg);
+    const int par = S.iters & 1;
+    const T* __restrict__ e = p.e + (long long)par * p.sstride + (long long)s * 6 * N;
+    const T* __restrict__ v = p.v + (long long)par * p.sstride + (long long)s * 6 * N;
+    T* __restrict__ e_out = p.e + (long long)(1 - par) * p.sstride + (long long)s * 6 * N;
+    T* __restrict__ v_out = p.v + (long long)(1 - par) * p.sstride + (long long)s * 6 * N;
+    const T* __restrict__ phi = p.phi + (size_t)s * N;
+    const T* __restrict__ gam = p.gamma + (size_t)s * p.gstride;
+    T acc[kNSum];
+#pragma unroll
+    for (int q = 0; q < kNSum; ++q) acc[q] = T(0);
+    const long long ngroups = N / W;
+    const long long gstride = (long long)gridDim.x * kThreads;
+    for (long long q = (long long)blockIdx.x * kThreads + threadIdx.x; q < ngroups; q += gstride) {
+        const long long lin0 = q * W;
+        const unsigned row = fdiv((unsigned)lin0, g.div_n3);
+        const int k0 = (int)(lin0 - (long long)row * g.n3);
+        const RowNb rn = row_neighbours(g, row);
+        const int kp = (k0 + W == g.n3) ? 0 : k0 + W;
+        const int km = (k0 == 0) ? g.n3 - 1 : k0 - 1;
+        T ec[6][W], vc[6][W];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            V::ld(e + c * N + lin0, ec[c]);
+            V::ld(v + c * N + lin0, vc[c]);
+        }
+        T gm[W], ph[W];
+        V::ld(gam + lin0, gm);
+        V::ld(phi + lin0, ph);
+        // x and y neighbours (whole groups), z neighbours inside the group or one scalar each side
+        T e2x[W], v2x[W], e1x[W], v1x[W], e2y[W], v2y[W], e1y[W], v1y[W];
+        T phxp[W], phxm[W], phyp[W], phym[W];
+        V::ld(e + 3 * N + rn.ip + k0, e2x);
+        V::ld(v + 3 * N + rn.ip + k0, v2x);
+        V::ld(e + 0 * N + rn.im + k0, e1x);
+        V::ld(v + 0 * N + rn.im + k0, v1x);
+        V::ld(e + 4 * N + rn.jp + k0, e2y);
+        V::ld(v + 4 * N + rn.jp + k0, v2y);
+        V::ld(e + 1 * N + rn.jm + k0, e1y);
+        V::ld(v + 1 * N + rn.jm + k0, v1y);
+        V::ld(phi + rn.ip + k0, phxp);
+        V::ld(phi + rn.im + k0, phxm);
+        V::ld(phi + rn.jp + k0, phyp);
+        V::ld(phi + rn.jm + k0, phym);
+        const T e2z_after = __ldg(e + 5 * N + rn.row + kp), v2z_after = __ldg(v + 5 * N + rn.row + kp);
+        const T e1z_before = __ldg(e + 2 * N + rn.row + km), v1z_before = __ldg(v + 2 * N + rn.row + km);
+        const T ph_after = __ldg(phi + rn.row + kp), ph_before = __ldg(phi + rn.row + km);
+        T eo[6][W], vo[6][W];
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+            T ecu[6], vcu[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                ecu[c] = ec[c][u];
+                vcu[c] = vc[c][u];
+            }
+            const bool last = (u + 1 == W), first = (u == 0);
+            const T php[3] = {phxp[u], phyp[u], last ? ph_after : ph[(u + 1) % W]};
+            const T phm[3] = {phxm[u], phym[u], first ? ph_before : ph[(u + W - 1) % W]};
+            const T e2p[3] = {e2x[u], e2y[u], last ? e2z_after : ec[5][(u + 1) % W]};
+            const T v2p[3] = {v2x[u], v2y[u], last ? v2z_after : vc[5][(u + 1) % W]};
+            const T e1m[3] = {e1x[u], e1y[u], first ? e1z_before : ec[2][(u + W - 1) % W]};
+            const T v1m[3] = {v1x[u], v1y[u], first ? v1z_before : vc[2][(u + W - 1) % W]};
+            T eou[6], vou[6], fl[3];
+            voxel_step<T, false>(K, ecu, vcu, gm[u], ph[u], php, phm, e2p, v2p, e1m, v1m, acc, eou, vou, fl);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                eo[c][u] = eou[c];
+                vo[c][u] = vou[c];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            V::st(e_out + c * N + lin0, eo[c]);
+            V::st(v_out + c * N + lin0, vo[c]);
+        }
+    }
+    update_epilogue<T, false>(g, p, cfg, S, s, rho_d, acc);
 }
 
 }  // namespace ccmf

@@ -15,6 +15,8 @@ struct Ctx {
     const T* sym[3];      // 4 sin^2(pi k / N_a) per axis
     const double* xi_stage;  // [batch][3] unit normals (device)
     LaunchShape sh;
+    bool vec_div;         // 16-byte path of the divergence pass (N3 % W == 0)
+    bool vec_update;      // 16-byte path of the update pass (also needs gamma 16-byte aligned)
 };
 
 // Kernel classes of one loop iteration, in launch order.
@@ -37,6 +39,19 @@ __global__ void k_setup(SolveScalars* sc, const double* __restrict__ xi, int bat
     sc[s].active = 0;
 }
 
+inline long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
+
+// Runs the statement list with the compile-time constant LN equal to the runtime
+// line count L (a power of two <= 16).
+#define CCMF_DISPATCH_LINES(L, ...)                              \
+    switch (L) {                                                 \
+        case 16: { constexpr int LN = 16; __VA_ARGS__; } break; \
+        case 8: { constexpr int LN = 8; __VA_ARGS__; } break;   \
+        case 4: { constexpr int LN = 4; __VA_ARGS__; } break;   \
+        case 2: { constexpr int LN = 2; __VA_ARGS__; } break;   \
+        default: { constexpr int LN = 1; __VA_ARGS__; } break;  \
+    }
+
 template <typename T>
 cudaError_t configure_kernels(const LaunchShape& sh) {
     cudaError_t err = cudaSuccess;
@@ -44,15 +59,18 @@ cudaError_t configure_kernels(const LaunchShape& sh) {
         if (err == cudaSuccess && bytes > 48 * 1024)
             err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     };
-    set((const void*)k_div_rfft_z<T>, sh.smem_z);
-    set((const void*)k_irfft_z<T>, sh.smem_z);
-    set((const void*)k_fft_strided<T, 0>, sh.smem_y);
-    set((const void*)k_fft_strided<T, 2>, sh.smem_y);
-    set((const void*)k_fft_strided<T, 1>, sh.smem_x);
+    CCMF_DISPATCH_LINES(sh.pairs_per_block, {
+        set((const void*)k_div_rfft_z<T, LN, true>, sh.smem_z);
+        set((const void*)k_div_rfft_z<T, LN, false>, sh.smem_z);
+        set((const void*)k_irfft_z<T, LN>, sh.smem_z);
+    });
+    CCMF_DISPATCH_LINES(sh.lpb_y, {
+        set((const void*)k_fft_strided<T, 0, LN>, sh.smem_y);
+        set((const void*)k_fft_strided<T, 2, LN>, sh.smem_y);
+    });
+    CCMF_DISPATCH_LINES(sh.lpb_x, { set((const void*)k_fft_strided<T, 1, LN>, sh.smem_x); });
     return err;
 }
-
-inline long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
 
 template <typename T>
 void launch_init(const Ctx<T>& c, cudaStream_t st) {
@@ -62,7 +80,7 @@ void launch_init(const Ctx<T>& c, cudaStream_t st) {
     if (!c.cfg.resume) k_init_state<T><<<grid, kThreads, 0, st>>>(c.g, c.p);
 }
 
-// Enqueue one ADMM iteration (or, with p.run_all and OUT, the final evaluation).
+// Enqueue one ADMM iteration (or, with OUT, the final evaluation).
 // `between` is called after every kernel with its class (used to record events).
 template <typename T, bool OUT, typename F>
 void launch_passes(const Ctx<T>& c, const Ptrs<T>& p, cudaStream_t st, F&& between) {
@@ -74,20 +92,37 @@ void launch_passes(const Ctx<T>& c, const Ptrs<T>& p, cudaStream_t st, F&& betwe
     dim3 gx((unsigned)ceil_div((long long)g.n2 * g.n3h, sh.lpb_x), (unsigned)g.batch);
     dim3 gu((unsigned)sh.grid_update, (unsigned)g.batch);
     const T inv_n = (T)(1.0 / (double)g.N);
-    k_div_rfft_z<T><<<gz, kThreads, sh.smem_z, st>>>(g, p, c.ax[2], c.tw[2], sh.pairs_per_block);
+    CCMF_DISPATCH_LINES(sh.pairs_per_block, {
+        if (c.vec_div)
+            k_div_rfft_z<T, LN, true><<<gz, kThreads, sh.smem_z, st>>>(g, p, c.ax[2], c.tw[2]);
+        else
+            k_div_rfft_z<T, LN, false><<<gz, kThreads, sh.smem_z, st>>>(g, p, c.ax[2], c.tw[2]);
+    });
     between(kKDivRfftZ);
-    k_fft_strided<T, 0><<<gy, kThreads, sh.smem_y, st>>>(g, p, c.ax[1], c.tw[1], sh.lpb_y, c.sym[0], c.sym[1],
-                                                         c.sym[2], inv_n);
+    CCMF_DISPATCH_LINES(sh.lpb_y, {
+        k_fft_strided<T, 0, LN><<<gy, kThreads, sh.smem_y, st>>>(g, p, c.ax[1], c.tw[1], c.sym[0], c.sym[1],
+                                                                  c.sym[2], inv_n);
+    });
     between(kKFftYFwd);
-    k_fft_strided<T, 1><<<gx, kThreads, sh.smem_x, st>>>(g, p, c.ax[0], c.tw[0], sh.lpb_x, c.sym[0], c.sym[1],
-                                                         c.sym[2], inv_n);
+    CCMF_DISPATCH_LINES(sh.lpb_x, {
+        k_fft_strided<T, 1, LN><<<gx, kThreads, sh.smem_x, st>>>(g, p, c.ax[0], c.tw[0], c.sym[0], c.sym[1],
+                                                                  c.sym[2], inv_n);
+    });
     between(kKFftXSolve);
-    k_fft_strided<T, 2><<<gy, kThreads, sh.smem_y, st>>>(g, p, c.ax[1], c.tw[1], sh.lpb_y, c.sym[0], c.sym[1],
-                                                         c.sym[2], inv_n);
+    CCMF_DISPATCH_LINES(sh.lpb_y, {
+        k_fft_strided<T, 2, LN><<<gy, kThreads, sh.smem_y, st>>>(g, p, c.ax[1], c.tw[1], c.sym[0], c.sym[1],
+                                                                  c.sym[2], inv_n);
+    });
     between(kKFftYInv);
-    k_irfft_z<T><<<gz, kThreads, sh.smem_z, st>>>(g, p, c.ax[2], c.tw[2], sh.pairs_per_block);
+    CCMF_DISPATCH_LINES(sh.pairs_per_block,
+                        { k_irfft_z<T, LN><<<gz, kThreads, sh.smem_z, st>>>(g, p, c.ax[2], c.tw[2]); });
     between(kKIrfftZ);
-    k_update<T, OUT><<<gu, kThreads, 0, st>>>(g, p, c.cfg);
+    if (OUT)
+        k_update<T, true><<<gu, kThreads, 0, st>>>(g, p, c.cfg);
+    else if (c.vec_update)
+        k_update_vec<T><<<gu, kThreads, 0, st>>>(g, p, c.cfg);
+    else
+        k_update<T, false><<<gu, kThreads, 0, st>>>(g, p, c.cfg);
     between(kKUpdate);
 }
 

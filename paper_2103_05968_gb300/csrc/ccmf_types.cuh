@@ -48,26 +48,6 @@ struct LoopConfig {
     int max_iter, fixed_iters, rho_rule, hist_len, resume;
 };
 
-// Unsigned division by a fixed divisor through a multiply-high and shift
-// (Granlund & Montgomery, PLDI 1994): q = (umulhi(n, m) + n) >> s, exact for n < 2^32.
-struct FastDiv {
-    unsigned d, m, s;
-};
-
-inline FastDiv make_fastdiv(unsigned d) {
-    FastDiv f;
-    f.d = d;
-    unsigned s = 0;
-    while ((1ull << s) < d) ++s;
-    f.s = s;
-    f.m = (unsigned)((((1ull << 32) * ((1ull << s) - d)) / d) + 1ull);
-    return f;
-}
-
-__device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv& f) {
-    return (unsigned)(((unsigned long long)__umulhi(n, f.m) + n) >> f.s);
-}
-
 struct Geom {
     int n1, n2, n3, n3h, batch;
     long long N;    // voxels per solve

@@ -179,6 +179,49 @@ int ccmf_kernel_times(const ccmf_plan* plan, double* ms, long long* launches, co
  * inside the captured graph; fixed_iters mode only). */
 int ccmf_set_kernel_timing(ccmf_plan* plan, int enable);
 
+/*
+ * Size of the fixed device scratch area used by ccmf_solve_static (64 MiB). The
+ * area is a file-scope __device__ array of the library: every GPU that loads the
+ * library holds it until the process exits.
+ */
+#define CCMF_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
+
+/*
+ * ccmf_solve_static - one solve (batch 1) that allocates no memory.
+ *
+ * The paper has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory where they need a solve, for example code running while
+ * one of its own streams is being captured into a CUDA graph (cudaMalloc is not
+ * allowed there), plug-ins whose host application owns all device memory through
+ * its own pool, or latency-critical paths that must avoid the implicit device
+ * synchronisation of cudaMalloc and cudaFree. It needs no plan and no workspace:
+ * its state, spectra, reduction partials, history and FFT tables live in the
+ * library's fixed scratch area of CCMF_STATIC_SCRATCH_BYTES bytes, and it calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *
+ *   n1, n2, n3 : grid as for ccmf_plan_create; a grid whose state does not fit the
+ *                scratch area is rejected with CCMF_ERR_UNSUPPORTED_SIZE (about
+ *                500k voxels in CCMF_FP32_MIXED, 260k in CCMF_FP64, e.g. 80^3 / 64^3)
+ *   precision  : CCMF_FP64 or CCMF_FP32_MIXED (element type of gamma, flow, cut)
+ *   gamma      : device array [N1][N2][N3]
+ *   xi_bar     : host array [3], the crack normal (normalised internally)
+ *   params     : as for ccmf_solve (NULL = defaults); resume must be 0
+ *   flow, cut  : optional device outputs [3][N] and [6][N] (NULL to skip)
+ *   result     : optional host result; when given, the call synchronises the stream
+ * Returns CCMF_OK or an error code; per-solve failures are in result->status.
+ *
+ * The first call on a device looks up the device address of the scratch area
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture. Kernels are launched directly on `stream` (no graph); with a
+ * tolerance (fixed_iters = 0) the host reads a counter from the device every
+ * check_every updates. Every call on a device shares the one scratch area and
+ * overwrites what the previous call left there: calls whose GPU work overlaps in
+ * time (other streams, other host threads) race with each other and must be
+ * serialised by the caller.
+ */
+int ccmf_solve_static(int n1, int n2, int n3, int precision, const void* gamma, const double* xi_bar,
+                      const ccmf_params* params, void* flow, void* cut, ccmf_result* result, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

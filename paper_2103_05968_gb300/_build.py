@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libccmf.so")
-SOURCES = ["ccmf_abi.cu", "ccmf_f32.cu", "ccmf_f64.cu"]
+SOURCES = ["ccmf_abi.cu", "ccmf_f32.cu", "ccmf_f64.cu", "ccmf_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

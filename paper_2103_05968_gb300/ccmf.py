@@ -94,6 +94,10 @@ _SIGNATURES = {
                                           ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_char_p),
                                           ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "ccmf_set_kernel_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "ccmf_solve_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ccmf_params),
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ccmf_result),
+                                          ctypes.c_void_p]),
 }
 
 
@@ -197,6 +201,16 @@ def ccmf_kernel_times(plan):
 
 def ccmf_set_kernel_timing(plan, enable):
     return load_library().ccmf_set_kernel_timing(plan, int(enable))
+
+
+def ccmf_solve_static(n1, n2, n3, precision, gamma_ptr, xi_bar, params, flow_ptr, cut_ptr, result, stream):
+    """The allocation-free single solve (see include/ccmf.h): all scratch lives in the
+    library's fixed device array, so no workspace or plan is passed."""
+    xi = np.ascontiguousarray(xi_bar, dtype=np.float64).reshape(3)
+    return load_library().ccmf_solve_static(int(n1), int(n2), int(n3), int(precision), gamma_ptr,
+                                            xi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                            ctypes.byref(params) if params is not None else None,
+                                            flow_ptr, cut_ptr, result, stream)
 
 
 # ---- torch-facing convenience layer (argument marshalling only) --------------

@@ -408,6 +408,25 @@ int ccmf_plan_create(int n1, int n2, int n3, int batch, int precision, ccmf_plan
         long long gu = (g.N + kThreads - 1) / kThreads;
         if (gu > 608) gu = 608;
         sh.grid_update = (int)gu;
+        // TMA-staged update: tiles of J z rows with J * N3 <= 512 (FP32) / 256 (FP64) voxels,
+        // J a power of two dividing N2; two stages must fit the shared memory of a block
+        int sms = 0, dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+            sms = 152;
+        const int tv_max = precision == CCMF_FP64 ? 256 : 512;
+        const int W = precision == CCMF_FP64 ? 2 : 4;
+        int J = 1;
+        while (2 * J * n3 <= tv_max && n2 % (2 * J) == 0) J *= 2;
+        const size_t smem_tma = 2 * (size_t)tma_stage_elems(J * n3, n3) * pl->esize + 16;
+        sh.tma_rows = (n3 % W == 0 && smem_tma <= 200 * 1024) ? J : 0;
+        sh.smem_tma = smem_tma;
+        long long ntiles = (long long)n1 * (n2 / J);
+        long long gt = (2LL * sms + batch - 1) / batch;
+        if (gt > ntiles) gt = ntiles;
+        if (gt < 1) gt = 1;
+        sh.grid_tma = (int)gt;
+        sh.grid_partials = sh.grid_update > sh.grid_tma ? sh.grid_update : sh.grid_tma;
     }
 
     // workspace layout
@@ -421,7 +440,7 @@ int ccmf_plan_create(int n1, int n2, int n3, int batch, int precision, ccmf_plan
     pl->off_sc = take(256 * (size_t)batch);
     pl->off_nact = take(256);
     pl->off_xi = take(3 * sizeof(double) * batch);
-    pl->off_part = take(sizeof(double) * kNSum * (size_t)sh.grid_update * batch);
+    pl->off_part = take(sizeof(double) * kNSum * (size_t)sh.grid_partials * batch);
     pl->off_hist = take(sizeof(double) * kHistFields * (size_t)kHistCap * batch);
     pl->off_e = take(pl->esize * 6 * N * batch * 2);
     pl->off_v = take(pl->esize * 6 * N * batch * 2);

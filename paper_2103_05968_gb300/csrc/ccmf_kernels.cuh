@@ -624,7 +624,9 @@ __device__ void update_epilogue(const Geom& g, const Ptrs<T>& p, const LoopConfi
     const int done = kk + 1 - S.call_start;
     S.iters = kk + 1;
     bool stop = false;
-    if (!finite || !isfinite(rho_new) || !(rho_new > 0.0)) {
+    if (S.status != 0) {
+        stop = true;   // a failure recorded during the pass (e.g. a bounded wait that gave up)
+    } else if (!finite || !isfinite(rho_new) || !(rho_new > 0.0)) {
         S.status = 5;  // CCMF_ERR_NUMERICAL: rho and the state are left as they are
         stop = true;
     } else {
@@ -813,6 +815,212 @@ __global__ void __launch_bounds__(kThreads) k_update_vec(Geom g, Ptrs<T> p, Loop
             V::st(e_out + c * N + lin0, eo[c]);
             V::st(v_out + c * N + lin0, vo[c]);
         }
+    }
+    update_epilogue<T, false>(g, p, cfg, S, s, rho_d, acc);
+}
+
+// ---------------------------------------------------------------------------
+// TMA-staged update pass. A tile is J consecutive z rows (i, j0 .. j0+J-1) of one
+// solve, TV = J * N3 voxels. One elected thread copies everything the tile's
+// stencil reads into shared memory with bulk asynchronous copies (cp.async.bulk,
+// completion counted in bytes on an mbarrier): the 12 state fields, gamma and phi
+// of the tile, the halo rows j0-1 / j0+J of the fields that reach across y, and
+// the rows of the planes i-1 / i+1 that reach across x. Two stages alternate so
+// that the copies of the next tiles overlap the arithmetic of the current one.
+// Every wait is bounded: a wait that gives up records CCMF_ERR_TIMEOUT for the
+// solve, waits (bounded) for its copies in flight and leaves the loop.
+// ---------------------------------------------------------------------------
+constexpr unsigned kSpinLimit = 1u << 22;
+
+__device__ __forceinline__ unsigned smem_u32(const void* ptr) {
+    return (unsigned)__cvta_generic_to_shared(ptr);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity; false if it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+    for (unsigned spin = 0; spin < kSpinLimit; ++spin)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Elements of one stage: own[14][TV] (e0..e5, v0..v5, gamma, phi), yh[6][N3]
+// (e1, v1 at row j0-1; e4, v4 at row j0+J; phi at j0-1, j0+J), xn[6][TV]
+// (e0, v0 at plane i-1; e3, v3 at plane i+1; phi at i-1, i+1).
+__host__ __device__ inline long long tma_stage_elems(int TV, int n3) { return 20LL * TV + 6LL * n3; }
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 2) k_update_tma(Geom g, Ptrs<T> p, LoopConfig cfg, int J) {
+    const int s = blockIdx.y;
+    SolveScalars& S = p.sc[s];
+    if (!S.active) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n3 = g.n3;
+    const int TV = J * n3;
+    const long long selems = tma_stage_elems(TV, n3);
+    T* stage0 = reinterpret_cast<T*>(smem_raw);
+    T* stage1 = stage0 + selems;
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(stage0 + 2 * selems);
+    const unsigned stage_bytes = (unsigned)(selems * sizeof(T));
+    const unsigned tv_bytes = (unsigned)(TV * sizeof(T)), row_bytes = (unsigned)(n3 * sizeof(T));
+
+    const long long N = g.N;
+    const double rho_d = S.rho;
+    const StepConsts<T> K = step_consts<T>(S, cfg);
+    const int par = S.iters & 1;
+    const T* __restrict__ e = p.e + (long long)par * p.sstride + (long long)s * 6 * N;
+    const T* __restrict__ v = p.v + (long long)par * p.sstride + (long long)s * 6 * N;
+    T* __restrict__ e_out = p.e + (long long)(1 - par) * p.sstride + (long long)s * 6 * N;
+    T* __restrict__ v_out = p.v + (long long)(1 - par) * p.sstride + (long long)s * 6 * N;
+    const T* __restrict__ phi = p.phi + (size_t)s * N;
+    const T* __restrict__ gam = p.gamma + (size_t)s * p.gstride;
+    const int tiles_j = g.n2 / J;
+    const int ntiles = g.n1 * tiles_j;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    // producer: all copies of one tile into one stage (thread 0 only)
+    auto issue = [&](int tile, int st) {
+        T* b = st ? stage1 : stage0;
+        const int i = tile / tiles_j;
+        const int j0 = (tile - i * tiles_j) * J;
+        const int ip = (i + 1 == g.n1) ? 0 : i + 1, im = (i == 0) ? g.n1 - 1 : i - 1;
+        const int jp = (j0 + J == g.n2) ? 0 : j0 + J, jm = (j0 == 0) ? g.n2 - 1 : j0 - 1;
+        const long long base = ((long long)i * g.n2 + j0) * n3;
+        const long long bip = ((long long)ip * g.n2 + j0) * n3, bim = ((long long)im * g.n2 + j0) * n3;
+        const long long rjp = ((long long)i * g.n2 + jp) * n3, rjm = ((long long)i * g.n2 + jm) * n3;
+        unsigned long long* bar = &bars[st];
+        mbar_expect_tx(bar, stage_bytes);
+        T* own = b;
+        T* yh = b + 14LL * TV;
+        T* xn = yh + 6LL * n3;
+        for (int c = 0; c < 6; ++c) {
+            bulk_g2s(own + (long long)c * TV, e + c * N + base, tv_bytes, bar);
+            bulk_g2s(own + (long long)(6 + c) * TV, v + c * N + base, tv_bytes, bar);
+        }
+        bulk_g2s(own + 12LL * TV, gam + base, tv_bytes, bar);
+        bulk_g2s(own + 13LL * TV, phi + base, tv_bytes, bar);
+        bulk_g2s(yh + 0LL * n3, e + 1 * N + rjm, row_bytes, bar);
+        bulk_g2s(yh + 1LL * n3, v + 1 * N + rjm, row_bytes, bar);
+        bulk_g2s(yh + 2LL * n3, e + 4 * N + rjp, row_bytes, bar);
+        bulk_g2s(yh + 3LL * n3, v + 4 * N + rjp, row_bytes, bar);
+        bulk_g2s(yh + 4LL * n3, phi + rjm, row_bytes, bar);
+        bulk_g2s(yh + 5LL * n3, phi + rjp, row_bytes, bar);
+        bulk_g2s(xn + 0LL * TV, e + 0 * N + bim, tv_bytes, bar);
+        bulk_g2s(xn + 1LL * TV, v + 0 * N + bim, tv_bytes, bar);
+        bulk_g2s(xn + 2LL * TV, e + 3 * N + bip, tv_bytes, bar);
+        bulk_g2s(xn + 3LL * TV, v + 3 * N + bip, tv_bytes, bar);
+        bulk_g2s(xn + 4LL * TV, phi + bim, tv_bytes, bar);
+        bulk_g2s(xn + 5LL * TV, phi + bip, tv_bytes, bar);
+    };
+
+    const int t0 = blockIdx.x;
+    const int tstep = gridDim.x;
+    if (threadIdx.x == 0) {
+        if (t0 < ntiles) issue(t0, 0);
+        if (t0 + tstep < ntiles) issue(t0 + tstep, 1);
+    }
+    T acc[kNSum];
+#pragma unroll
+    for (int q = 0; q < kNSum; ++q) acc[q] = T(0);
+    unsigned phase0 = 0, phase1 = 0;
+    int it = 0;
+    bool failed = false;
+    for (int tile = t0; tile < ntiles; tile += tstep, ++it) {
+        const int st = it & 1;
+        const unsigned ph = st ? phase1 : phase0;
+        const bool ok = mbar_wait_bounded(&bars[st], ph);
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        if (st) phase1 ^= 1u; else phase0 ^= 1u;
+        const T* b = st ? stage1 : stage0;
+        const T* own = b;
+        const T* yh = b + 14LL * TV;
+        const T* xn = yh + 6LL * n3;
+        const int i = tile / tiles_j;
+        const int j0 = (tile - i * tiles_j) * J;
+        const long long base = ((long long)i * g.n2 + j0) * n3;
+        for (int lv = threadIdx.x; lv < TV; lv += kThreads) {
+            const int r = (int)fdiv((unsigned)lv, g.div_n3);
+            const int k = lv - r * n3;
+            const int kp = (k + 1 == n3) ? 0 : k + 1, km = (k == 0) ? n3 - 1 : k - 1;
+            const int lzp = r * n3 + kp, lzm = r * n3 + km;
+            T ec[6], vc[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                ec[c] = own[c * TV + lv];
+                vc[c] = own[(6 + c) * TV + lv];
+            }
+            const bool top = (r + 1 == J), bot = (r == 0);
+            const T php[3] = {xn[5 * TV + lv], top ? yh[5 * n3 + k] : own[13 * TV + lv + n3], own[13 * TV + lzp]};
+            const T phm[3] = {xn[4 * TV + lv], bot ? yh[4 * n3 + k] : own[13 * TV + lv - n3], own[13 * TV + lzm]};
+            const T e2p[3] = {xn[2 * TV + lv], top ? yh[2 * n3 + k] : own[4 * TV + lv + n3], own[5 * TV + lzp]};
+            const T v2p[3] = {xn[3 * TV + lv], top ? yh[3 * n3 + k] : own[10 * TV + lv + n3], own[11 * TV + lzp]};
+            const T e1m[3] = {xn[0 * TV + lv], bot ? yh[0 * n3 + k] : own[1 * TV + lv - n3], own[2 * TV + lzm]};
+            const T v1m[3] = {xn[1 * TV + lv], bot ? yh[1 * n3 + k] : own[7 * TV + lv - n3], own[8 * TV + lzm]};
+            T eo[6], vo[6], fl[3];
+            voxel_step<T, false>(K, ec, vc, own[12 * TV + lv], own[13 * TV + lv], php, phm, e2p, v2p, e1m, v1m, acc,
+                                 eo, vo, fl);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                e_out[c * N + base + lv] = eo[c];
+                v_out[c * N + base + lv] = vo[c];
+            }
+        }
+        __syncthreads();   // every thread is done with this stage
+        if (threadIdx.x == 0 && tile + 2 * tstep < ntiles) {
+            fence_proxy_async_smem();
+            issue(tile + 2 * tstep, st);
+        }
+    }
+    if (failed) {
+        // the copies still in flight land in this block's shared memory: wait for them (bounded)
+        if (threadIdx.x == 0) {
+            for (int extra = 0; extra < 2; ++extra) {
+                const int st = (it + extra) & 1;
+                const int tile = t0 + (it + extra) * tstep;
+                if (tile < ntiles) (void)mbar_wait_bounded(&bars[st], st ? phase1 : phase0);
+            }
+            atomicExch(&S.status, 6);   // CCMF_ERR_TIMEOUT
+        }
+        __syncthreads();
     }
     update_epilogue<T, false>(g, p, cfg, S, s, rho_d, acc);
 }

@@ -78,6 +78,10 @@ struct LaunchShape {
     int lpb_y, lpb_x;         // strided passes: lines per block
     int grid_update;          // blocks per solve of the voxel passes
     size_t smem_z, smem_y, smem_x;
+    int tma_rows;             // TMA-staged update: z rows per tile (0 = path not available)
+    int grid_tma;             // blocks per solve of the TMA-staged update
+    size_t smem_tma;          // its dynamic shared memory (two stages + barriers)
+    int grid_partials;        // partial-sum slots per solve (max of the update grids)
 };
 
 }  // namespace ccmf

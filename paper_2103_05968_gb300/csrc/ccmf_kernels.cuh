@@ -498,10 +498,31 @@ struct StepConsts {
     T xi[3];
 };
 
+// Projection helpers. FP64 uses correctly rounded sqrt and division, as the
+// FP64 path is compared with the oracle at the 1e-10 level. FP32 uses the
+// hardware reciprocal square root (relative error ~1e-7, below FP32 field noise):
+// scale = gamma / |z| when |z| > gamma is gamma * rsqrt(|z|^2), compared in squares.
+template <typename T> struct Proj;
+template <> struct Proj<double> {
+    __device__ __forceinline__ static double scale(double nz2, double gm) {
+        const double nz = sqrt(nz2);
+        return (nz > gm) ? gm / nz : 1.0;
+    }
+    __device__ __forceinline__ static double norm(double x2) { return sqrt(x2); }
+};
+template <> struct Proj<float> {
+    __device__ __forceinline__ static float scale(float nz2, float gm) {
+        return (nz2 > gm * gm) ? gm * rsqrtf(nz2) : 1.0f;
+    }
+    __device__ __forceinline__ static float norm(float x2) { return x2 > 0.0f ? x2 * rsqrtf(x2) : 0.0f; }
+};
+
 // Per-voxel work of the update pass. Inputs: the voxel's own state (ec, vc),
 // gamma, phi at the voxel and at p +- e_a, and the neighbour state components
 // the stencil needs: e/v of w2_a at p + e_a and of w1_a at p - e_a.
-template <typename T, bool OUT>
+// RULE selects which penalty sums are accumulated (0 BB, 1 constant, 2 LTD,
+// -1 all of them).
+template <typename T, bool OUT, int RULE = -1>
 __device__ __forceinline__ void voxel_step(const StepConsts<T>& K, const T (&ec)[6], const T (&vc)[6], T gm, T ph0,
                                            const T (&php)[3], const T (&phm)[3], const T (&e2p)[3],
                                            const T (&v2p)[3], const T (&e1m)[3], const T (&v1m)[3],
@@ -529,7 +550,7 @@ __device__ __forceinline__ void voxel_step(const StepConsts<T>& K, const T (&ec)
         acc[kSumV + c] += vc[c];
     }
     acc[kSumRes] += r2;
-    acc[kSumPrimal] += gm * Real<T>::sqrt_(nx2);
+    acc[kSumPrimal] += gm * Proj<T>::norm(nx2);
     if (OUT) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) eo[c] = xh[c];                   // the cut xi^{K+1/2}
@@ -543,19 +564,22 @@ __device__ __forceinline__ void voxel_step(const StepConsts<T>& K, const T (&ec)
             z[c] = vc[c] + K.rho * (K.alpha * xh[c] - K.beta * ec[c]);
             nz2 += z[c] * z[c];
         }
-        const T nz = Real<T>::sqrt_(nz2);
-        const T scale = (nz > gm) ? gm / nz : T(1);
+        const T scale = Proj<T>::scale(nz2, gm);
         T dvde = T(0), dede = T(0), dvdv = T(0), vv = T(0), ee = T(0);
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
             const T vn = z[c] * scale;
             const T en = (z[c] - vn) * K.irho;
-            const T dv = vn - vc[c], de = en - ec[c];
-            dvde += dv * de;
-            dede += de * de;
-            dvdv += dv * dv;
-            vv += vn * vn;
-            ee += en * en;
+            if (RULE == 0 || RULE == -1) {
+                const T dv = vn - vc[c], de = en - ec[c];
+                dvde += dv * de;
+                dede += de * de;
+                dvdv += dv * dv;
+            }
+            if (RULE == 2 || RULE == -1) {
+                vv += vn * vn;
+                ee += en * en;
+            }
             eo[c] = en;
             vo[c] = vn;
         }
@@ -879,8 +903,30 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
 // (e0, v0 at plane i-1; e3, v3 at plane i+1; phi at i-1, i+1).
 __host__ __device__ inline long long tma_stage_elems(int TV, int n3) { return 20LL * TV + 6LL * n3; }
 
-template <typename T>
+// Vector of VW = 8 / sizeof(T) values (float2 for FP32, one double for FP64)
+// read from shared memory in one access.
+template <typename T> struct Vec8;
+template <> struct Vec8<float> {
+    static constexpr int W = 2;
+    __device__ __forceinline__ static void ld(const float* p, float (&o)[2]) {
+        const float2 t = *reinterpret_cast<const float2*>(p);
+        o[0] = t.x;
+        o[1] = t.y;
+    }
+    __device__ __forceinline__ static void st(float* p, const float (&o)[2]) {
+        *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
+    }
+};
+template <> struct Vec8<double> {
+    static constexpr int W = 1;
+    __device__ __forceinline__ static void ld(const double* p, double (&o)[1]) { o[0] = *p; }
+    __device__ __forceinline__ static void st(double* p, const double (&o)[1]) { *p = o[0]; }
+};
+
+template <typename T, int RULE>
 __global__ void __launch_bounds__(kThreads, 2) k_update_tma(Geom g, Ptrs<T> p, LoopConfig cfg, int J) {
+    using V = Vec8<T>;
+    constexpr int W = V::W;
     const int s = blockIdx.y;
     SolveScalars& S = p.sc[s];
     if (!S.active) return;
@@ -961,6 +1007,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_update_tma(Geom g, Ptrs<T> p, L
     unsigned phase0 = 0, phase1 = 0;
     int it = 0;
     bool failed = false;
+    const int ngroups = TV / W;
     for (int tile = t0; tile < ntiles; tile += tstep, ++it) {
         const int st = it & 1;
         const unsigned ph = st ? phase1 : phase0;
@@ -977,31 +1024,68 @@ __global__ void __launch_bounds__(kThreads, 2) k_update_tma(Geom g, Ptrs<T> p, L
         const int i = tile / tiles_j;
         const int j0 = (tile - i * tiles_j) * J;
         const long long base = ((long long)i * g.n2 + j0) * n3;
-        for (int lv = threadIdx.x; lv < TV; lv += kThreads) {
-            const int r = (int)fdiv((unsigned)lv, g.div_n3);
-            const int k = lv - r * n3;
-            const int kp = (k + 1 == n3) ? 0 : k + 1, km = (k == 0) ? n3 - 1 : k - 1;
-            const int lzp = r * n3 + kp, lzm = r * n3 + km;
-            T ec[6], vc[6];
-#pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                ec[c] = own[c * TV + lv];
-                vc[c] = own[(6 + c) * TV + lv];
-            }
+        for (int gi = threadIdx.x; gi < ngroups; gi += kThreads) {
+            const int lv0 = gi * W;
+            const int r = (int)fdiv((unsigned)lv0, g.div_n3);
+            const int k0 = lv0 - r * n3;
+            const int kp = (k0 + W == n3) ? 0 : k0 + W, km = (k0 == 0) ? n3 - 1 : k0 - 1;
             const bool top = (r + 1 == J), bot = (r == 0);
-            const T php[3] = {xn[5 * TV + lv], top ? yh[5 * n3 + k] : own[13 * TV + lv + n3], own[13 * TV + lzp]};
-            const T phm[3] = {xn[4 * TV + lv], bot ? yh[4 * n3 + k] : own[13 * TV + lv - n3], own[13 * TV + lzm]};
-            const T e2p[3] = {xn[2 * TV + lv], top ? yh[2 * n3 + k] : own[4 * TV + lv + n3], own[5 * TV + lzp]};
-            const T v2p[3] = {xn[3 * TV + lv], top ? yh[3 * n3 + k] : own[10 * TV + lv + n3], own[11 * TV + lzp]};
-            const T e1m[3] = {xn[0 * TV + lv], bot ? yh[0 * n3 + k] : own[1 * TV + lv - n3], own[2 * TV + lzm]};
-            const T v1m[3] = {xn[1 * TV + lv], bot ? yh[1 * n3 + k] : own[7 * TV + lv - n3], own[8 * TV + lzm]};
-            T eo[6], vo[6], fl[3];
-            voxel_step<T, false>(K, ec, vc, own[12 * TV + lv], own[13 * TV + lv], php, phm, e2p, v2p, e1m, v1m, acc,
-                                 eo, vo, fl);
+            // W-wide reads of every field this group needs
+            T ec[6][W], vc[6][W], gm[W], ph[W];
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
-                e_out[c * N + base + lv] = eo[c];
-                v_out[c * N + base + lv] = vo[c];
+                V::ld(own + c * TV + lv0, ec[c]);
+                V::ld(own + (6 + c) * TV + lv0, vc[c]);
+            }
+            V::ld(own + 12 * TV + lv0, gm);
+            V::ld(own + 13 * TV + lv0, ph);
+            T e2x[W], v2x[W], e1x[W], v1x[W], phxp[W], phxm[W];
+            V::ld(xn + 2 * TV + lv0, e2x);
+            V::ld(xn + 3 * TV + lv0, v2x);
+            V::ld(xn + 0 * TV + lv0, e1x);
+            V::ld(xn + 1 * TV + lv0, v1x);
+            V::ld(xn + 5 * TV + lv0, phxp);
+            V::ld(xn + 4 * TV + lv0, phxm);
+            T e2y[W], v2y[W], e1y[W], v1y[W], phyp[W], phym[W];
+            V::ld(top ? yh + 2 * n3 + k0 : own + 4 * TV + lv0 + n3, e2y);
+            V::ld(top ? yh + 3 * n3 + k0 : own + 10 * TV + lv0 + n3, v2y);
+            V::ld(bot ? yh + 0 * n3 + k0 : own + 1 * TV + lv0 - n3, e1y);
+            V::ld(bot ? yh + 1 * n3 + k0 : own + 7 * TV + lv0 - n3, v1y);
+            V::ld(top ? yh + 5 * n3 + k0 : own + 13 * TV + lv0 + n3, phyp);
+            V::ld(bot ? yh + 4 * n3 + k0 : own + 13 * TV + lv0 - n3, phym);
+            const int rz = r * n3;
+            const T e2z_after = own[5 * TV + rz + kp], v2z_after = own[11 * TV + rz + kp];
+            const T e1z_before = own[2 * TV + rz + km], v1z_before = own[8 * TV + rz + km];
+            const T ph_after = own[13 * TV + rz + kp], ph_before = own[13 * TV + rz + km];
+            T eo[6][W], vo[6][W];
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                T ecu[6], vcu[6];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+                    ecu[c] = ec[c][u];
+                    vcu[c] = vc[c][u];
+                }
+                const bool last = (u + 1 == W), first = (u == 0);
+                const T php[3] = {phxp[u], phyp[u], last ? ph_after : ph[(u + 1) % W]};
+                const T phm[3] = {phxm[u], phym[u], first ? ph_before : ph[(u + W - 1) % W]};
+                const T e2p[3] = {e2x[u], e2y[u], last ? e2z_after : ec[5][(u + 1) % W]};
+                const T v2p[3] = {v2x[u], v2y[u], last ? v2z_after : vc[5][(u + 1) % W]};
+                const T e1m[3] = {e1x[u], e1y[u], first ? e1z_before : ec[2][(u + W - 1) % W]};
+                const T v1m[3] = {v1x[u], v1y[u], first ? v1z_before : vc[2][(u + W - 1) % W]};
+                T eou[6], vou[6], fl[3];
+                voxel_step<T, false, RULE>(K, ecu, vcu, gm[u], ph[u], php, phm, e2p, v2p, e1m, v1m, acc, eou, vou,
+                                           fl);
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+                    eo[c][u] = eou[c];
+                    vo[c][u] = vou[c];
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                V::st(e_out + c * N + base + lv0, eo[c]);
+                V::st(v_out + c * N + base + lv0, vo[c]);
             }
         }
         __syncthreads();   // every thread is done with this stage

@@ -69,7 +69,11 @@ cudaError_t configure_kernels(const LaunchShape& sh) {
         set((const void*)k_fft_strided<T, 2, LN>, sh.smem_y);
     });
     CCMF_DISPATCH_LINES(sh.lpb_x, { set((const void*)k_fft_strided<T, 1, LN>, sh.smem_x); });
-    if (sh.tma_rows > 0) set((const void*)k_update_tma<T>, sh.smem_tma);
+    if (sh.tma_rows > 0) {
+        set((const void*)k_update_tma<T, 0>, sh.smem_tma);
+        set((const void*)k_update_tma<T, 1>, sh.smem_tma);
+        set((const void*)k_update_tma<T, 2>, sh.smem_tma);
+    }
     return err;
 }
 
@@ -120,9 +124,15 @@ void launch_passes(const Ctx<T>& c, const Ptrs<T>& p, cudaStream_t st, F&& betwe
     between(kKIrfftZ);
     if (OUT)
         k_update<T, true><<<gu, kThreads, 0, st>>>(g, p, c.cfg);
-    else if (c.vec_update && sh.tma_rows > 0)
-        k_update_tma<T><<<dim3((unsigned)sh.grid_tma, (unsigned)g.batch), kThreads, sh.smem_tma, st>>>(
-            g, p, c.cfg, sh.tma_rows);
+    else if (c.vec_update && sh.tma_rows > 0) {
+        const dim3 gt((unsigned)sh.grid_tma, (unsigned)g.batch);
+        if (c.cfg.rho_rule == 0)
+            k_update_tma<T, 0><<<gt, kThreads, sh.smem_tma, st>>>(g, p, c.cfg, sh.tma_rows);
+        else if (c.cfg.rho_rule == 2)
+            k_update_tma<T, 2><<<gt, kThreads, sh.smem_tma, st>>>(g, p, c.cfg, sh.tma_rows);
+        else
+            k_update_tma<T, 1><<<gt, kThreads, sh.smem_tma, st>>>(g, p, c.cfg, sh.tma_rows);
+    }
     else if (c.vec_update)
         k_update_vec<T><<<gu, kThreads, 0, st>>>(g, p, c.cfg);
     else

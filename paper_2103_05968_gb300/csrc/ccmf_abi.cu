@@ -16,6 +16,7 @@ using namespace ccmf;
 
 namespace ccmf {
 template <typename T> cudaError_t configure_kernels(const LaunchShape&);
+template <typename T> int pipe_blocks_per_sm(int, size_t);
 template <typename T> void launch_init(const Ctx<T>&, cudaStream_t);
 template <typename T> void launch_iteration(const Ctx<T>&, cudaStream_t);
 template <typename T> void launch_iteration_timed(const Ctx<T>&, cudaStream_t, cudaEvent_t*);
@@ -27,6 +28,7 @@ namespace {
 constexpr int kMaxN = 1024;
 constexpr size_t kSmemBudget = 96 * 1024;
 constexpr int kMaxTimedIters = 2048;
+constexpr int kDefaultUpdateVariant = 2;
 constexpr double kPi = 3.14159265358979323846264338327950288;
 
 size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
@@ -426,7 +428,32 @@ int ccmf_plan_create(int n1, int n2, int n3, int batch, int precision, ccmf_plan
         if (gt > ntiles) gt = ntiles;
         if (gt < 1) gt = 1;
         sh.grid_tma = (int)gt;
+        // pipelined update: a tile is one W-group per thread, TV = threads * W voxels = whole z rows
+        const char* env = getenv("CCMF_UPDATE_VARIANT");
+        int variant = env ? atoi(env) : kDefaultUpdateVariant;
+        if (variant < 0 || variant > 5) variant = kDefaultUpdateVariant;
+        sh.upd_variant = 0;
+        if (variant >= 2) {
+            const int vw = precision == CCMF_FP64 ? 1 : 2;
+            const int tv = kUpdatePipe[variant][0] * vw;
+            const int stages = kUpdatePipe[variant][1];
+            if (n3 % W == 0 && tv % n3 == 0 && n2 % (tv / n3) == 0) {
+                const size_t smem = (size_t)stages * (size_t)tma_stage_elems(tv, n3) * pl->esize + 8 * stages;
+                const int nb = precision == CCMF_FP64 ? pipe_blocks_per_sm<double>(variant, smem)
+                                                      : pipe_blocks_per_sm<float>(variant, smem);
+                if (nb > 0) {
+                    sh.upd_variant = variant;
+                    sh.smem_pipe = smem;
+                    long long nt = (long long)n1 * (n2 / (tv / n3));
+                    long long gp = ((long long)nb * sms + batch - 1) / batch;
+                    if (gp > nt) gp = nt;
+                    sh.grid_pipe = (int)(gp < 1 ? 1 : gp);
+                }
+            }
+        }
+        if (sh.upd_variant == 0 && variant >= 1 && sh.tma_rows > 0) sh.upd_variant = 1;
         sh.grid_partials = sh.grid_update > sh.grid_tma ? sh.grid_update : sh.grid_tma;
+        if (sh.grid_pipe > sh.grid_partials) sh.grid_partials = sh.grid_pipe;
     }
 
     // workspace layout

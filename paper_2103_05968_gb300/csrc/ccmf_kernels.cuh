@@ -45,10 +45,10 @@ __device__ __forceinline__ T warp_sum(T x) {
 // Block reduction of kNSum per-thread values (T) into one double each, written
 // to partial[b * kNSum + q]; returns true in every thread of the block that
 // finishes last for this solve (its partials are then visible to it).
-template <typename T, int NQ>
+template <typename T, int NQ, int NT = kThreads>
 __device__ bool block_partials(T (&acc)[NQ], double* __restrict__ partial, unsigned int* counter,
                                int nblocks, int b) {
-    __shared__ double red[kThreads / 32][NQ];
+    __shared__ double red[NT / 32][NQ];
     __shared__ int last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -59,7 +59,7 @@ __device__ bool block_partials(T (&acc)[NQ], double* __restrict__ partial, unsig
     __syncthreads();
     if (threadIdx.x < NQ) {
         double s = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) s += red[w][threadIdx.x];
+        for (int w = 0; w < NT / 32; ++w) s += red[w][threadIdx.x];
         partial[(size_t)b * NQ + threadIdx.x] = s;
     }
     __threadfence();
@@ -73,14 +73,14 @@ __device__ bool block_partials(T (&acc)[NQ], double* __restrict__ partial, unsig
 }
 
 // Deterministic double reduction of nblocks x NQ partials by one block.
-template <int NQ>
+template <int NQ, int NT = kThreads>
 __device__ void reduce_partials(const double* __restrict__ partial, int nblocks, double (&out)[NQ]) {
-    __shared__ double red[kThreads / 32][NQ];
+    __shared__ double red[NT / 32][NQ];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
         double s = 0.0;
-        for (int b = threadIdx.x; b < nblocks; b += kThreads) s += __ldcg(partial + (size_t)b * NQ + q);
+        for (int b = threadIdx.x; b < nblocks; b += NT) s += __ldcg(partial + (size_t)b * NQ + q);
         s = warp_sum(s);
         if (lane == 0) red[wid][q] = s;
     }
@@ -88,7 +88,7 @@ __device__ void reduce_partials(const double* __restrict__ partial, int nblocks,
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
         double s = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) s += red[w][q];
+        for (int w = 0; w < NT / 32; ++w) s += red[w][q];
         out[q] = s;
     }
 }
@@ -593,15 +593,15 @@ __device__ __forceinline__ void voxel_step(const StepConsts<T>& K, const T (&ec)
 
 // Reduction epilogue of the update pass: block partials, then the last block of
 // the solve reduces them in double and runs the penalty / history / stop logic.
-template <typename T, bool OUT>
+template <typename T, bool OUT, int NT = kThreads>
 __device__ void update_epilogue(const Geom& g, const Ptrs<T>& p, const LoopConfig& cfg, SolveScalars& S, int s,
                                 double rho_d, T (&acc)[kNSum]) {
     const int nblocks = gridDim.x;
     double* part = p.partial + (size_t)s * nblocks * kNSum;
-    const bool last = block_partials<T, kNSum>(acc, part, &S.counter, nblocks, blockIdx.x);
+    const bool last = block_partials<T, kNSum, NT>(acc, part, &S.counter, nblocks, blockIdx.x);
     if (!last) return;
     double sums[kNSum];
-    reduce_partials<kNSum>(part, nblocks, sums);
+    reduce_partials<kNSum, NT>(part, nblocks, sums);
     if (threadIdx.x != 0) return;
     S.counter = 0;
     const double Nd = (double)g.N;
@@ -1107,6 +1107,195 @@ __global__ void __launch_bounds__(kThreads, 2) k_update_tma(Geom g, Ptrs<T> p, L
         __syncthreads();
     }
     update_epilogue<T, false>(g, p, cfg, S, s, rho_d, acc);
+}
+
+// Pipelined variant: NT threads, each owning one W-wide group of every tile
+// (TV = NT * W voxels = J whole z rows, J = TV / N3 dividing N2), so that all
+// per-thread index arithmetic is fixed for the whole kernel; STAGES tiles are
+// in flight. Same copies, waits and arithmetic as k_update_tma.
+template <typename T, int RULE, int STAGES, int NT>
+__global__ void __launch_bounds__(NT) k_update_pipe(Geom g, Ptrs<T> p, LoopConfig cfg) {
+    using V = Vec8<T>;
+    constexpr int W = V::W;
+    constexpr int TV = NT * W;
+    const int s = blockIdx.y;
+    SolveScalars& S = p.sc[s];
+    if (!S.active) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n3 = g.n3;
+    const int J = TV / n3;
+    const long long selems = tma_stage_elems(TV, n3);
+    T* stages = reinterpret_cast<T*>(smem_raw);
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(stages + STAGES * selems);
+    const unsigned stage_bytes = (unsigned)(selems * sizeof(T));
+    constexpr unsigned tv_bytes = (unsigned)(TV * sizeof(T));
+    const unsigned row_bytes = (unsigned)(n3 * sizeof(T));
+
+    const long long N = g.N;
+    const double rho_d = S.rho;
+    const StepConsts<T> K = step_consts<T>(S, cfg);
+    const int par = S.iters & 1;
+    const T* __restrict__ e = p.e + (long long)par * p.sstride + (long long)s * 6 * N;
+    const T* __restrict__ v = p.v + (long long)par * p.sstride + (long long)s * 6 * N;
+    T* __restrict__ e_out = p.e + (long long)(1 - par) * p.sstride + (long long)s * 6 * N;
+    T* __restrict__ v_out = p.v + (long long)(1 - par) * p.sstride + (long long)s * 6 * N;
+    const T* __restrict__ phi = p.phi + (size_t)s * N;
+    const T* __restrict__ gam = p.gamma + (size_t)s * p.gstride;
+    const int tiles_j = g.n2 / J;
+    const int ntiles = g.n1 * tiles_j;
+
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < STAGES; ++q) mbar_init(&bars[q], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int tile, int st) {
+        T* b = stages + st * selems;
+        const int i = tile / tiles_j;
+        const int j0 = (tile - i * tiles_j) * J;
+        const int ip = (i + 1 == g.n1) ? 0 : i + 1, im = (i == 0) ? g.n1 - 1 : i - 1;
+        const int jp = (j0 + J == g.n2) ? 0 : j0 + J, jm = (j0 == 0) ? g.n2 - 1 : j0 - 1;
+        const long long base = ((long long)i * g.n2 + j0) * n3;
+        const long long bip = ((long long)ip * g.n2 + j0) * n3, bim = ((long long)im * g.n2 + j0) * n3;
+        const long long rjp = ((long long)i * g.n2 + jp) * n3, rjm = ((long long)i * g.n2 + jm) * n3;
+        unsigned long long* bar = &bars[st];
+        mbar_expect_tx(bar, stage_bytes);
+        T* own = b;
+        T* yh = b + 14 * TV;
+        T* xn = yh + 6LL * n3;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            bulk_g2s(own + c * TV, e + c * N + base, tv_bytes, bar);
+            bulk_g2s(own + (6 + c) * TV, v + c * N + base, tv_bytes, bar);
+        }
+        bulk_g2s(own + 12 * TV, gam + base, tv_bytes, bar);
+        bulk_g2s(own + 13 * TV, phi + base, tv_bytes, bar);
+        bulk_g2s(yh + 0LL * n3, e + 1 * N + rjm, row_bytes, bar);
+        bulk_g2s(yh + 1LL * n3, v + 1 * N + rjm, row_bytes, bar);
+        bulk_g2s(yh + 2LL * n3, e + 4 * N + rjp, row_bytes, bar);
+        bulk_g2s(yh + 3LL * n3, v + 4 * N + rjp, row_bytes, bar);
+        bulk_g2s(yh + 4LL * n3, phi + rjm, row_bytes, bar);
+        bulk_g2s(yh + 5LL * n3, phi + rjp, row_bytes, bar);
+        bulk_g2s(xn + 0 * TV, e + 0 * N + bim, tv_bytes, bar);
+        bulk_g2s(xn + 1 * TV, v + 0 * N + bim, tv_bytes, bar);
+        bulk_g2s(xn + 2 * TV, e + 3 * N + bip, tv_bytes, bar);
+        bulk_g2s(xn + 3 * TV, v + 3 * N + bip, tv_bytes, bar);
+        bulk_g2s(xn + 4 * TV, phi + bim, tv_bytes, bar);
+        bulk_g2s(xn + 5 * TV, phi + bip, tv_bytes, bar);
+    };
+
+    const int t0 = blockIdx.x;
+    const int tstep = gridDim.x;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < STAGES; ++q)
+            if (t0 + q * tstep < ntiles) issue(t0 + q * tstep, q);
+    }
+    // this thread's group: fixed offsets for the whole kernel
+    const int lv0 = threadIdx.x * W;
+    const int r = lv0 / n3;
+    const int k0 = lv0 - r * n3;
+    const int kp = (k0 + W == n3) ? 0 : k0 + W, km = (k0 == 0) ? n3 - 1 : k0 - 1;
+    const int rz = r * n3;
+    const bool top = (r + 1 == J), bot = (r == 0);
+    const int o_e2y = top ? 14 * TV + 2 * n3 + k0 : 4 * TV + lv0 + n3;
+    const int o_v2y = top ? 14 * TV + 3 * n3 + k0 : 10 * TV + lv0 + n3;
+    const int o_e1y = bot ? 14 * TV + 0 * n3 + k0 : 1 * TV + lv0 - n3;
+    const int o_v1y = bot ? 14 * TV + 1 * n3 + k0 : 7 * TV + lv0 - n3;
+    const int o_pyp = top ? 14 * TV + 5 * n3 + k0 : 13 * TV + lv0 + n3;
+    const int o_pym = bot ? 14 * TV + 4 * n3 + k0 : 13 * TV + lv0 - n3;
+    const int xo = 14 * TV + 6 * n3 + lv0;   // xn[0] at this group
+
+    T acc[kNSum];
+#pragma unroll
+    for (int q = 0; q < kNSum; ++q) acc[q] = T(0);
+    int it = 0;
+    bool failed = false;
+    for (int tile = t0; tile < ntiles; tile += tstep, ++it) {
+        const int st = it % STAGES;
+        const unsigned ph = (unsigned)(it / STAGES) & 1u;
+        const bool ok = mbar_wait_bounded(&bars[st], ph);
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        const T* b = stages + st * selems;
+        T ec[6][W], vc[6][W], gm[W], ph_[W];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            V::ld(b + c * TV + lv0, ec[c]);
+            V::ld(b + (6 + c) * TV + lv0, vc[c]);
+        }
+        V::ld(b + 12 * TV + lv0, gm);
+        V::ld(b + 13 * TV + lv0, ph_);
+        T e2x[W], v2x[W], e1x[W], v1x[W], phxp[W], phxm[W];
+        V::ld(b + xo + 2 * TV, e2x);
+        V::ld(b + xo + 3 * TV, v2x);
+        V::ld(b + xo + 0 * TV, e1x);
+        V::ld(b + xo + 1 * TV, v1x);
+        V::ld(b + xo + 5 * TV, phxp);
+        V::ld(b + xo + 4 * TV, phxm);
+        T e2y[W], v2y[W], e1y[W], v1y[W], phyp[W], phym[W];
+        V::ld(b + o_e2y, e2y);
+        V::ld(b + o_v2y, v2y);
+        V::ld(b + o_e1y, e1y);
+        V::ld(b + o_v1y, v1y);
+        V::ld(b + o_pyp, phyp);
+        V::ld(b + o_pym, phym);
+        const T e2z_after = b[5 * TV + rz + kp], v2z_after = b[11 * TV + rz + kp];
+        const T e1z_before = b[2 * TV + rz + km], v1z_before = b[8 * TV + rz + km];
+        const T ph_after = b[13 * TV + rz + kp], ph_before = b[13 * TV + rz + km];
+        __syncthreads();   // the stage has been read into registers: refill it
+        if (threadIdx.x == 0 && tile + STAGES * tstep < ntiles) {
+            fence_proxy_async_smem();
+            issue(tile + STAGES * tstep, st);
+        }
+        const int i = tile / tiles_j;
+        const int j0 = (tile - i * tiles_j) * J;
+        const long long gbase = ((long long)i * g.n2 + j0) * n3 + lv0;
+        T eo[6][W], vo[6][W];
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+            T ecu[6], vcu[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                ecu[c] = ec[c][u];
+                vcu[c] = vc[c][u];
+            }
+            const bool last = (u + 1 == W), first = (u == 0);
+            const T php[3] = {phxp[u], phyp[u], last ? ph_after : ph_[(u + 1) % W]};
+            const T phm[3] = {phxm[u], phym[u], first ? ph_before : ph_[(u + W - 1) % W]};
+            const T e2p[3] = {e2x[u], e2y[u], last ? e2z_after : ec[5][(u + 1) % W]};
+            const T v2p[3] = {v2x[u], v2y[u], last ? v2z_after : vc[5][(u + 1) % W]};
+            const T e1m[3] = {e1x[u], e1y[u], first ? e1z_before : ec[2][(u + W - 1) % W]};
+            const T v1m[3] = {v1x[u], v1y[u], first ? v1z_before : vc[2][(u + W - 1) % W]};
+            T eou[6], vou[6], fl[3];
+            voxel_step<T, false, RULE>(K, ecu, vcu, gm[u], ph_[u], php, phm, e2p, v2p, e1m, v1m, acc, eou, vou, fl);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                eo[c][u] = eou[c];
+                vo[c][u] = vou[c];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            V::st(e_out + c * N + gbase, eo[c]);
+            V::st(v_out + c * N + gbase, vo[c]);
+        }
+    }
+    if (failed) {
+        if (threadIdx.x == 0) {
+            for (int extra = 0; extra < STAGES; ++extra) {
+                const int n = it + extra;
+                if (t0 + n * tstep < ntiles) (void)mbar_wait_bounded(&bars[n % STAGES], (unsigned)(n / STAGES) & 1u);
+            }
+            atomicExch(&S.status, 6);   // CCMF_ERR_TIMEOUT
+        }
+        __syncthreads();
+    }
+    update_epilogue<T, false, NT>(g, p, cfg, S, s, rho_d, acc);
 }
 
 }  // namespace ccmf

@@ -52,6 +52,30 @@ inline long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
         default: { constexpr int LN = 1; __VA_ARGS__; } break;  \
     }
 
+// Runs the statement list with compile-time ST (stages) and NTH (threads) of a
+// pipelined update variant 2..5.
+#define CCMF_DISPATCH_PIPE(VAR, ...)                                                 \
+    switch (VAR) {                                                                   \
+        case 2: { constexpr int NTH = 256, ST = 2; __VA_ARGS__; } break;            \
+        case 3: { constexpr int NTH = 128, ST = 3; __VA_ARGS__; } break;            \
+        case 4: { constexpr int NTH = 128, ST = 4; __VA_ARGS__; } break;            \
+        default: { constexpr int NTH = 256, ST = 3; __VA_ARGS__; } break;           \
+    }
+
+// Blocks per SM of a pipelined update variant (occupancy API), 0 on error.
+template <typename T>
+int pipe_blocks_per_sm(int variant, size_t smem) {
+    int nb = 0;
+    cudaError_t err = cudaSuccess;
+    CCMF_DISPATCH_PIPE(variant, {
+        err = cudaFuncSetAttribute((const void*)k_update_pipe<T, 0, ST, NTH>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err == cudaSuccess)
+            err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_update_pipe<T, 0, ST, NTH>, NTH, smem);
+    });
+    return err == cudaSuccess ? nb : 0;
+}
+
 template <typename T>
 cudaError_t configure_kernels(const LaunchShape& sh) {
     cudaError_t err = cudaSuccess;
@@ -73,6 +97,13 @@ cudaError_t configure_kernels(const LaunchShape& sh) {
         set((const void*)k_update_tma<T, 0>, sh.smem_tma);
         set((const void*)k_update_tma<T, 1>, sh.smem_tma);
         set((const void*)k_update_tma<T, 2>, sh.smem_tma);
+    }
+    if (sh.upd_variant >= 2) {
+        CCMF_DISPATCH_PIPE(sh.upd_variant, {
+            set((const void*)k_update_pipe<T, 0, ST, NTH>, sh.smem_pipe);
+            set((const void*)k_update_pipe<T, 1, ST, NTH>, sh.smem_pipe);
+            set((const void*)k_update_pipe<T, 2, ST, NTH>, sh.smem_pipe);
+        });
     }
     return err;
 }
@@ -124,7 +155,17 @@ void launch_passes(const Ctx<T>& c, const Ptrs<T>& p, cudaStream_t st, F&& betwe
     between(kKIrfftZ);
     if (OUT)
         k_update<T, true><<<gu, kThreads, 0, st>>>(g, p, c.cfg);
-    else if (c.vec_update && sh.tma_rows > 0) {
+    else if (c.vec_update && sh.upd_variant >= 2) {
+        const dim3 gp((unsigned)sh.grid_pipe, (unsigned)g.batch);
+        CCMF_DISPATCH_PIPE(sh.upd_variant, {
+            if (c.cfg.rho_rule == 0)
+                k_update_pipe<T, 0, ST, NTH><<<gp, NTH, sh.smem_pipe, st>>>(g, p, c.cfg);
+            else if (c.cfg.rho_rule == 2)
+                k_update_pipe<T, 2, ST, NTH><<<gp, NTH, sh.smem_pipe, st>>>(g, p, c.cfg);
+            else
+                k_update_pipe<T, 1, ST, NTH><<<gp, NTH, sh.smem_pipe, st>>>(g, p, c.cfg);
+        });
+    } else if (c.vec_update && sh.upd_variant == 1 && sh.tma_rows > 0) {
         const dim3 gt((unsigned)sh.grid_tma, (unsigned)g.batch);
         if (c.cfg.rho_rule == 0)
             k_update_tma<T, 0><<<gt, kThreads, sh.smem_tma, st>>>(g, p, c.cfg, sh.tma_rows);

@@ -82,6 +82,13 @@ struct LaunchShape {
     int grid_tma;             // blocks per solve of the TMA-staged update
     size_t smem_tma;          // its dynamic shared memory (two stages + barriers)
     int grid_partials;        // partial-sum slots per solve (max of the update grids)
+    int upd_variant;          // update pass: 0 register vectors, 1 TMA (2 stages, any tile),
+                              // 2..5 pipelined TMA (see kUpdatePipe)
+    int grid_pipe;            // blocks per solve of the pipelined update
+    size_t smem_pipe;         // its dynamic shared memory
 };
+
+// Pipelined update variants: {threads per block, stages}.
+constexpr int kUpdatePipe[6][2] = {{0, 0}, {0, 0}, {256, 2}, {128, 3}, {128, 4}, {256, 3}};
 
 }  // namespace ccmf

@@ -28,7 +28,11 @@ namespace {
 constexpr int kMaxN = 1024;
 constexpr size_t kSmemBudget = 96 * 1024;
 constexpr int kMaxTimedIters = 2048;
-constexpr int kDefaultUpdateVariant = 2;
+// update-pass variant per precision, from measurements on GB300 (128^3 x 3 solves):
+// FP32 is bandwidth-bound and best with the 3-stage TMA pipeline of 128 threads,
+// FP64 is ALU-bound and best with register vectors
+constexpr int kDefaultUpdateVariantF32 = 3;
+constexpr int kDefaultUpdateVariantF64 = 0;
 constexpr double kPi = 3.14159265358979323846264338327950288;
 
 size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
@@ -57,11 +61,28 @@ bool make_axis_plan(int n, AxisPlan* ap) {
         if (!push(5)) return false;
     ap->nst = st;
     unsigned ns = 1;
+    int span = n;
     for (int t = 0; t < st; ++t) {
         ap->ns[t] = make_fastdiv(ns);
         ns *= (unsigned)ap->rad[t];
+        ap->span[t] = span;
+        ap->sub[t] = make_fastdiv((unsigned)(span / ap->rad[t]));
+        span /= ap->rad[t];
     }
     return m == 1;
+}
+
+// Frequency held by slot p after the in-place decimation-in-frequency stages:
+// k(p) = sum_s q_s prod_{t<s} R_t with q_s = (p / m_s) mod R_s.
+int digit_reversed_frequency(const AxisPlan& ap, int p) {
+    int k = 0, w = 1;
+    for (int t = 0; t < ap.nst; ++t) {
+        const int m = ap.span[t] / ap.rad[t];
+        const int q = (p / m) % ap.rad[t];
+        k += q * w;
+        w *= ap.rad[t];
+    }
+    return k;
 }
 
 // Largest power of two <= min(cap, x), at least 1.
@@ -89,6 +110,7 @@ struct ccmf_plan {
     LaunchShape sh;
     void* tw[3];
     void* sym[3];
+    void* rsym[2];   // x, y symbol tables in digit-reversed order
     // workspace layout
     size_t off_sc, off_nact, off_xi, off_part, off_hist, off_e, off_v, off_spec, off_phi, off_gam, off_cut,
         off_flow, total;
@@ -111,6 +133,7 @@ namespace {
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? CCMF_OK : CCMF_ERR_CUDA; }
 
+
 bool is_device_ptr(const void* ptr) {
     if (!ptr) return false;
     cudaPointerAttributes a;
@@ -132,6 +155,8 @@ Ctx<T> make_ctx(const ccmf_plan* pl, unsigned char* ws, const T* gamma, long lon
         c.tw[a] = reinterpret_cast<const cx<T>*>(pl->tw[a]);
         c.sym[a] = reinterpret_cast<const T*>(pl->sym[a]);
     }
+    c.rsym[0] = reinterpret_cast<const T*>(pl->rsym[0]);
+    c.rsym[1] = reinterpret_cast<const T*>(pl->rsym[1]);
     c.sh = pl->sh;
     c.xi_stage = reinterpret_cast<const double*>(ws + pl->off_xi);
     c.p.sc = reinterpret_cast<SolveScalars*>(ws + pl->off_sc);
@@ -163,8 +188,10 @@ template <typename T>
 int capture_loop(ccmf_plan* pl, const Ctx<T>& c, const GraphKey& key) {
     if (pl->have_graph && memcmp(&pl->gkey, &key, sizeof(key)) == 0) return CCMF_OK;
     destroy_graph(pl);
+    int cls[kNumKernelClasses];
+    const int nk = iteration_classes(pl->sh, cls);
     if (key.timed) {
-        size_t need = (size_t)key.chunk * kNumKernelClasses + 1;
+        size_t need = (size_t)key.chunk * nk + 1;
         while (pl->events.size() < need) {
             cudaEvent_t ev;
             if (cudaEventCreate(&ev) != cudaSuccess) return CCMF_ERR_CUDA;
@@ -177,7 +204,7 @@ int capture_loop(ccmf_plan* pl, const Ctx<T>& c, const GraphKey& key) {
     if (key.timed) cudaEventRecordWithFlags(pl->events[0], pl->cap_stream, cudaEventRecordExternal);
     for (int it = 0; it < key.chunk; ++it) {
         if (key.timed)
-            launch_iteration_timed<T>(c, pl->cap_stream, pl->events.data() + (size_t)it * kNumKernelClasses);
+            launch_iteration_timed<T>(c, pl->cap_stream, pl->events.data() + (size_t)it * nk);
         else
             launch_iteration<T>(c, pl->cap_stream);
     }
@@ -263,7 +290,8 @@ int solve_impl(ccmf_plan* pl, const void* gamma_in, long long gstride_in, const 
     pl->launches_last = 0;
     for (long long ch = 0; ch < nchunks_max; ++ch) {
         if (cudaGraphLaunch(pl->gexec, st) != cudaSuccess) return CCMF_ERR_CUDA;
-        pl->launches_last += (long long)chunk * kNumKernelClasses;
+        int cls_tmp[kNumKernelClasses];
+        pl->launches_last += (long long)chunk * iteration_classes(pl->sh, cls_tmp);
         if (!fixed) {
             if (cudaMemcpyAsync(pl->h_nactive, ws + pl->off_nact, sizeof(int), cudaMemcpyDeviceToHost, st) !=
                 cudaSuccess)
@@ -312,13 +340,15 @@ int solve_impl(ccmf_plan* pl, const void* gamma_in, long long gstride_in, const 
             pl->kms[k] = 0.0;
             pl->klaunch[k] = 0;
         }
+        int cls[kNumKernelClasses];
+        const int nk = iteration_classes(pl->sh, cls);
         for (int it = 0; it < chunk; ++it)
-            for (int k = 0; k < kNumKernelClasses; ++k) {
+            for (int k = 0; k < nk; ++k) {
                 float ms = 0.f;
-                size_t a = (size_t)it * kNumKernelClasses + k;
+                size_t a = (size_t)it * nk + k;
                 if (cudaEventElapsedTime(&ms, pl->events[a], pl->events[a + 1]) == cudaSuccess) {
-                    pl->kms[k] += ms;
-                    pl->klaunch[k] += 1;
+                    pl->kms[cls[k]] += ms;
+                    pl->klaunch[cls[k]] += 1;
                 }
             }
         pl->timed_iters = chunk;
@@ -391,6 +421,7 @@ int ccmf_plan_create(int n1, int n2, int n3, int batch, int precision, ccmf_plan
     g.div_n3 = make_fastdiv((unsigned)n3);
     g.div_n2 = make_fastdiv((unsigned)n2);
     g.div_n3h = make_fastdiv((unsigned)pl->n3h);
+    g.div_n1 = make_fastdiv((unsigned)n1);
 
     // launch shape
     const size_t cs = 2 * pl->esize;  // complex element
@@ -430,8 +461,9 @@ int ccmf_plan_create(int n1, int n2, int n3, int batch, int precision, ccmf_plan
         sh.grid_tma = (int)gt;
         // pipelined update: a tile is one W-group per thread, TV = threads * W voxels = whole z rows
         const char* env = getenv("CCMF_UPDATE_VARIANT");
-        int variant = env ? atoi(env) : kDefaultUpdateVariant;
-        if (variant < 0 || variant > 5) variant = kDefaultUpdateVariant;
+        const int vdef = precision == CCMF_FP64 ? kDefaultUpdateVariantF64 : kDefaultUpdateVariantF32;
+        int variant = env ? atoi(env) : vdef;
+        if (variant < 0 || variant > 7) variant = vdef;
         sh.upd_variant = 0;
         if (variant >= 2) {
             const int vw = precision == CCMF_FP64 ? 1 : 2;
@@ -454,6 +486,12 @@ int ccmf_plan_create(int n1, int n2, int n3, int batch, int precision, ccmf_plan
         if (sh.upd_variant == 0 && variant >= 1 && sh.tma_rows > 0) sh.upd_variant = 1;
         sh.grid_partials = sh.grid_update > sh.grid_tma ? sh.grid_update : sh.grid_tma;
         if (sh.grid_pipe > sh.grid_partials) sh.grid_partials = sh.grid_pipe;
+        // fused plane FFT pass when the (x, y) plane of one k_z fits one block's shared memory
+        const size_t smem_plane = ((size_t)n1 + n2 + (size_t)n1 * (n2 + 1)) * cs;
+        const char* envp = getenv("CCMF_PLANE_FUSED");
+        const bool allow_plane = !(envp && atoi(envp) == 0);
+        sh.plane_fused = (allow_plane && (long long)n1 * n2 <= kPlaneMax && smem_plane <= 200 * 1024) ? 1 : 0;
+        sh.smem_plane = smem_plane;
     }
 
     // workspace layout
@@ -483,7 +521,7 @@ int ccmf_plan_create(int n1, int n2, int n3, int batch, int precision, ccmf_plan
     // twiddle and symbol tables
     for (int a = 0; a < 3 && rc == CCMF_OK; ++a) {
         const int n = nn[a];
-        std::vector<double> tw(2 * (size_t)n), sy((size_t)n);
+        std::vector<double> tw(2 * (size_t)n), sy((size_t)n), rs((size_t)n);
         for (int t = 0; t < n; ++t) {
             const double ang = -2.0 * kPi * (double)t / (double)n;
             tw[2 * t] = cos(ang);
@@ -491,18 +529,27 @@ int ccmf_plan_create(int n1, int n2, int n3, int batch, int precision, ccmf_plan
             const double sn = sin(kPi * (double)t / (double)n);
             sy[t] = 4.0 * sn * sn;
         }
+        for (int t = 0; t < n; ++t) rs[t] = sy[digit_reversed_frequency(ax[a], t)];
         if (precision == CCMF_FP64) {
             if (cudaMalloc(&pl->tw[a], tw.size() * 8) != cudaSuccess ||
                 cudaMemcpy(pl->tw[a], tw.data(), tw.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
                 cudaMalloc(&pl->sym[a], sy.size() * 8) != cudaSuccess ||
                 cudaMemcpy(pl->sym[a], sy.data(), sy.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
                 rc = CCMF_ERR_CUDA;
+            if (rc == CCMF_OK && a < 2 &&
+                (cudaMalloc(&pl->rsym[a], rs.size() * 8) != cudaSuccess ||
+                 cudaMemcpy(pl->rsym[a], rs.data(), rs.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess))
+                rc = CCMF_ERR_CUDA;
         } else {
-            std::vector<float> twf(tw.begin(), tw.end()), syf(sy.begin(), sy.end());
+            std::vector<float> twf(tw.begin(), tw.end()), syf(sy.begin(), sy.end()), rsf(rs.begin(), rs.end());
             if (cudaMalloc(&pl->tw[a], twf.size() * 4) != cudaSuccess ||
                 cudaMemcpy(pl->tw[a], twf.data(), twf.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
                 cudaMalloc(&pl->sym[a], syf.size() * 4) != cudaSuccess ||
                 cudaMemcpy(pl->sym[a], syf.data(), syf.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+                rc = CCMF_ERR_CUDA;
+            if (rc == CCMF_OK && a < 2 &&
+                (cudaMalloc(&pl->rsym[a], rsf.size() * 4) != cudaSuccess ||
+                 cudaMemcpy(pl->rsym[a], rsf.data(), rsf.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess))
                 rc = CCMF_ERR_CUDA;
         }
     }
@@ -529,6 +576,8 @@ int ccmf_plan_destroy(ccmf_plan* pl) {
         if (pl->tw[a]) cudaFree(pl->tw[a]);
         if (pl->sym[a]) cudaFree(pl->sym[a]);
     }
+    for (int a = 0; a < 2; ++a)
+        if (pl->rsym[a]) cudaFree(pl->rsym[a]);
     if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
     if (pl->h_nactive) cudaFreeHost(pl->h_nactive);
     delete pl;

@@ -44,6 +44,8 @@ struct AxisPlan {
     int nst;                   // number of radix stages
     int rad[kMaxStages];       // radix of each stage, product = n
     FastDiv ns[kMaxStages];    // divisor Ns (product of the earlier radices) of each stage
+    int span[kMaxStages];      // in-place stages: sub-transform length Ls = n / (rad[0] ... rad[st-1])
+    FastDiv sub[kMaxStages];   // in-place stages: divisor m = Ls / rad[st]
 };
 
 template <typename T> struct CxOf;
@@ -197,6 +199,66 @@ __device__ C* block_fft(C* a, C* b, const AxisPlan& ap, const C* __restrict__ tw
         b = t;
     }
     return a;
+}
+
+// In-place mixed-radix Cooley-Tukey stages on lines held in shared memory
+// (element m of line c at buf[c * ls + m * es]). Stage st works on blocks of Ls
+// elements; butterfly (block b, offset j < m = Ls / R) combines the elements
+// b Ls + j + r m, r < R, and writes its outputs back to the same slots, so a stage
+// needs no second buffer. Decimation in frequency (DIF: transform, then twiddle
+// W_Ls^{j q}) maps natural order to digit-reversed order: slot p holds
+// frequency k(p) = sum_s q_s prod_{t<s} R_t with q_s = (p / m_s) mod R_s.
+// Decimation in time (DIT: twiddle, then transform, stages in reverse order)
+// maps digit-reversed input to natural-order output. Both use the forward
+// kernel exp(-2 pi i / n). Threads take consecutive lines first.
+template <typename C, int R, bool DIF, int NT>
+__device__ __forceinline__ void inplace_stage(C* buf, int n, int nlines, int es, int ls, int Ls,
+                                              const FastDiv& msub, const FastDiv& nld,
+                                              const C* __restrict__ tw) {
+    const int m = (int)msub.d;
+    const int total = nlines * (n / R);
+    const int tws = n / Ls;
+    for (int q = threadIdx.x; q < total; q += NT) {
+        const int bj = (int)fdiv((unsigned)q, nld);
+        const int c = q - bj * nlines;
+        const int b = (int)fdiv((unsigned)bj, msub);
+        const int j = bj - b * m;
+        C* x = buf + c * ls + (b * Ls + j) * es;
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = x[r * m * es];
+        if (DIF) {
+            Dft<C, R>::run(v);
+            if (j > 0) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[j * r * tws]);
+            }
+        } else {
+            if (j > 0) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[j * r * tws]);
+            }
+            Dft<C, R>::run(v);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[r * m * es] = v[r];
+    }
+    __syncthreads();
+}
+
+template <typename C, bool DIF, int NT>
+__device__ void inplace_fft(C* buf, const AxisPlan& ap, int nlines, int es, int ls, const FastDiv& nld,
+                            const C* __restrict__ tw) {
+    for (int k = 0; k < ap.nst; ++k) {
+        const int st = DIF ? k : ap.nst - 1 - k;
+        switch (ap.rad[st]) {
+            case 8: inplace_stage<C, 8, DIF, NT>(buf, ap.n, nlines, es, ls, ap.span[st], ap.sub[st], nld, tw); break;
+            case 4: inplace_stage<C, 4, DIF, NT>(buf, ap.n, nlines, es, ls, ap.span[st], ap.sub[st], nld, tw); break;
+            case 2: inplace_stage<C, 2, DIF, NT>(buf, ap.n, nlines, es, ls, ap.span[st], ap.sub[st], nld, tw); break;
+            case 3: inplace_stage<C, 3, DIF, NT>(buf, ap.n, nlines, es, ls, ap.span[st], ap.sub[st], nld, tw); break;
+            default: inplace_stage<C, 5, DIF, NT>(buf, ap.n, nlines, es, ls, ap.span[st], ap.sub[st], nld, tw); break;
+        }
+    }
 }
 
 }  // namespace ccmf

@@ -347,28 +347,32 @@ __global__ void __launch_bounds__(kThreads) k_div_rfft_z(Geom g, Ptrs<T> p, Axis
     }
     __syncthreads();
     C* R = block_fft<C, P>(A, B, az, twl);
+    // half spectrum, k_z-major: spec[kz][i][j]; consecutive threads take consecutive line pairs
     const int cnt2 = P * g.n3h;
     C* spec = p.spec + (size_t)s * g.Nh;
     for (int idx = threadIdx.x; idx < cnt2; idx += kThreads) {
-        const int c = (int)fdiv((unsigned)idx, g.div_n3h);
-        const int kz = idx - c * g.n3h;
+        const int kz = idx / P;
+        const int c = idx - kz * P;
         const C Z = R[kz * stride + c];
         const int kmr = (kz == 0) ? 0 : g.n3 - kz;
         const C Zm = cconj(R[kmr * stride + c]);
         const C Sm = cadd(Z, Zm), D = csub(Z, Zm);
         const long long la = l0 + 2 * c, lb = la + 1;
-        if (la < L) spec[la * g.n3h + kz] = cmake<C>(T(0.5) * Sm.x, T(0.5) * Sm.y);
-        if (lb < L) spec[lb * g.n3h + kz] = cmake<C>(T(0.5) * D.y, T(-0.5) * D.x);
+        C* dst = spec + (long long)kz * L + la;
+        if (la < L) dst[0] = cmake<C>(T(0.5) * Sm.x, T(0.5) * Sm.y);
+        if (lb < L) dst[1] = cmake<C>(T(0.5) * D.y, T(-0.5) * D.x);
     }
 }
 
 // ---------------------------------------------------------------------------
-// Passes 2-4: FFTs along the strided axes of the half spectrum [n1][n2][n3h].
-// MODE 0: forward along y.  MODE 2: inverse along y.
+// Passes 2-4: FFTs along y and x of the half spectrum, stored k_z-major as
+// [n3h][n1][n2] (a (x, y) plane per k_z is contiguous).
+// MODE 0: forward along y.  MODE 2: inverse along y.  y-lines (kz, i) are
+// contiguous runs of n2 elements, so loads and stores walk along the line.
 // MODE 1: forward along x, multiply by 1 / (N lambda(k)) with
 //         lambda(k) = -sum_a 4 sin^2(pi k_a / N_a) and 0 at k = 0, inverse along x.
-// A block transforms LPB lines (consecutive line ids, so that each element row
-// of the tile is a contiguous run of the spectrum).
+//         x-lines (kz, j) have stride n2; consecutive lines are adjacent.
+// A block transforms LPB consecutive lines.
 // ---------------------------------------------------------------------------
 template <typename T, int MODE, int LPB>
 __global__ void __launch_bounds__(kThreads) k_fft_strided(Geom g, Ptrs<T> p, AxisPlan ap,
@@ -386,39 +390,28 @@ __global__ void __launch_bounds__(kThreads) k_fft_strided(Geom g, Ptrs<T> p, Axi
     C* A = twl + n;
     C* B = A + (size_t)n * stride;
     for (int t = threadIdx.x; t < n; t += kThreads) twl[t] = tw[t];
-    const long long nlines = (MODE == 1) ? (long long)g.n2 * g.n3h : (long long)g.n1 * g.n3h;
-    const long long es = (MODE == 1) ? (long long)g.n2 * g.n3h : (long long)g.n3h;
+    const long long plane = (long long)g.n1 * g.n2;
+    const long long nlines = (MODE == 1) ? (long long)g.n3h * g.n2 : (long long)g.n3h * g.n1;
     const long long l0 = (long long)blockIdx.x * LPB;
     C* spec = p.spec + (size_t)s * g.Nh;
-    // this thread always handles line c of the tile; its global base offset is fixed
-    const int c = threadIdx.x & (LPB - 1);
-    const int m0 = threadIdx.x >> lsh;
-    constexpr int mstep = kThreads / LPB;
-    const long long l = l0 + c;
-    const bool valid = l < nlines;
-    long long base = 0;
-    int k2 = 0, kz = 0;
-    if (valid) {
-        if (MODE == 1) {
-            base = l;
-            k2 = (int)fdiv((unsigned)l, g.div_n3h);
-            kz = (int)l - k2 * g.n3h;
-        } else {
-            const long long i = fdiv((unsigned)l, g.div_n3h);
-            base = i * g.n2 * g.n3h + (l - i * g.n3h);
-        }
-    }
-    for (int m = m0; m < n; m += mstep) {
-        C val = cmake<C>(T(0), T(0));
-        if (valid) {
-            val = spec[base + m * es];
-            if (MODE == 2) val = cconj(val);
-        }
-        A[m * stride + c] = val;
-    }
-    __syncthreads();
-    C* R = block_fft<C, LPB>(A, B, ap, twl);
+    const int cnt = LPB * n;
     if (MODE == 1) {
+        // line l = kz * n2 + j: elements i at base + i * n2
+        const int c = threadIdx.x & (LPB - 1);
+        const int m0 = threadIdx.x >> lsh;
+        constexpr int mstep = kThreads / LPB;
+        const long long l = l0 + c;
+        const bool valid = l < nlines;
+        int kz = 0, k2 = 0;
+        long long base = 0;
+        if (valid) {
+            kz = (int)fdiv((unsigned)l, g.div_n2);
+            k2 = (int)(l - (long long)kz * g.n2);
+            base = (long long)kz * plane + k2;
+        }
+        for (int m = m0; m < n; m += mstep) A[m * stride + c] = valid ? spec[base + (long long)m * g.n2] : cmake<C>(T(0), T(0));
+        __syncthreads();
+        C* R = block_fft<C, LPB>(A, B, ap, twl);
         const T lam23 = valid ? sym2[k2] + sym3[kz] : T(0);
         for (int m = m0; m < n; m += mstep) {
             const T lam = sym1[m] + lam23;
@@ -429,13 +422,92 @@ __global__ void __launch_bounds__(kThreads) k_fft_strided(Geom g, Ptrs<T> p, Axi
         __syncthreads();
         C* other = (R == A) ? B : A;
         R = block_fft<C, LPB>(R, other, ap, twl);
-    }
-    if (valid) {
-        for (int m = m0; m < n; m += mstep) {
-            C val = R[m * stride + c];
-            if (MODE != 0) val = cconj(val);
-            spec[base + m * es] = val;
+        if (valid)
+            for (int m = m0; m < n; m += mstep) spec[base + (long long)m * g.n2] = cconj(R[m * stride + c]);
+    } else {
+        // line l = kz * n1 + i: n2 contiguous elements at l * n2
+        for (int idx = threadIdx.x; idx < cnt; idx += kThreads) {
+            const int c = (int)fdiv((unsigned)idx, g.div_n2);
+            const int m = idx - c * n;
+            const long long l = l0 + c;
+            C val = cmake<C>(T(0), T(0));
+            if (l < nlines) {
+                val = spec[l * n + m];
+                if (MODE == 2) val = cconj(val);
+            }
+            A[m * stride + c] = val;
         }
+        __syncthreads();
+        C* R = block_fft<C, LPB>(A, B, ap, twl);
+        for (int idx = threadIdx.x; idx < cnt; idx += kThreads) {
+            const int c = (int)fdiv((unsigned)idx, g.div_n2);
+            const int m = idx - c * n;
+            const long long l = l0 + c;
+            if (l < nlines) {
+                C val = R[m * stride + c];
+                if (MODE == 2) val = cconj(val);
+                spec[l * n + m] = val;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fused plane pass (planes up to kPlaneMax elements): one block per (k_z, solve)
+// holds the whole (x, y) plane of the half spectrum in shared memory (rows of
+// n2 + 1 elements). Forward transforms along y then x run in place as
+// decimation in frequency, leaving both axes in digit-reversed order; the
+// Poisson symbol is applied there (tables of 4 sin^2 in digit-reversed order);
+// the inverse runs as conj(DIT(conj(.))) along x then y, which returns natural
+// order. No permutation pass and no second buffer are needed.
+// ---------------------------------------------------------------------------
+constexpr int kPlaneThreads = 512;
+constexpr int kPlaneMax = 16384;
+
+template <typename T>
+__global__ void __launch_bounds__(kPlaneThreads, 1) k_fft_plane(Geom g, Ptrs<T> p, AxisPlan ax1, AxisPlan ax2,
+                                                                const cx<T>* __restrict__ tw1,
+                                                                const cx<T>* __restrict__ tw2,
+                                                                const T* __restrict__ rsym1,
+                                                                const T* __restrict__ rsym2,
+                                                                const T* __restrict__ sym3, T inv_n) {
+    using C = cx<T>;
+    const int s = blockIdx.y;
+    if (!p.run_all && !p.sc[s].active) return;
+    const int kz = blockIdx.x;
+    const int n1 = g.n1, n2 = g.n2;
+    const int P2 = n2 + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tx = reinterpret_cast<C*>(smem_raw);
+    C* ty = tx + n1;
+    C* tile = ty + n2;
+    for (int t = threadIdx.x; t < n1; t += kPlaneThreads) tx[t] = tw1[t];
+    for (int t = threadIdx.x; t < n2; t += kPlaneThreads) ty[t] = tw2[t];
+    C* spec = p.spec + (size_t)s * g.Nh + (long long)kz * n1 * n2;
+    const int cnt = n1 * n2;
+    for (int idx = threadIdx.x; idx < cnt; idx += kPlaneThreads) {
+        const int i = (int)fdiv((unsigned)idx, g.div_n2);
+        tile[i * P2 + (idx - i * n2)] = spec[idx];
+    }
+    __syncthreads();
+    const FastDiv dn1 = g.div_n1, dn2 = g.div_n2;
+    inplace_fft<C, true, kPlaneThreads>(tile, ax2, n1, 1, P2, dn1, ty);    // y: n1 rows
+    inplace_fft<C, true, kPlaneThreads>(tile, ax1, n2, P2, 1, dn2, tx);    // x: n2 columns
+    const T l3 = sym3[kz];
+    for (int idx = threadIdx.x; idx < cnt; idx += kPlaneThreads) {
+        const int i = (int)fdiv((unsigned)idx, g.div_n2);
+        const int j = idx - i * n2;
+        const T lam = rsym1[i] + rsym2[j] + l3;
+        const T gk = (lam > T(0)) ? -inv_n / lam : T(0);
+        const C z = tile[i * P2 + j];
+        tile[i * P2 + j] = cmake<C>(z.x * gk, -z.y * gk);   // conj: the inverse runs as conj(DIT(conj))
+    }
+    __syncthreads();
+    inplace_fft<C, false, kPlaneThreads>(tile, ax1, n2, P2, 1, dn2, tx);
+    inplace_fft<C, false, kPlaneThreads>(tile, ax2, n1, 1, P2, dn1, ty);
+    for (int idx = threadIdx.x; idx < cnt; idx += kPlaneThreads) {
+        const int i = (int)fdiv((unsigned)idx, g.div_n2);
+        spec[idx] = cconj(tile[i * P2 + (idx - i * n2)]);
     }
 }
 
@@ -459,11 +531,12 @@ __global__ void __launch_bounds__(kThreads) k_irfft_z(Geom g, Ptrs<T> p, AxisPla
     const C* spec = p.spec + (size_t)s * g.Nh;
     const int cnt = P * g.n3h;
     for (int idx = threadIdx.x; idx < cnt; idx += kThreads) {
-        const int c = (int)fdiv((unsigned)idx, g.div_n3h);
-        const int kz = idx - c * g.n3h;
+        const int kz = idx / P;
+        const int c = idx - kz * P;
         const long long la = l0 + 2 * c, lb = la + 1;
-        const C a = (la < L) ? spec[la * g.n3h + kz] : cmake<C>(T(0), T(0));
-        const C b = (lb < L) ? spec[lb * g.n3h + kz] : cmake<C>(T(0), T(0));
+        const C* src = spec + (long long)kz * L + la;
+        const C a = (la < L) ? src[0] : cmake<C>(T(0), T(0));
+        const C b = (lb < L) ? src[1] : cmake<C>(T(0), T(0));
         if (kz == 0 || 2 * kz == g.n3) {
             // Z = Re(a) + i Re(b); store conj(Z)
             A[kz * stride + c] = cmake<C>(a.x, -b.x);

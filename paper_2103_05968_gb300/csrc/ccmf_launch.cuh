@@ -13,19 +13,38 @@ struct Ctx {
     AxisPlan ax[3];
     const cx<T>* tw[3];   // twiddle tables W_n^t, t < n, per axis
     const T* sym[3];      // 4 sin^2(pi k / N_a) per axis
+    const T* rsym[2];     // the x and y tables in digit-reversed order (fused plane pass)
     const double* xi_stage;  // [batch][3] unit normals (device)
     LaunchShape sh;
     bool vec_div;         // 16-byte path of the divergence pass (N3 % W == 0)
     bool vec_update;      // 16-byte path of the update pass (also needs gamma 16-byte aligned)
 };
 
-// Kernel classes of one loop iteration, in launch order.
-enum KernelClass { kKDivRfftZ = 0, kKFftYFwd, kKFftXSolve, kKFftYInv, kKIrfftZ, kKUpdate, kNumKernelClasses };
+// Kernel classes of one loop iteration.
+enum KernelClass {
+    kKDivRfftZ = 0, kKFftYFwd, kKFftXSolve, kKFftYInv, kKFftPlane, kKIrfftZ, kKUpdate, kNumKernelClasses
+};
 
 inline const char* kernel_class_name(int c) {
-    static const char* names[kNumKernelClasses] = {"k_div_rfft_z", "k_fft_y_fwd", "k_fft_x_solve",
-                                                   "k_fft_y_inv", "k_irfft_z", "k_update"};
+    static const char* names[kNumKernelClasses] = {"k_div_rfft_z", "k_fft_y_fwd", "k_fft_x_solve", "k_fft_y_inv",
+                                                   "k_fft_plane", "k_irfft_z", "k_update"};
     return (c >= 0 && c < kNumKernelClasses) ? names[c] : "?";
+}
+
+// The kernel classes one iteration launches, in order; returns their number.
+inline int iteration_classes(const LaunchShape& sh, int* cls) {
+    int n = 0;
+    cls[n++] = kKDivRfftZ;
+    if (sh.plane_fused) {
+        cls[n++] = kKFftPlane;
+    } else {
+        cls[n++] = kKFftYFwd;
+        cls[n++] = kKFftXSolve;
+        cls[n++] = kKFftYInv;
+    }
+    cls[n++] = kKIrfftZ;
+    cls[n++] = kKUpdate;
+    return n;
 }
 
 template <typename T>
@@ -53,13 +72,15 @@ inline long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
     }
 
 // Runs the statement list with compile-time ST (stages) and NTH (threads) of a
-// pipelined update variant 2..5.
+// pipelined update variant 2..7.
 #define CCMF_DISPATCH_PIPE(VAR, ...)                                                 \
     switch (VAR) {                                                                   \
         case 2: { constexpr int NTH = 256, ST = 2; __VA_ARGS__; } break;            \
         case 3: { constexpr int NTH = 128, ST = 3; __VA_ARGS__; } break;            \
         case 4: { constexpr int NTH = 128, ST = 4; __VA_ARGS__; } break;            \
-        default: { constexpr int NTH = 256, ST = 3; __VA_ARGS__; } break;           \
+        case 5: { constexpr int NTH = 256, ST = 3; __VA_ARGS__; } break;            \
+        case 6: { constexpr int NTH = 128, ST = 2; __VA_ARGS__; } break;            \
+        default: { constexpr int NTH = 64, ST = 3; __VA_ARGS__; } break;            \
     }
 
 // Blocks per SM of a pipelined update variant (occupancy API), 0 on error.
@@ -93,6 +114,7 @@ cudaError_t configure_kernels(const LaunchShape& sh) {
         set((const void*)k_fft_strided<T, 2, LN>, sh.smem_y);
     });
     CCMF_DISPATCH_LINES(sh.lpb_x, { set((const void*)k_fft_strided<T, 1, LN>, sh.smem_x); });
+    if (sh.plane_fused) set((const void*)k_fft_plane<T>, sh.smem_plane);
     if (sh.tma_rows > 0) {
         set((const void*)k_update_tma<T, 0>, sh.smem_tma);
         set((const void*)k_update_tma<T, 1>, sh.smem_tma);
@@ -135,21 +157,27 @@ void launch_passes(const Ctx<T>& c, const Ptrs<T>& p, cudaStream_t st, F&& betwe
             k_div_rfft_z<T, LN, false><<<gz, kThreads, sh.smem_z, st>>>(g, p, c.ax[2], c.tw[2]);
     });
     between(kKDivRfftZ);
-    CCMF_DISPATCH_LINES(sh.lpb_y, {
-        k_fft_strided<T, 0, LN><<<gy, kThreads, sh.smem_y, st>>>(g, p, c.ax[1], c.tw[1], c.sym[0], c.sym[1],
-                                                                  c.sym[2], inv_n);
-    });
-    between(kKFftYFwd);
-    CCMF_DISPATCH_LINES(sh.lpb_x, {
-        k_fft_strided<T, 1, LN><<<gx, kThreads, sh.smem_x, st>>>(g, p, c.ax[0], c.tw[0], c.sym[0], c.sym[1],
-                                                                  c.sym[2], inv_n);
-    });
-    between(kKFftXSolve);
-    CCMF_DISPATCH_LINES(sh.lpb_y, {
-        k_fft_strided<T, 2, LN><<<gy, kThreads, sh.smem_y, st>>>(g, p, c.ax[1], c.tw[1], c.sym[0], c.sym[1],
-                                                                  c.sym[2], inv_n);
-    });
-    between(kKFftYInv);
+    if (sh.plane_fused) {
+        k_fft_plane<T><<<dim3((unsigned)g.n3h, (unsigned)g.batch), kPlaneThreads, sh.smem_plane, st>>>(
+            g, p, c.ax[0], c.ax[1], c.tw[0], c.tw[1], c.rsym[0], c.rsym[1], c.sym[2], inv_n);
+        between(kKFftPlane);
+    } else {
+        CCMF_DISPATCH_LINES(sh.lpb_y, {
+            k_fft_strided<T, 0, LN><<<gy, kThreads, sh.smem_y, st>>>(g, p, c.ax[1], c.tw[1], c.sym[0], c.sym[1],
+                                                                      c.sym[2], inv_n);
+        });
+        between(kKFftYFwd);
+        CCMF_DISPATCH_LINES(sh.lpb_x, {
+            k_fft_strided<T, 1, LN><<<gx, kThreads, sh.smem_x, st>>>(g, p, c.ax[0], c.tw[0], c.sym[0], c.sym[1],
+                                                                      c.sym[2], inv_n);
+        });
+        between(kKFftXSolve);
+        CCMF_DISPATCH_LINES(sh.lpb_y, {
+            k_fft_strided<T, 2, LN><<<gy, kThreads, sh.smem_y, st>>>(g, p, c.ax[1], c.tw[1], c.sym[0], c.sym[1],
+                                                                      c.sym[2], inv_n);
+        });
+        between(kKFftYInv);
+    }
     CCMF_DISPATCH_LINES(sh.pairs_per_block,
                         { k_irfft_z<T, LN><<<gz, kThreads, sh.smem_z, st>>>(g, p, c.ax[2], c.tw[2]); });
     between(kKIrfftZ);

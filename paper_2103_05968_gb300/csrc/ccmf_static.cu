@@ -79,9 +79,13 @@ bool radix_plan(int n, AxisPlan* ap) {
         }
     ap->nst = st;
     unsigned ns = 1;
+    int span = n;
     for (int t = 0; t < st; ++t) {
         ap->ns[t] = make_fastdiv(ns);
         ns *= (unsigned)ap->rad[t];
+        ap->span[t] = span;
+        ap->sub[t] = make_fastdiv((unsigned)(span / ap->rad[t]));
+        span /= ap->rad[t];
     }
     return m == 1;
 }

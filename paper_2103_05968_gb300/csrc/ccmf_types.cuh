@@ -52,7 +52,7 @@ struct Geom {
     int n1, n2, n3, n3h, batch;
     long long N;    // voxels per solve
     long long Nh;   // half-spectrum entries per solve (n1 n2 n3h)
-    FastDiv div_n3, div_n2, div_n3h;
+    FastDiv div_n3, div_n2, div_n3h, div_n1;
 };
 
 template <typename T>
@@ -83,12 +83,14 @@ struct LaunchShape {
     size_t smem_tma;          // its dynamic shared memory (two stages + barriers)
     int grid_partials;        // partial-sum slots per solve (max of the update grids)
     int upd_variant;          // update pass: 0 register vectors, 1 TMA (2 stages, any tile),
-                              // 2..5 pipelined TMA (see kUpdatePipe)
+                              // 2..7 pipelined TMA (see kUpdatePipe)
     int grid_pipe;            // blocks per solve of the pipelined update
     size_t smem_pipe;         // its dynamic shared memory
+    int plane_fused;          // 1: y / x / solve / x / y in one k_fft_plane launch per iteration
+    size_t smem_plane;        // its dynamic shared memory
 };
 
 // Pipelined update variants: {threads per block, stages}.
-constexpr int kUpdatePipe[6][2] = {{0, 0}, {0, 0}, {256, 2}, {128, 3}, {128, 4}, {256, 3}};
+constexpr int kUpdatePipe[8][2] = {{0, 0}, {0, 0}, {256, 2}, {128, 3}, {128, 4}, {256, 3}, {128, 2}, {64, 3}};
 
 }  // namespace ccmf

@@ -279,8 +279,12 @@ def test_kernel_timing_mode():
     g = torch.from_numpy(gamma.astype(np.float32)).to(DEV)
     res, _, _ = plan.solve(g, [[0, 0, 1]], ccmf.Params(fixed_iters=10))
     t = plan.kernel_times()
-    assert set(t) == {"k_div_rfft_z", "k_fft_y_fwd", "k_fft_x_solve", "k_fft_y_inv", "k_irfft_z", "k_update"}
-    for name, (ms, n) in t.items():
+    launched = {name for name, (ms, n) in t.items() if n > 0}
+    fused = {"k_div_rfft_z", "k_fft_plane", "k_irfft_z", "k_update"}
+    split = {"k_div_rfft_z", "k_fft_y_fwd", "k_fft_x_solve", "k_fft_y_inv", "k_irfft_z", "k_update"}
+    assert launched in (fused, split)
+    for name in launched:
+        ms, n = t[name]
         assert n == 10 and ms > 0.0
     plan.set_kernel_timing(False)
     res2, _, _ = plan.solve(g, [[0, 0, 1]], ccmf.Params(fixed_iters=10))

@@ -344,6 +344,13 @@ class Plan:
         _check(code, "ccmf_history_export")
         return h
 
+    def branches(self):
+        """Independent graph branches the loop runs the batch in (at most 4, one per solve)."""
+        import os
+        env = os.environ.get("CCMF_BRANCHES")
+        nb = int(env) if env else 4
+        return max(1, min(nb, 4, self.batch))
+
     def set_kernel_timing(self, enable):
         _check(ccmf_set_kernel_timing(self.handle, 1 if enable else 0), "ccmf_set_kernel_timing")
 

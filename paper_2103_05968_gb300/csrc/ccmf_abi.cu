@@ -19,6 +19,7 @@ template <typename T> cudaError_t configure_kernels(const LaunchShape&);
 template <typename T> int pipe_blocks_per_sm(int, size_t);
 template <typename T> void launch_init(const Ctx<T>&, cudaStream_t);
 template <typename T> void launch_iteration(const Ctx<T>&, cudaStream_t);
+template <typename T> void launch_iteration_range(const Ctx<T>&, int, int, cudaStream_t);
 template <typename T> void launch_iteration_timed(const Ctx<T>&, cudaStream_t, cudaEvent_t*);
 template <typename T> void launch_final(const Ctx<T>&, cudaStream_t, T*, T*);
 }  // namespace ccmf
@@ -33,6 +34,10 @@ constexpr int kMaxTimedIters = 2048;
 // FP64 is ALU-bound and best with register vectors
 constexpr int kDefaultUpdateVariantF32 = 3;
 constexpr int kDefaultUpdateVariantF64 = 0;
+// the captured loop runs the solves of a batch as up to this many independent graph
+// branches, so that one branch's FFT pass (on-chip work) overlaps another branch's
+// streaming passes (HBM work)
+constexpr int kMaxBranches = 4;
 constexpr double kPi = 3.14159265358979323846264338327950288;
 
 size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
@@ -115,6 +120,9 @@ struct ccmf_plan {
     size_t off_sc, off_nact, off_xi, off_part, off_hist, off_e, off_v, off_spec, off_phi, off_gam, off_cut,
         off_flow, total;
     cudaStream_t cap_stream;
+    cudaStream_t branch_stream[kMaxBranches];
+    cudaEvent_t fork_event, join_event[kMaxBranches];
+    int branches;    // graph branches of the loop (1 = one chain for the whole batch)
     int* h_nactive;  // pinned
     // captured loop graph
     cudaGraphExec_t gexec;
@@ -202,11 +210,24 @@ int capture_loop(ccmf_plan* pl, const Ctx<T>& c, const GraphKey& key) {
     cudaError_t err = cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (err != cudaSuccess) return CCMF_ERR_CUDA;
     if (key.timed) cudaEventRecordWithFlags(pl->events[0], pl->cap_stream, cudaEventRecordExternal);
-    for (int it = 0; it < key.chunk; ++it) {
-        if (key.timed)
-            launch_iteration_timed<T>(c, pl->cap_stream, pl->events.data() + (size_t)it * nk);
-        else
-            launch_iteration<T>(c, pl->cap_stream);
+    if (key.timed || pl->branches <= 1) {
+        for (int it = 0; it < key.chunk; ++it) {
+            if (key.timed)
+                launch_iteration_timed<T>(c, pl->cap_stream, pl->events.data() + (size_t)it * nk);
+            else
+                launch_iteration<T>(c, pl->cap_stream);
+        }
+    } else {
+        // fork: each branch runs its solves' chain of iterations; join at the end of the chunk
+        const int nb = pl->branches;
+        cudaEventRecord(pl->fork_event, pl->cap_stream);
+        for (int b = 0; b < nb; ++b) {
+            const int s0 = (int)((long long)pl->batch * b / nb), s1 = (int)((long long)pl->batch * (b + 1) / nb);
+            cudaStreamWaitEvent(pl->branch_stream[b], pl->fork_event, 0);
+            for (int it = 0; it < key.chunk; ++it) launch_iteration_range<T>(c, s0, s1 - s0, pl->branch_stream[b]);
+            cudaEventRecord(pl->join_event[b], pl->branch_stream[b]);
+            cudaStreamWaitEvent(pl->cap_stream, pl->join_event[b], 0);
+        }
     }
     err = cudaStreamEndCapture(pl->cap_stream, &graph);
     if (err != cudaSuccess) return CCMF_ERR_CUDA;
@@ -559,6 +580,21 @@ int ccmf_plan_create(int n1, int n2, int n3, int batch, int precision, ccmf_plan
     }
     if (rc == CCMF_OK && cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
         rc = CCMF_ERR_CUDA;
+    {
+        const char* envb = getenv("CCMF_BRANCHES");
+        int nb = envb ? atoi(envb) : kMaxBranches;
+        if (nb < 1) nb = 1;
+        if (nb > kMaxBranches) nb = kMaxBranches;
+        if (nb > batch) nb = batch;
+        pl->branches = nb;
+        if (rc == CCMF_OK && cudaEventCreateWithFlags(&pl->fork_event, cudaEventDisableTiming) != cudaSuccess)
+            rc = CCMF_ERR_CUDA;
+        for (int b = 0; b < nb && rc == CCMF_OK; ++b) {
+            if (cudaStreamCreateWithFlags(&pl->branch_stream[b], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&pl->join_event[b], cudaEventDisableTiming) != cudaSuccess)
+                rc = CCMF_ERR_CUDA;
+        }
+    }
     if (rc == CCMF_OK && cudaMallocHost((void**)&pl->h_nactive, sizeof(int)) != cudaSuccess) rc = CCMF_ERR_CUDA;
     if (rc != CCMF_OK) {
         ccmf_plan_destroy(pl);
@@ -579,6 +615,11 @@ int ccmf_plan_destroy(ccmf_plan* pl) {
     for (int a = 0; a < 2; ++a)
         if (pl->rsym[a]) cudaFree(pl->rsym[a]);
     if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+    for (int b = 0; b < kMaxBranches; ++b) {
+        if (pl->branch_stream[b]) cudaStreamDestroy(pl->branch_stream[b]);
+        if (pl->join_event[b]) cudaEventDestroy(pl->join_event[b]);
+    }
+    if (pl->fork_event) cudaEventDestroy(pl->fork_event);
     if (pl->h_nactive) cudaFreeHost(pl->h_nactive);
     delete pl;
     return CCMF_OK;

@@ -99,7 +99,7 @@ __device__ void reduce_partials(const double* __restrict__ partial, int nblocks,
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_init_stats(Geom g, Ptrs<T> p, LoopConfig cfg) {
-    const int s = blockIdx.y;
+    const int s = blockIdx.y + p.s0;
     const T* gam = p.gamma + (size_t)s * p.gstride;
     double acc_min = INFINITY, acc_max = -INFINITY, acc_sum = 0.0, acc_bad = 0.0;
     const long long stride = (long long)gridDim.x * kThreads;
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(kThreads) k_init_stats(Geom g, Ptrs<T> p, Loop
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_init_state(Geom g, Ptrs<T> p) {
-    const int s = blockIdx.y;
+    const int s = blockIdx.y + p.s0;
     const double h = 0.70710678118654752440084436210485;
     const SolveScalars& S = p.sc[s];
     const T a0 = (T)(S.xi[0] * h), a1 = (T)(S.xi[1] * h), a2 = (T)(S.xi[2] * h);
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(kThreads) k_div_rfft_z(Geom g, Ptrs<T> p, Axis
     using C = cx<T>;
     constexpr int stride = P + 1;
     constexpr int W = VEC ? Vec16<T>::W : 1;
-    const int s = blockIdx.y;
+    const int s = blockIdx.y + p.s0;
     if (!p.run_all && !p.sc[s].active) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* twl = reinterpret_cast<C*>(smem_raw);
@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(kThreads) k_fft_strided(Geom g, Ptrs<T> p, Axi
     using C = cx<T>;
     constexpr int stride = LPB + 1;
     constexpr int lsh = (LPB >= 16) ? 4 : (LPB >= 8) ? 3 : (LPB >= 4) ? 2 : (LPB >= 2) ? 1 : 0;
-    const int s = blockIdx.y;
+    const int s = blockIdx.y + p.s0;
     if (!p.run_all && !p.sc[s].active) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = ap.n;
@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) k_fft_plane(Geom g, Ptrs<T> 
                                                                 const T* __restrict__ rsym2,
                                                                 const T* __restrict__ sym3, T inv_n) {
     using C = cx<T>;
-    const int s = blockIdx.y;
+    const int s = blockIdx.y + p.s0;
     if (!p.run_all && !p.sc[s].active) return;
     const int kz = blockIdx.x;
     const int n1 = g.n1, n2 = g.n2;
@@ -519,7 +519,7 @@ __global__ void __launch_bounds__(kThreads) k_irfft_z(Geom g, Ptrs<T> p, AxisPla
                                                       const cx<T>* __restrict__ tw) {
     using C = cx<T>;
     constexpr int stride = P + 1;
-    const int s = blockIdx.y;
+    const int s = blockIdx.y + p.s0;
     if (!p.run_all && !p.sc[s].active) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* twl = reinterpret_cast<C*>(smem_raw);
@@ -760,7 +760,7 @@ __device__ __forceinline__ StepConsts<T> step_consts(const SolveScalars& S, cons
 // Scalar version (any N3, unaligned inputs, and the final evaluation pass).
 template <typename T, bool OUT>
 __global__ void __launch_bounds__(kThreads) k_update(Geom g, Ptrs<T> p, LoopConfig cfg) {
-    const int s = blockIdx.y;
+    const int s = blockIdx.y + p.s0;
     SolveScalars& S = p.sc[s];
     if (!OUT && !S.active) return;
     const long long N = g.N;
@@ -831,7 +831,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_update_vec(Geom g, Ptrs<T> p, LoopConfig cfg) {
     constexpr int W = Vec16<T>::W;
     using V = Vec16<T>;
-    const int s = blockIdx.y;
+    const int s = blockIdx.y + p.s0;
     SolveScalars& S = p.sc[s];
     if (!S.active) return;
     const long long N = g.N;
@@ -1000,7 +1000,7 @@ template <typename T, int RULE>
 __global__ void __launch_bounds__(kThreads, 2) k_update_tma(Geom g, Ptrs<T> p, LoopConfig cfg, int J) {
     using V = Vec8<T>;
     constexpr int W = V::W;
-    const int s = blockIdx.y;
+    const int s = blockIdx.y + p.s0;
     SolveScalars& S = p.sc[s];
     if (!S.active) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1191,7 +1191,7 @@ __global__ void __launch_bounds__(NT) k_update_pipe(Geom g, Ptrs<T> p, LoopConfi
     using V = Vec8<T>;
     constexpr int W = V::W;
     constexpr int TV = NT * W;
-    const int s = blockIdx.y;
+    const int s = blockIdx.y + p.s0;
     SolveScalars& S = p.sc[s];
     if (!S.active) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -142,7 +142,7 @@ void launch_init(const Ctx<T>& c, cudaStream_t st) {
 // `between` is called after every kernel with its class (used to record events).
 template <typename T, bool OUT, typename F>
 void launch_passes(const Ctx<T>& c, const Ptrs<T>& p, cudaStream_t st, F&& between) {
-    const Geom& g = c.g;
+    const Geom& g = c.g;   // g.batch = number of solves of this launch, starting at p.s0
     const LaunchShape& sh = c.sh;
     const long long pairs = ceil_div((long long)g.n1 * g.n2, 2);
     dim3 gz((unsigned)ceil_div(pairs, sh.pairs_per_block), (unsigned)g.batch);
@@ -216,6 +216,15 @@ struct NoHook {
 template <typename T>
 void launch_iteration(const Ctx<T>& c, cudaStream_t st) {
     launch_passes<T, false>(c, c.p, st, NoHook());
+}
+
+// One iteration for the solves [s0, s0 + ns) only (a branch of the captured graph).
+template <typename T>
+void launch_iteration_range(const Ctx<T>& c, int s0, int ns, cudaStream_t st) {
+    Ctx<T> cr = c;
+    cr.g.batch = ns;
+    cr.p.s0 = s0;
+    launch_passes<T, false>(cr, cr.p, st, NoHook());
 }
 
 template <typename T>

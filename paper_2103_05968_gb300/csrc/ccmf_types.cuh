@@ -71,6 +71,7 @@ struct Ptrs {
     T* cut;               // [batch][6][N] (final pass, may be null)
     T* flow;              // [batch][3][N] (final pass, may be null)
     int run_all;          // 1: passes run for every solve (final evaluation), 0: active solves only
+    int s0;               // first solve of this launch (blockIdx.y counts from it)
 };
 
 struct LaunchShape {

@@ -36,7 +36,8 @@ WORKLOADS = {
     "boolean128": dict(shape=(128, 128, 128), normals=[[1, 0, 0], [0, 1, 0], [0, 0, 1]],
                        desc="128^3 Boolean spheres r=6 vf=0.20 gamma 0.3/1.0, normals e1,e2,e3 (3 solves)"),
     "fibres512": dict(shape=(512, 512, 512), normals=[[0, 0, 1]],
-                      desc="512^3 short fibres d=6 AR=20 vf=0.12 gamma 3.0/1.0, normal e3 (1 solve)"),
+                      desc="512^3 short fibres d=6 AR=20 vf=0.12 gamma 3.0/1.0 (256^3 RSA cell tiled 2x2x2), "
+                           "normal e3 (1 solve)"),
 }
 
 
@@ -46,7 +47,7 @@ def make_gamma(name, dtype):
         g, _ = M.config_boolean_spheres_128(dtype=dtype)
         return g
     if name == "fibres512":
-        g, _ = M.short_fibres((512, 512, 512), 6.0, 20.0, 0.12, 3.0, 1.0, seed=2103, dtype=dtype)
+        g, _ = M.config_short_fibres_512(dtype=dtype)
         return g
     raise ValueError(name)
 

@@ -490,14 +490,18 @@ int ccmf_plan_create(int n1, int n2, int n3, int batch, int precision, ccmf_plan
             const int vw = precision == CCMF_FP64 ? 1 : 2;
             const int tv = kUpdatePipe[variant][0] * vw;
             const int stages = kUpdatePipe[variant][1];
-            if (n3 % W == 0 && tv % n3 == 0 && n2 % (tv / n3) == 0) {
-                const size_t smem = (size_t)stages * (size_t)tma_stage_elems(tv, n3) * pl->esize + 8 * stages;
+            const bool rows_ok = n3 <= tv && tv % n3 == 0 && n2 % (tv / n3) == 0;
+            const bool seg_ok = n3 > tv && n3 % tv == 0;
+            if (n3 % W == 0 && (rows_ok || seg_ok)) {
+                const int kt = seg_ok ? tv : n3;
+                const size_t smem = (size_t)stages * (size_t)pipe_stage_elems(tv, kt, seg_ok, 16 / (int)pl->esize) *
+                                        pl->esize + 8 * stages;
                 const int nb = precision == CCMF_FP64 ? pipe_blocks_per_sm<double>(variant, smem)
                                                       : pipe_blocks_per_sm<float>(variant, smem);
                 if (nb > 0) {
                     sh.upd_variant = variant;
                     sh.smem_pipe = smem;
-                    long long nt = (long long)n1 * (n2 / (tv / n3));
+                    long long nt = (long long)n1 * (n2 / (tv / kt)) * (n3 / kt);
                     long long gp = ((long long)nb * sms + batch - 1) / batch;
                     if (gp > nt) gp = nt;
                     sh.grid_pipe = (int)(gp < 1 ? 1 : gp);

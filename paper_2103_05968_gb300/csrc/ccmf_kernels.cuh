@@ -1183,26 +1183,38 @@ __global__ void __launch_bounds__(kThreads, 2) k_update_tma(Geom g, Ptrs<T> p, L
 }
 
 // Pipelined variant: NT threads, each owning one W-wide group of every tile
-// (TV = NT * W voxels = J whole z rows, J = TV / N3 dividing N2), so that all
-// per-thread index arithmetic is fixed for the whole kernel; STAGES tiles are
-// in flight. Same copies, waits and arithmetic as k_update_tma.
+// (TV = NT * W voxels), so that all per-thread index arithmetic is fixed for the
+// whole kernel; STAGES tiles are in flight. A tile is either J = TV / N3 whole z
+// rows (N3 <= TV, J dividing N2) or a segment of KT = TV voxels of one row
+// (N3 > TV, TV dividing N3); segments add the 16-byte z-halo chunks holding the
+// voxels just before and after them. Same copies, waits and arithmetic as
+// k_update_tma.
+__host__ __device__ inline long long pipe_stage_elems(int TV, int KT, bool seg, int cw) {
+    return 20LL * TV + 6LL * KT + (seg ? 6LL * cw : 0LL);
+}
+
 template <typename T, int RULE, int STAGES, int NT>
 __global__ void __launch_bounds__(NT) k_update_pipe(Geom g, Ptrs<T> p, LoopConfig cfg) {
     using V = Vec8<T>;
     constexpr int W = V::W;
     constexpr int TV = NT * W;
+    constexpr int CW = 16 / (int)sizeof(T);   // elements of a 16-byte z-halo chunk
     const int s = blockIdx.y + p.s0;
     SolveScalars& S = p.sc[s];
     if (!S.active) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n3 = g.n3;
-    const int J = TV / n3;
-    const long long selems = tma_stage_elems(TV, n3);
+    const bool seg = n3 > TV;
+    const int KT = seg ? TV : n3;            // z extent of a tile
+    const int J = TV / KT;                   // rows of a tile
+    const int nseg = n3 / KT;                // tiles per row
+    const long long selems = pipe_stage_elems(TV, KT, seg, CW);
     T* stages = reinterpret_cast<T*>(smem_raw);
     unsigned long long* bars = reinterpret_cast<unsigned long long*>(stages + STAGES * selems);
     const unsigned stage_bytes = (unsigned)(selems * sizeof(T));
     constexpr unsigned tv_bytes = (unsigned)(TV * sizeof(T));
-    const unsigned row_bytes = (unsigned)(n3 * sizeof(T));
+    const unsigned kt_bytes = (unsigned)(KT * sizeof(T));
+    constexpr unsigned cw_bytes = 16;
 
     const long long N = g.N;
     const double rho_d = S.rho;
@@ -1215,7 +1227,7 @@ __global__ void __launch_bounds__(NT) k_update_pipe(Geom g, Ptrs<T> p, LoopConfi
     const T* __restrict__ phi = p.phi + (size_t)s * N;
     const T* __restrict__ gam = p.gamma + (size_t)s * p.gstride;
     const int tiles_j = g.n2 / J;
-    const int ntiles = g.n1 * tiles_j;
+    const int ntiles = g.n1 * tiles_j * nseg;
 
     if (threadIdx.x == 0) {
 #pragma unroll
@@ -1224,20 +1236,28 @@ __global__ void __launch_bounds__(NT) k_update_pipe(Geom g, Ptrs<T> p, LoopConfi
     }
     __syncthreads();
 
+    // tile -> (i, j0, k0)
+    auto tile_origin = [&](int tile, int& i, int& j0, int& k0) {
+        const int row_tile = tile / nseg;
+        k0 = (tile - row_tile * nseg) * KT;
+        i = row_tile / tiles_j;
+        j0 = (row_tile - i * tiles_j) * J;
+    };
     auto issue = [&](int tile, int st) {
         T* b = stages + st * selems;
-        const int i = tile / tiles_j;
-        const int j0 = (tile - i * tiles_j) * J;
+        int i, j0, k0;
+        tile_origin(tile, i, j0, k0);
         const int ip = (i + 1 == g.n1) ? 0 : i + 1, im = (i == 0) ? g.n1 - 1 : i - 1;
         const int jp = (j0 + J == g.n2) ? 0 : j0 + J, jm = (j0 == 0) ? g.n2 - 1 : j0 - 1;
-        const long long base = ((long long)i * g.n2 + j0) * n3;
-        const long long bip = ((long long)ip * g.n2 + j0) * n3, bim = ((long long)im * g.n2 + j0) * n3;
-        const long long rjp = ((long long)i * g.n2 + jp) * n3, rjm = ((long long)i * g.n2 + jm) * n3;
+        const long long base = ((long long)i * g.n2 + j0) * n3 + k0;
+        const long long bip = ((long long)ip * g.n2 + j0) * n3 + k0, bim = ((long long)im * g.n2 + j0) * n3 + k0;
+        const long long rjp = ((long long)i * g.n2 + jp) * n3 + k0, rjm = ((long long)i * g.n2 + jm) * n3 + k0;
         unsigned long long* bar = &bars[st];
         mbar_expect_tx(bar, stage_bytes);
         T* own = b;
         T* yh = b + 14 * TV;
-        T* xn = yh + 6LL * n3;
+        T* xn = yh + 6LL * KT;
+        T* zh = xn + 6 * TV;
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
             bulk_g2s(own + c * TV, e + c * N + base, tv_bytes, bar);
@@ -1245,18 +1265,30 @@ __global__ void __launch_bounds__(NT) k_update_pipe(Geom g, Ptrs<T> p, LoopConfi
         }
         bulk_g2s(own + 12 * TV, gam + base, tv_bytes, bar);
         bulk_g2s(own + 13 * TV, phi + base, tv_bytes, bar);
-        bulk_g2s(yh + 0LL * n3, e + 1 * N + rjm, row_bytes, bar);
-        bulk_g2s(yh + 1LL * n3, v + 1 * N + rjm, row_bytes, bar);
-        bulk_g2s(yh + 2LL * n3, e + 4 * N + rjp, row_bytes, bar);
-        bulk_g2s(yh + 3LL * n3, v + 4 * N + rjp, row_bytes, bar);
-        bulk_g2s(yh + 4LL * n3, phi + rjm, row_bytes, bar);
-        bulk_g2s(yh + 5LL * n3, phi + rjp, row_bytes, bar);
+        bulk_g2s(yh + 0LL * KT, e + 1 * N + rjm, kt_bytes, bar);
+        bulk_g2s(yh + 1LL * KT, v + 1 * N + rjm, kt_bytes, bar);
+        bulk_g2s(yh + 2LL * KT, e + 4 * N + rjp, kt_bytes, bar);
+        bulk_g2s(yh + 3LL * KT, v + 4 * N + rjp, kt_bytes, bar);
+        bulk_g2s(yh + 4LL * KT, phi + rjm, kt_bytes, bar);
+        bulk_g2s(yh + 5LL * KT, phi + rjp, kt_bytes, bar);
         bulk_g2s(xn + 0 * TV, e + 0 * N + bim, tv_bytes, bar);
         bulk_g2s(xn + 1 * TV, v + 0 * N + bim, tv_bytes, bar);
         bulk_g2s(xn + 2 * TV, e + 3 * N + bip, tv_bytes, bar);
         bulk_g2s(xn + 3 * TV, v + 3 * N + bip, tv_bytes, bar);
         bulk_g2s(xn + 4 * TV, phi + bim, tv_bytes, bar);
         bulk_g2s(xn + 5 * TV, phi + bip, tv_bytes, bar);
+        if (seg) {
+            // 16-byte chunks ending at k0 - 1 and starting at k0 + KT (periodic in z)
+            const long long row = ((long long)i * g.n2 + j0) * n3;
+            const long long cb = row + ((k0 == 0) ? n3 - CW : k0 - CW);
+            const long long ca = row + ((k0 + KT == n3) ? 0 : k0 + KT);
+            bulk_g2s(zh + 0 * CW, e + 2 * N + cb, cw_bytes, bar);
+            bulk_g2s(zh + 1 * CW, v + 2 * N + cb, cw_bytes, bar);
+            bulk_g2s(zh + 2 * CW, phi + cb, cw_bytes, bar);
+            bulk_g2s(zh + 3 * CW, e + 5 * N + ca, cw_bytes, bar);
+            bulk_g2s(zh + 4 * CW, v + 5 * N + ca, cw_bytes, bar);
+            bulk_g2s(zh + 5 * CW, phi + ca, cw_bytes, bar);
+        }
     };
 
     const int t0 = blockIdx.x;
@@ -1266,20 +1298,25 @@ __global__ void __launch_bounds__(NT) k_update_pipe(Geom g, Ptrs<T> p, LoopConfi
         for (int q = 0; q < STAGES; ++q)
             if (t0 + q * tstep < ntiles) issue(t0 + q * tstep, q);
     }
-    // this thread's group: fixed offsets for the whole kernel
+    // this thread's group: fixed stage offsets for the whole kernel
     const int lv0 = threadIdx.x * W;
-    const int r = lv0 / n3;
-    const int k0 = lv0 - r * n3;
-    const int kp = (k0 + W == n3) ? 0 : k0 + W, km = (k0 == 0) ? n3 - 1 : k0 - 1;
-    const int rz = r * n3;
+    const int r = lv0 / KT;
+    const int kk = lv0 - r * KT;
+    const int rz = r * KT;
     const bool top = (r + 1 == J), bot = (r == 0);
-    const int o_e2y = top ? 14 * TV + 2 * n3 + k0 : 4 * TV + lv0 + n3;
-    const int o_v2y = top ? 14 * TV + 3 * n3 + k0 : 10 * TV + lv0 + n3;
-    const int o_e1y = bot ? 14 * TV + 0 * n3 + k0 : 1 * TV + lv0 - n3;
-    const int o_v1y = bot ? 14 * TV + 1 * n3 + k0 : 7 * TV + lv0 - n3;
-    const int o_pyp = top ? 14 * TV + 5 * n3 + k0 : 13 * TV + lv0 + n3;
-    const int o_pym = bot ? 14 * TV + 4 * n3 + k0 : 13 * TV + lv0 - n3;
-    const int xo = 14 * TV + 6 * n3 + lv0;   // xn[0] at this group
+    const int o_e2y = top ? 14 * TV + 2 * KT + kk : 4 * TV + lv0 + KT;
+    const int o_v2y = top ? 14 * TV + 3 * KT + kk : 10 * TV + lv0 + KT;
+    const int o_e1y = bot ? 14 * TV + 0 * KT + kk : 1 * TV + lv0 - KT;
+    const int o_v1y = bot ? 14 * TV + 1 * KT + kk : 7 * TV + lv0 - KT;
+    const int o_pyp = top ? 14 * TV + 5 * KT + kk : 13 * TV + lv0 + KT;
+    const int o_pym = bot ? 14 * TV + 4 * KT + kk : 13 * TV + lv0 - KT;
+    const int xo = 14 * TV + 6 * KT + lv0;   // xn[0] at this group
+    const int zo = 20 * TV + 6 * KT;         // zh[0]
+    // z neighbours just outside the group: inside the tile, wrapped within a whole
+    // row, or from the z-halo chunks of a segment
+    const bool after_in = kk + W < KT, before_in = kk > 0;
+    const int o_after = after_in ? rz + kk + W : (seg ? -1 : rz);
+    const int o_before = before_in ? rz + kk - 1 : (seg ? -1 : rz + KT - 1);
 
     T acc[kNSum];
 #pragma unroll
@@ -1317,17 +1354,33 @@ __global__ void __launch_bounds__(NT) k_update_pipe(Geom g, Ptrs<T> p, LoopConfi
         V::ld(b + o_v1y, v1y);
         V::ld(b + o_pyp, phyp);
         V::ld(b + o_pym, phym);
-        const T e2z_after = b[5 * TV + rz + kp], v2z_after = b[11 * TV + rz + kp];
-        const T e1z_before = b[2 * TV + rz + km], v1z_before = b[8 * TV + rz + km];
-        const T ph_after = b[13 * TV + rz + kp], ph_before = b[13 * TV + rz + km];
+        T e2z_after, v2z_after, ph_after, e1z_before, v1z_before, ph_before;
+        if (o_after >= 0) {
+            e2z_after = b[5 * TV + o_after];
+            v2z_after = b[11 * TV + o_after];
+            ph_after = b[13 * TV + o_after];
+        } else {
+            e2z_after = b[zo + 3 * CW];
+            v2z_after = b[zo + 4 * CW];
+            ph_after = b[zo + 5 * CW];
+        }
+        if (o_before >= 0) {
+            e1z_before = b[2 * TV + o_before];
+            v1z_before = b[8 * TV + o_before];
+            ph_before = b[13 * TV + o_before];
+        } else {
+            e1z_before = b[zo + 0 * CW + CW - 1];
+            v1z_before = b[zo + 1 * CW + CW - 1];
+            ph_before = b[zo + 2 * CW + CW - 1];
+        }
         __syncthreads();   // the stage has been read into registers: refill it
         if (threadIdx.x == 0 && tile + STAGES * tstep < ntiles) {
             fence_proxy_async_smem();
             issue(tile + STAGES * tstep, st);
         }
-        const int i = tile / tiles_j;
-        const int j0 = (tile - i * tiles_j) * J;
-        const long long gbase = ((long long)i * g.n2 + j0) * n3 + lv0;
+        int ti, tj0, tk0;
+        tile_origin(tile, ti, tj0, tk0);
+        const long long gbase = ((long long)ti * g.n2 + tj0) * n3 + tk0 + (long long)r * n3 + kk;
         T eo[6][W], vo[6][W];
 #pragma unroll
         for (int u = 0; u < W; ++u) {

@@ -35,6 +35,9 @@ FALLBACK_HBM_GBS = 6800.0
 WORKLOADS = {
     "boolean128": dict(shape=(128, 128, 128), normals=[[1, 0, 0], [0, 1, 0], [0, 0, 1]],
                        desc="128^3 Boolean spheres r=6 vf=0.20 gamma 0.3/1.0, normals e1,e2,e3 (3 solves)"),
+    "batch192": dict(shape=None, normals=[[1, 0, 0], [0, 1, 0], [0, 0, 1]],
+                     desc="192 solves: 64 Boolean-sphere realisations (radius U[4,8], volume fraction U[0.10,0.30], "
+                          "gamma 0.2/1.0, grid drawn from {64,96,128,160}^3) x normals e1,e2,e3, one graph"),
     "fibres512": dict(shape=(512, 512, 512), normals=[[0, 0, 1]],
                       desc="512^3 short fibres d=6 AR=20 vf=0.12 gamma 3.0/1.0 (256^3 RSA cell tiled 2x2x2), "
                            "normal e3 (1 solve)"),
@@ -50,6 +53,76 @@ def make_gamma(name, dtype):
         g, _ = M.config_short_fibres_512(dtype=dtype)
         return g
     raise ValueError(name)
+
+
+def batch_inputs(dtype, seed=2103):
+    """The 64 realisations of the batched workload: (fields, per-solve field index, normals, shapes)."""
+    from paper_2103_05968_gb300 import microstructure as M
+    rng = np.random.default_rng(seed)
+    fields = []
+    for r in range(64):
+        n = int(rng.choice([64, 96, 128, 160]))
+        vf = float(rng.uniform(0.10, 0.30))
+        g, _ = M.boolean_spheres((n, n, n), 4.0, vf, 0.2, 1.0, seed=seed + 1 + r, radius_max=8.0, dtype=dtype)
+        fields.append(g)
+    index = [r for r in range(64) for _ in range(3)]
+    normals = np.array([nv for _ in range(64) for nv in WORKLOADS["batch192"]["normals"]], dtype=np.float64)
+    shapes = [fields[r].shape for r in index]
+    return fields, index, normals, shapes
+
+
+def run_batch(args, world, rank, local):
+    """The batched workload: 192 solves of 4 grid shapes in one captured graph."""
+    import torch
+
+    import __graft_entry__
+    from paper_2103_05968_gb300 import ccmf
+
+    __graft_entry__.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    prec = ccmf.CCMF_FP64 if args.precision == "fp64" else ccmf.CCMF_FP32_MIXED
+    np_dtype = np.float64 if prec == ccmf.CCMF_FP64 else np.float32
+    esize = 8 if prec == ccmf.CCMF_FP64 else 4
+    fields, index, normals, shapes = batch_inputs(np_dtype)
+    dfields = [torch.from_numpy(f).to(dev) for f in fields]
+    gammas = [dfields[r] for r in index]
+    vox = sum(int(np.prod(sh)) for sh in shapes)
+    batch = ccmf.Batch(shapes, precision=prec, device=dev)
+    K, W = args.steps, args.warmup
+    p = ccmf.Params(fixed_iters=K, check_every=K)
+    batch.solve(gammas, normals, ccmf.Params(fixed_iters=W, check_every=W))
+    batch.solve(gammas, normals, p, want_results=False)      # capture
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    batch.solve(gammas, normals, p, want_results=False)      # init + K iterations + final evaluation
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    t_ms = max_over_ranks(ev0.elapsed_time(ev1), world)
+    clk = clocks.stop()
+    value = world * vox * K / (t_ms * 1e-3)
+    peak, peak_kind = load_peaks()
+    step_bytes = vox * (12 * esize + 2 * esize + 12 * esize + 12 * esize + 6 * esize)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+                "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if esize == 8 else "f32", "data": "synthetic",
+                "config": {"workload": WORKLOADS["batch192"]["desc"], "solves": len(shapes),
+                           "voxels_per_step": vox, "buckets": batch.buckets(), "precision": args.precision,
+                           "l2": "inputs larger than L2"},
+                "roofline": {"bound": "hbm", "achieved": step_bytes / (t_ms / K * 1e-3) / 1e9, "peak": peak,
+                             "unit": "GB/s", "frac": step_bytes / (t_ms / K * 1e-3) / 1e9 / peak,
+                             "traffic": None, "kernel": "whole step (196 B/voxel FP32 basis)",
+                             "peak_kind": peak_kind},
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+    batch.close()
 
 
 def bytes_per_voxel(kernel, esize, n3):
@@ -370,7 +443,10 @@ def main():
         run_reference(args, world, rank)
         return
     world, rank, local = dist_setup(args)
-    run_gpu(args, world, rank, local)
+    if args.workload == "batch192":
+        run_batch(args, world, rank, local)
+    else:
+        run_gpu(args, world, rank, local)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

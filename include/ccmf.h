@@ -180,6 +180,41 @@ int ccmf_kernel_times(const ccmf_plan* plan, double* ms, long long* launches, co
 int ccmf_set_kernel_timing(ccmf_plan* plan, int enable);
 
 /*
+ * Batches of independent solves on grids of different shapes (for example many
+ * microstructure realisations and crack normals, Sec. 4.5 / Sec. 4.6 style studies).
+ * The solves are grouped by shape into sub-plans; one captured CUDA graph runs all
+ * groups as independent branches and each solve iterates until its own Eq. 31
+ * test holds (or for fixed_iters updates).
+ */
+typedef struct ccmf_batch ccmf_batch;
+
+/* count solves; shapes = host array [count][3] of (N1, N2, N3), each as for
+ * ccmf_plan_create. Allocates the sub-plans' tables. */
+int ccmf_batch_create(int count, const int* shapes, int precision, ccmf_batch** out);
+
+/* Release a batch (NULL is accepted). */
+int ccmf_batch_destroy(ccmf_batch* batch);
+
+/* Bytes of device workspace ccmf_batch_solve needs. */
+int ccmf_batch_workspace_bytes(const ccmf_batch* batch, size_t* bytes);
+
+/* Number of shape groups (sub-plans) of the batch. */
+int ccmf_batch_buckets(const ccmf_batch* batch, int* buckets);
+
+/*
+ * Solve every problem of the batch (Eq. 30, Eq. 31).
+ *   gammas    : host array [count] of DEVICE pointers to each solve's gamma field
+ *               (element type of the precision; solves may share a pointer)
+ *   xi_bar    : host array [count][3] of crack normals
+ *   params    : as for ccmf_solve (NULL = defaults); resume must be 0
+ *   workspace : device memory of ccmf_batch_workspace_bytes bytes, 256-byte aligned
+ *   results   : optional host array [count]; when given, the call synchronises the stream
+ */
+int ccmf_batch_solve(ccmf_batch* batch, const void* const* gammas, const double* xi_bar,
+                     const ccmf_params* params, void* workspace, size_t workspace_bytes,
+                     ccmf_result* results, void* stream);
+
+/*
  * Size of the fixed device scratch area used by ccmf_solve_static (64 MiB). The
  * area is a file-scope __device__ array of the library: every GPU that loads the
  * library holds it until the process exits.

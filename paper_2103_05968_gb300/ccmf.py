@@ -94,6 +94,15 @@ _SIGNATURES = {
                                           ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_char_p),
                                           ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "ccmf_set_kernel_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "ccmf_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_void_p)]),
+    "ccmf_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "ccmf_batch_workspace_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    "ccmf_batch_buckets": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "ccmf_batch_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ccmf_params),
+                                         ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ccmf_result),
+                                         ctypes.c_void_p]),
     "ccmf_solve_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ccmf_params),
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ccmf_result),
@@ -201,6 +210,38 @@ def ccmf_kernel_times(plan):
 
 def ccmf_set_kernel_timing(plan, enable):
     return load_library().ccmf_set_kernel_timing(plan, int(enable))
+
+
+def ccmf_batch_create(shapes, precision):
+    sh = np.ascontiguousarray(np.asarray(shapes, dtype=np.int32).reshape(-1, 3))
+    out = ctypes.c_void_p()
+    code = load_library().ccmf_batch_create(int(sh.shape[0]), sh.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                            int(precision), ctypes.byref(out))
+    return code, out.value
+
+
+def ccmf_batch_destroy(batch):
+    return load_library().ccmf_batch_destroy(batch)
+
+
+def ccmf_batch_workspace_bytes(batch):
+    b = ctypes.c_size_t()
+    code = load_library().ccmf_batch_workspace_bytes(batch, ctypes.byref(b))
+    return code, b.value
+
+
+def ccmf_batch_buckets(batch):
+    n = ctypes.c_int()
+    code = load_library().ccmf_batch_buckets(batch, ctypes.byref(n))
+    return code, n.value
+
+
+def ccmf_batch_solve(batch, gamma_ptrs, xi_bar, params, workspace_ptr, workspace_bytes, results, stream):
+    ptrs = (ctypes.c_void_p * len(gamma_ptrs))(*[int(p) for p in gamma_ptrs])
+    xi = np.ascontiguousarray(xi_bar, dtype=np.float64).reshape(-1)
+    return load_library().ccmf_batch_solve(batch, ptrs, xi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                           ctypes.byref(params) if params is not None else None,
+                                           workspace_ptr, int(workspace_bytes), results, stream)
 
 
 def ccmf_solve_static(n1, n2, n3, precision, gamma_ptr, xi_bar, params, flow_ptr, cut_ptr, result, stream):
@@ -358,3 +399,55 @@ class Plan:
         code, t = ccmf_kernel_times(self.handle)
         _check(code, "ccmf_kernel_times")
         return t
+
+
+class Batch:
+    """Solves on grids of different shapes in one call (argument marshalling only)."""
+
+    def __init__(self, shapes, precision=CCMF_FP32_MIXED, device="cuda"):
+        import torch
+
+        self.torch = torch
+        self.shapes = [tuple(int(x) for x in sh) for sh in shapes]
+        self.count = len(self.shapes)
+        self.precision = precision
+        self.device = torch.device(device)
+        with torch.cuda.device(self.device):
+            code, self.handle = ccmf_batch_create(self.shapes, precision)
+            _check(code, "ccmf_batch_create")
+            code, nbytes = ccmf_batch_workspace_bytes(self.handle)
+            _check(code, "ccmf_batch_workspace_bytes")
+            self.workspace_bytes = nbytes
+            self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        self.ws_ptr = (self.workspace.data_ptr() + 255) // 256 * 256
+
+    def buckets(self):
+        code, n = ccmf_batch_buckets(self.handle)
+        _check(code, "ccmf_batch_buckets")
+        return n
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ccmf_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, gammas, normals, params=None, want_results=True):
+        """gammas: list of device tensors (one per solve, may repeat); normals: (count, 3)."""
+        torch = self.torch
+        params = params or Params()
+        ptrs = [g.data_ptr() for g in gammas]
+        res = (ccmf_result * self.count)()
+        with torch.cuda.device(self.device):
+            code = ccmf_batch_solve(self.handle, ptrs, np.asarray(normals, dtype=np.float64), params.to_c(),
+                                    ctypes.c_void_p(self.ws_ptr), self.workspace_bytes,
+                                    res if want_results else None, _stream_handle(torch, self.device))
+        _check(code, "ccmf_batch_solve")
+        if not want_results:
+            return None
+        return [{f[0]: getattr(r, f[0]) for f in ccmf_result._fields_} for r in res]

@@ -781,4 +781,286 @@ int ccmf_set_kernel_timing(ccmf_plan* plan, int enable) {
     return CCMF_OK;
 }
 
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches of solves on grids of different shapes. Solves are grouped by shape
+// into sub-plans (buckets); every bucket keeps its state in its own slice of the
+// workspace, and one captured CUDA graph runs the iteration chains of all
+// buckets (and of the solve branches inside each bucket) as independent
+// branches, so that short and long passes of different grids fill the GPU
+// together. The graph's executor plays the role of the work queue: no kernel
+// waits on another.
+// ---------------------------------------------------------------------------
+struct ccmf_batch {
+    int count, prec;
+    std::vector<ccmf_plan*> plans;           // one per distinct shape
+    std::vector<std::vector<int>> members;   // original solve indices of each bucket
+    std::vector<size_t> ws_off;              // offset of each bucket's workspace slice
+    std::vector<size_t> gp_off;              // offset of each bucket's gamma pointer table
+    size_t total;
+    cudaStream_t cap_stream;
+    cudaEvent_t fork_event;
+    std::vector<cudaEvent_t> join_events;
+    cudaGraphExec_t gexec;
+    bool have_graph;
+    GraphKey gkey;
+    int* h_active;                           // pinned, one counter per bucket
+};
+
+namespace {
+
+void batch_free(ccmf_batch* b) {
+    if (!b) return;
+    if (b->have_graph) cudaGraphExecDestroy(b->gexec);
+    for (ccmf_plan* pl : b->plans) ccmf_plan_destroy(pl);
+    for (cudaEvent_t ev : b->join_events) cudaEventDestroy(ev);
+    if (b->fork_event) cudaEventDestroy(b->fork_event);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->h_active) cudaFreeHost(b->h_active);
+    delete b;
+}
+
+template <typename T>
+int batch_solve_impl(ccmf_batch* bt, const void* const* gammas, const double* xi_host, const ccmf_params* prm,
+                     unsigned char* ws, ccmf_result* results, cudaStream_t st) {
+    const int nb = (int)bt->plans.size();
+    LoopConfig cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.tol = prm->tol;
+    cfg.delta = prm->delta;
+    cfg.rho0 = prm->rho0;
+    cfg.bb_corr_min = prm->bb_corr_min;
+    cfg.rho_step_max = prm->rho_step_max;
+    cfg.max_iter = prm->max_iter;
+    cfg.fixed_iters = prm->fixed_iters;
+    cfg.rho_rule = prm->rho_rule;
+    cfg.hist_len = prm->history_len;
+    cfg.resume = 0;
+    std::vector<Ctx<T>> ctx(nb);
+    bool aligned = true;
+    for (int b = 0; b < nb; ++b) {
+        ccmf_plan* pl = bt->plans[b];
+        unsigned char* wsb = ws + bt->ws_off[b];
+        const std::vector<int>& mem = bt->members[b];
+        std::vector<double> xi(3 * mem.size());
+        std::vector<const void*> gp(mem.size());
+        for (size_t q = 0; q < mem.size(); ++q) {
+            const double* x = xi_host + 3 * mem[q];
+            const double nn = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+            for (int a = 0; a < 3; ++a) xi[3 * q + a] = x[a] / nn;
+            gp[q] = gammas[mem[q]];
+            aligned = aligned && ((uintptr_t)gp[q] % 16) == 0;
+        }
+        if (cudaMemcpyAsync(wsb + pl->off_xi, xi.data(), xi.size() * sizeof(double), cudaMemcpyHostToDevice, st) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(ws + bt->gp_off[b], gp.data(), gp.size() * sizeof(void*), cudaMemcpyHostToDevice, st) !=
+                cudaSuccess ||
+            cudaMemsetAsync(wsb + pl->off_nact, 0, sizeof(int), st) != cudaSuccess ||
+            cudaMemsetAsync(wsb + pl->off_hist, 0xFF,
+                            sizeof(double) * kHistFields * (size_t)kHistCap * pl->batch, st) != cudaSuccess)
+            return CCMF_ERR_CUDA;
+        ctx[b] = make_ctx<T>(pl, wsb, nullptr, 0, cfg);
+        ctx[b].p.gptrs = reinterpret_cast<const T* const*>(ws + bt->gp_off[b]);
+    }
+    for (int b = 0; b < nb; ++b) {
+        ctx[b].vec_update = ctx[b].vec_div && aligned;
+        launch_init<T>(ctx[b], st);
+    }
+    if (cudaGetLastError() != cudaSuccess) return CCMF_ERR_CUDA;
+
+    const bool fixed = prm->fixed_iters > 0;
+    const int total = fixed ? prm->fixed_iters : prm->max_iter;
+    const int chunk = prm->check_every < total ? prm->check_every : total;
+    GraphKey key;
+    memset(&key, 0, sizeof(key));
+    key.chunk = chunk;
+    key.timed = aligned ? 2 : 3;   // records the alignment the captured kernels assume
+    key.ws = ws;
+    key.cfg = cfg;
+    if (!(bt->have_graph && memcmp(&bt->gkey, &key, sizeof(key)) == 0)) {
+        if (bt->have_graph) cudaGraphExecDestroy(bt->gexec);
+        bt->have_graph = false;
+        cudaGraph_t graph;
+        if (cudaStreamBeginCapture(bt->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return CCMF_ERR_CUDA;
+        cudaEventRecord(bt->fork_event, bt->cap_stream);
+        int ev = 0;
+        for (int b = 0; b < nb; ++b) {
+            ccmf_plan* pl = bt->plans[b];
+            const int nbr = pl->branches;
+            for (int r = 0; r < nbr; ++r) {
+                const int s0 = (int)((long long)pl->batch * r / nbr), s1 = (int)((long long)pl->batch * (r + 1) / nbr);
+                cudaStreamWaitEvent(pl->branch_stream[r], bt->fork_event, 0);
+                for (int it = 0; it < chunk; ++it) launch_iteration_range<T>(ctx[b], s0, s1 - s0, pl->branch_stream[r]);
+                cudaEventRecord(bt->join_events[ev], pl->branch_stream[r]);
+                cudaStreamWaitEvent(bt->cap_stream, bt->join_events[ev], 0);
+                ++ev;
+            }
+        }
+        cudaError_t err = cudaStreamEndCapture(bt->cap_stream, &graph);
+        if (err != cudaSuccess) return CCMF_ERR_CUDA;
+        err = cudaGraphInstantiate(&bt->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (err != cudaSuccess) return CCMF_ERR_CUDA;
+        bt->gkey = key;
+        bt->have_graph = true;
+    }
+    const long long nchunks = ((long long)total + chunk - 1) / chunk;
+    for (long long ch = 0; ch < nchunks; ++ch) {
+        if (cudaGraphLaunch(bt->gexec, st) != cudaSuccess) return CCMF_ERR_CUDA;
+        if (!fixed) {
+            for (int b = 0; b < nb; ++b)
+                if (cudaMemcpyAsync(bt->h_active + b, ws + bt->ws_off[b] + bt->plans[b]->off_nact, sizeof(int),
+                                    cudaMemcpyDeviceToHost, st) != cudaSuccess)
+                    return CCMF_ERR_CUDA;
+            if (cudaStreamSynchronize(st) != cudaSuccess) return CCMF_ERR_CUDA;
+            int act = 0;
+            for (int b = 0; b < nb; ++b) act += bt->h_active[b];
+            if (act <= 0) break;
+        }
+    }
+    for (int b = 0; b < nb; ++b) launch_final<T>(ctx[b], st, nullptr, nullptr);
+    if (cudaGetLastError() != cudaSuccess) return CCMF_ERR_CUDA;
+    if (results) {
+        for (int b = 0; b < nb; ++b) {
+            ccmf_plan* pl = bt->plans[b];
+            std::vector<SolveScalars> sc(pl->batch);
+            if (cudaMemcpyAsync(sc.data(), ws + bt->ws_off[b] + pl->off_sc, sizeof(SolveScalars) * pl->batch,
+                                cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                return CCMF_ERR_CUDA;
+            for (int q = 0; q < pl->batch; ++q) {
+                ccmf_result& r = results[bt->members[b][q]];
+                r.gamma_eff = sc[q].dual;
+                r.gamma_primal = sc[q].primal;
+                r.gamma_dual = sc[q].dual;
+                r.residual = sc[q].residual;
+                r.mean_v_norm = sc[q].mean_v;
+                r.rho = sc[q].rho;
+                r.iters = sc[q].iters;
+                r.converged = sc[q].converged;
+                r.status = sc[q].status;
+                r.reserved = 0;
+            }
+        }
+    }
+    return CCMF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ccmf_batch_create(int count, const int* shapes, int precision, ccmf_batch** out) {
+    if (!out) return CCMF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (count < 1 || !shapes || (precision != CCMF_FP64 && precision != CCMF_FP32_MIXED)) return CCMF_ERR_INVALID_ARG;
+    for (int s = 0; s < count; ++s) {
+        const int* sh = shapes + 3 * s;
+        if (sh[0] < 1 || sh[1] < 1 || sh[2] < 1) return CCMF_ERR_INVALID_ARG;
+        AxisPlan ap;
+        for (int a = 0; a < 3; ++a)
+            if (sh[a] > kMaxN || !make_axis_plan(sh[a], &ap)) return CCMF_ERR_UNSUPPORTED_SIZE;
+    }
+    ccmf_batch* bt = new (std::nothrow) ccmf_batch();
+    if (!bt) return CCMF_ERR_INVALID_ARG;
+    bt->count = count;
+    bt->prec = precision;
+    // buckets of equal shape, in order of first appearance
+    std::vector<std::vector<int>> keys;
+    for (int s = 0; s < count; ++s) {
+        const int* sh = shapes + 3 * s;
+        size_t b = 0;
+        for (; b < keys.size(); ++b)
+            if (keys[b][0] == sh[0] && keys[b][1] == sh[1] && keys[b][2] == sh[2]) break;
+        if (b == keys.size()) {
+            keys.push_back({sh[0], sh[1], sh[2]});
+            bt->members.push_back({});
+        }
+        bt->members[b].push_back(s);
+    }
+    int rc = CCMF_OK;
+    size_t off = 0;
+    for (size_t b = 0; b < keys.size() && rc == CCMF_OK; ++b) {
+        ccmf_plan* pl = nullptr;
+        rc = ccmf_plan_create(keys[b][0], keys[b][1], keys[b][2], (int)bt->members[b].size(), precision, &pl);
+        if (rc != CCMF_OK) break;
+        bt->plans.push_back(pl);
+        bt->ws_off.push_back(off);
+        off = align_up(off + pl->total);
+        bt->gp_off.push_back(off);
+        off = align_up(off + sizeof(void*) * bt->members[b].size());
+    }
+    bt->total = off;
+    int nev = 0;
+    for (ccmf_plan* pl : bt->plans) nev += pl->branches;
+    if (rc == CCMF_OK && cudaStreamCreateWithFlags(&bt->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        rc = CCMF_ERR_CUDA;
+    if (rc == CCMF_OK && cudaEventCreateWithFlags(&bt->fork_event, cudaEventDisableTiming) != cudaSuccess)
+        rc = CCMF_ERR_CUDA;
+    for (int e = 0; e < nev && rc == CCMF_OK; ++e) {
+        cudaEvent_t ev;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) rc = CCMF_ERR_CUDA;
+        else bt->join_events.push_back(ev);
+    }
+    if (rc == CCMF_OK && cudaMallocHost((void**)&bt->h_active, sizeof(int) * bt->plans.size()) != cudaSuccess)
+        rc = CCMF_ERR_CUDA;
+    if (rc != CCMF_OK) {
+        batch_free(bt);
+        return rc;
+    }
+    *out = bt;
+    return CCMF_OK;
+}
+
+int ccmf_batch_destroy(ccmf_batch* batch) {
+    batch_free(batch);
+    return CCMF_OK;
+}
+
+int ccmf_batch_workspace_bytes(const ccmf_batch* batch, size_t* bytes) {
+    if (!batch || !bytes) return CCMF_ERR_INVALID_ARG;
+    *bytes = batch->total;
+    return CCMF_OK;
+}
+
+int ccmf_batch_solve(ccmf_batch* batch, const void* const* gammas, const double* xi_bar, const ccmf_params* params,
+                     void* workspace, size_t workspace_bytes, ccmf_result* results, void* stream) {
+    if (!batch || !gammas || !xi_bar) return CCMF_ERR_INVALID_ARG;
+    ccmf_params prm;
+    if (params)
+        prm = *params;
+    else
+        ccmf_params_default(&prm);
+    for (int s = 0; s < batch->count; ++s) {
+        const double* x = xi_bar + 3 * s;
+        const double nn = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+        if (!isfinite(x[0]) || !isfinite(x[1]) || !isfinite(x[2]) || !(nn > 0.0) || !isfinite(nn))
+            return CCMF_ERR_INVALID_ARG;
+        if (!gammas[s] || !is_device_ptr(gammas[s])) return CCMF_ERR_INVALID_ARG;
+    }
+    if (prm.fixed_iters < 0 || prm.max_iter < 1 || prm.check_every < 1) return CCMF_ERR_INVALID_ARG;
+    if (prm.fixed_iters == 0 && !(prm.tol > 0.0)) return CCMF_ERR_INVALID_ARG;
+    if (!(prm.delta > 0.0 && prm.delta < 1.0)) return CCMF_ERR_INVALID_ARG;
+    if (prm.rho_rule < CCMF_RHO_BB || prm.rho_rule > CCMF_RHO_LTD) return CCMF_ERR_INVALID_ARG;
+    if (!(prm.rho_step_max >= 1.0) || !isfinite(prm.rho0) || !isfinite(prm.bb_corr_min)) return CCMF_ERR_INVALID_ARG;
+    if (prm.history_len < 0 || prm.history_len > kHistCap) return CCMF_ERR_INVALID_ARG;
+    if (prm.resume != 0) return CCMF_ERR_INVALID_ARG;
+    if (!workspace || workspace_bytes < batch->total || ((uintptr_t)workspace & 255u) != 0)
+        return CCMF_ERR_WORKSPACE;
+    if (cudaSetDevice(batch->plans[0]->device) != cudaSuccess) return CCMF_ERR_CUDA;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    unsigned char* ws = reinterpret_cast<unsigned char*>(workspace);
+    if (batch->prec == CCMF_FP64) return batch_solve_impl<double>(batch, gammas, xi_bar, &prm, ws, results, st);
+    return batch_solve_impl<float>(batch, gammas, xi_bar, &prm, ws, results, st);
+}
+
+int ccmf_batch_buckets(const ccmf_batch* batch, int* buckets) {
+    if (!batch || !buckets) return CCMF_ERR_INVALID_ARG;
+    *buckets = (int)batch->plans.size();
+    return CCMF_OK;
+}
+
 }  // extern "C"

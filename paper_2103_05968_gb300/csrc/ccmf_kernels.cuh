@@ -35,6 +35,12 @@ template <> struct Real<double> {
     __device__ __forceinline__ static double sqrt_(double x) { return sqrt(x); }
 };
 
+// gamma field of solve s: a per-solve pointer table when given, else base + s * stride.
+template <typename T>
+__device__ __forceinline__ const T* gamma_of(const Ptrs<T>& p, int s) {
+    return p.gptrs ? p.gptrs[s] : p.gamma + (size_t)s * p.gstride;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T x) {
 #pragma unroll
@@ -100,7 +106,7 @@ __device__ void reduce_partials(const double* __restrict__ partial, int nblocks,
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_init_stats(Geom g, Ptrs<T> p, LoopConfig cfg) {
     const int s = blockIdx.y + p.s0;
-    const T* gam = p.gamma + (size_t)s * p.gstride;
+    const T* gam = gamma_of(p, s);
     double acc_min = INFINITY, acc_max = -INFINITY, acc_sum = 0.0, acc_bad = 0.0;
     const long long stride = (long long)gridDim.x * kThreads;
     for (long long lin = (long long)blockIdx.x * kThreads + threadIdx.x; lin < g.N; lin += stride) {
@@ -774,7 +780,7 @@ __global__ void __launch_bounds__(kThreads) k_update(Geom g, Ptrs<T> p, LoopConf
     T* __restrict__ e_out = p.e + (long long)(1 - par) * p.sstride + (long long)s * 6 * N;
     T* __restrict__ v_out = p.v + (long long)(1 - par) * p.sstride + (long long)s * 6 * N;
     const T* __restrict__ phi = p.phi + (size_t)s * N;
-    const T* __restrict__ gam = p.gamma + (size_t)s * p.gstride;
+    const T* __restrict__ gam = gamma_of(p, s);
     T acc[kNSum];
 #pragma unroll
     for (int q = 0; q < kNSum; ++q) acc[q] = T(0);
@@ -843,7 +849,7 @@ __global__ void __launch_bounds__(kThreads) k_update_vec(Geom g, Ptrs<T> p, Loop
     T* __restrict__ e_out = p.e + (long long)(1 - par) * p.sstride + (long long)s * 6 * N;
     T* __restrict__ v_out = p.v + (long long)(1 - par) * p.sstride + (long long)s * 6 * N;
     const T* __restrict__ phi = p.phi + (size_t)s * N;
-    const T* __restrict__ gam = p.gamma + (size_t)s * p.gstride;
+    const T* __restrict__ gam = gamma_of(p, s);
     T acc[kNSum];
 #pragma unroll
     for (int q = 0; q < kNSum; ++q) acc[q] = T(0);
@@ -1022,7 +1028,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_update_tma(Geom g, Ptrs<T> p, L
     T* __restrict__ e_out = p.e + (long long)(1 - par) * p.sstride + (long long)s * 6 * N;
     T* __restrict__ v_out = p.v + (long long)(1 - par) * p.sstride + (long long)s * 6 * N;
     const T* __restrict__ phi = p.phi + (size_t)s * N;
-    const T* __restrict__ gam = p.gamma + (size_t)s * p.gstride;
+    const T* __restrict__ gam = gamma_of(p, s);
     const int tiles_j = g.n2 / J;
     const int ntiles = g.n1 * tiles_j;
 
@@ -1225,7 +1231,7 @@ __global__ void __launch_bounds__(NT) k_update_pipe(Geom g, Ptrs<T> p, LoopConfi
     T* __restrict__ e_out = p.e + (long long)(1 - par) * p.sstride + (long long)s * 6 * N;
     T* __restrict__ v_out = p.v + (long long)(1 - par) * p.sstride + (long long)s * 6 * N;
     const T* __restrict__ phi = p.phi + (size_t)s * N;
-    const T* __restrict__ gam = p.gamma + (size_t)s * p.gstride;
+    const T* __restrict__ gam = gamma_of(p, s);
     const int tiles_j = g.n2 / J;
     const int ntiles = g.n1 * tiles_j * nseg;
 

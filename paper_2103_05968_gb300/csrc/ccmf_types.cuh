@@ -66,8 +66,9 @@ struct Ptrs {
     long long sstride;    // elements between the two copies (batch * 6 * N)
     cx<T>* spec;          // [batch][Nh]
     T* phi;               // [batch][N]
-    const T* gamma;       // solve s at gamma + s * gstride
+    const T* gamma;       // solve s at gamma + s * gstride ...
     long long gstride;
+    const T* const* gptrs;  // ... or, when not null, at gptrs[s] (device array of pointers)
     T* cut;               // [batch][6][N] (final pass, may be null)
     T* flow;              // [batch][3][N] (final pass, may be null)
     int run_all;          // 1: passes run for every solve (final evaluation), 0: active solves only

@@ -139,6 +139,19 @@ def bytes_per_voxel(kernel, esize, n3):
     }[kernel]
 
 
+def load_traffic(kernel, workload, precision):
+    """DRAM bytes per launch of a kernel from the committed ncu summaries (profiles/*.md),
+    or None when no capture of this kernel, workload and precision is recorded."""
+    import glob
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for line in open(path):
+            parts = line.split()
+            if len(parts) == 5 and parts[0] == "dram_bytes_per_launch" and parts[1:4] == [kernel, workload,
+                                                                                           precision]:
+                return float(parts[4])
+    return None
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -378,7 +391,7 @@ def run_gpu(args, world, rank, local):
             for k, (ms, n) in kt.items()}
     step_bytes = sum(bytes_per_voxel(k, esize, n3) for k in kt) * N * B
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": dom, "peak_kind": peak_kind,
+                "traffic": load_traffic(dom, name, args.precision), "kernel": dom, "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": per_launch_bytes,
                 "kernel_times_from": f"sequential event-timed pass of the same {K} steps "
                                      f"({t_seq_ms / K:.4f} ms/step)",

@@ -180,6 +180,34 @@ int ccmf_kernel_times(const ccmf_plan* plan, double* ms, long long* launches, co
 int ccmf_set_kernel_timing(ccmf_plan* plan, int enable);
 
 /*
+ * Gradient of the effective crack energy with respect to the crack resistances,
+ * d gamma_eff / d gamma(x), through K unrolled updates of Eq. 30 (reverse mode).
+ * The differentiated function is the reported gamma_eff (the max-flow value
+ * <xi_bar, A* v^K> of Eq. 12) after K updates with the penalty sequence rho^0 ...
+ * rho^{K-1} held fixed: either the given schedule, or the one an adaptive run of
+ * K updates with `params` chooses (recorded first). At convergence the gradient
+ * tends to |xi*(x)| / N, the envelope derivative of the min-cut value (Eq. 21).
+ * Checkpoints of (e, v) are kept every ckpt_every updates; each segment is
+ * recomputed once during the reverse sweep (memory: ~K / ckpt_every + ckpt_every
+ * state copies).
+ *   gamma, gamma_stride : device gamma as for ccmf_solve
+ *   xi_bar              : host [batch][3]
+ *   params              : delta, rho rule and safeguard of the recording run (NULL = defaults)
+ *   K, ckpt_every       : unrolled updates (K <= 4096 when the schedule is recorded), checkpoint interval
+ *   rho_schedule        : optional host [batch][K] penalties to replay
+ *   workspace           : the plan's workspace (ccmf_plan_workspace_bytes)
+ *   adj_workspace       : device memory of ccmf_adjoint_workspace_bytes bytes, 256-byte aligned
+ *   grad_gamma          : device output [batch][N] (element type of the plan)
+ *   rho_out             : optional host output [batch][K], the schedule used
+ *   results             : optional host [batch]: gamma_eff of the replayed run; synchronises the stream
+ */
+int ccmf_adjoint_workspace_bytes(const ccmf_plan* plan, int K, int ckpt_every, size_t* bytes);
+int ccmf_adjoint(ccmf_plan* plan, const void* gamma, long long gamma_stride, const double* xi_bar,
+                 const ccmf_params* params, int K, int ckpt_every, const double* rho_schedule,
+                 void* workspace, size_t workspace_bytes, void* adj_workspace, size_t adj_workspace_bytes,
+                 void* grad_gamma, double* rho_out, ccmf_result* results, void* stream);
+
+/*
  * Batches of independent solves on grids of different shapes (for example many
  * microstructure realisations and crack normals, Sec. 4.5 / Sec. 4.6 style studies).
  * The solves are grouped by shape into sub-plans; one captured CUDA graph runs all

@@ -94,6 +94,14 @@ _SIGNATURES = {
                                           ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_char_p),
                                           ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "ccmf_set_kernel_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "ccmf_adjoint_workspace_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                                     ctypes.POINTER(ctypes.c_size_t)]),
+    "ccmf_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong,
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ccmf_params), ctypes.c_int,
+                                     ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_size_t,
+                                     ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ccmf_result),
+                                     ctypes.c_void_p]),
     "ccmf_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_void_p)]),
     "ccmf_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
@@ -210,6 +218,27 @@ def ccmf_kernel_times(plan):
 
 def ccmf_set_kernel_timing(plan, enable):
     return load_library().ccmf_set_kernel_timing(plan, int(enable))
+
+
+def ccmf_adjoint_workspace_bytes(plan, K, ckpt_every):
+    b = ctypes.c_size_t()
+    code = load_library().ccmf_adjoint_workspace_bytes(plan, int(K), int(ckpt_every), ctypes.byref(b))
+    return code, b.value
+
+
+def ccmf_adjoint(plan, gamma_ptr, gamma_stride, xi_bar, params, K, ckpt_every, rho_schedule, workspace_ptr,
+                 workspace_bytes, adj_ptr, adj_bytes, grad_ptr, rho_out, results, stream):
+    xi = np.ascontiguousarray(xi_bar, dtype=np.float64).reshape(-1)
+    sched = None
+    if rho_schedule is not None:
+        sched_arr = np.ascontiguousarray(rho_schedule, dtype=np.float64).reshape(-1)
+        sched = sched_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    rout = rho_out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if rho_out is not None else None
+    return load_library().ccmf_adjoint(plan, gamma_ptr, int(gamma_stride),
+                                       xi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       ctypes.byref(params) if params is not None else None, int(K), int(ckpt_every),
+                                       sched, workspace_ptr, int(workspace_bytes), adj_ptr, int(adj_bytes), grad_ptr,
+                                       rout, results, stream)
 
 
 def ccmf_batch_create(shapes, precision):
@@ -392,6 +421,31 @@ class Plan:
         nb = int(env) if env else 4
         return max(1, min(nb, 4, self.batch))
 
+    def gradient(self, gamma, normals, K, ckpt_every=20, params=None, rho_schedule=None):
+        """d gamma_eff / d gamma through K replayed updates (see ccmf_adjoint in include/ccmf.h).
+        Returns (grad [batch, N1, N2, N3] on the device, results, rho schedule [batch, K])."""
+        torch = self.torch
+        params = params or Params()
+        g = gamma
+        stride = 0 if g.dim() == 3 else self.n_voxels
+        normals = np.asarray(normals, dtype=np.float64).reshape(self.batch, 3)
+        n1, n2, n3 = self.shape
+        with torch.cuda.device(self.device):
+            code, abytes = ccmf_adjoint_workspace_bytes(self.handle, K, ckpt_every)
+            _check(code, "ccmf_adjoint_workspace_bytes")
+            aws = torch.empty(abytes + 256, dtype=torch.uint8, device=self.device)
+            aptr = (aws.data_ptr() + 255) // 256 * 256
+            grad = torch.empty((self.batch, n1, n2, n3), dtype=self.dtype, device=self.device)
+            rho_out = np.zeros((self.batch, K))
+            res = (ccmf_result * self.batch)()
+            code = ccmf_adjoint(self.handle, ctypes.c_void_p(g.data_ptr()), stride, normals, params.to_c(), K,
+                                ckpt_every, rho_schedule, ctypes.c_void_p(self.ws_ptr), self.workspace_bytes,
+                                ctypes.c_void_p(aptr), abytes, ctypes.c_void_p(grad.data_ptr()), rho_out, res,
+                                _stream_handle(torch, self.device))
+        _check(code, "ccmf_adjoint")
+        results = [{f[0]: getattr(r, f[0]) for f in ccmf_result._fields_} for r in res]
+        return grad, results, rho_out
+
     def set_kernel_timing(self, enable):
         _check(ccmf_set_kernel_timing(self.handle, 1 if enable else 0), "ccmf_set_kernel_timing")
 
@@ -451,3 +505,27 @@ class Batch:
         if not want_results:
             return None
         return [{f[0]: getattr(r, f[0]) for f in ccmf_result._fields_} for r in res]
+
+
+def crack_energy(gamma, normal, plan, K, ckpt_every=20, params=None):
+    """gamma_eff(normal) after K updates as a differentiable torch function of gamma.
+
+    The forward pass records the adaptive penalty schedule of K updates and returns
+    the max-flow value; the backward pass runs the library's reverse mode
+    (ccmf_adjoint) with that schedule held fixed.
+    """
+    import torch
+
+    class _CrackEnergy(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, g):
+            grad, res, rho = plan.gradient(g.detach().contiguous(), [normal], K, ckpt_every, params)
+            ctx.save_for_backward(grad)
+            return torch.tensor(res[0]["gamma_eff"], dtype=g.dtype, device=g.device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            (grad,) = ctx.saved_tensors
+            return gout * grad[0]
+
+    return _CrackEnergy.apply(gamma)

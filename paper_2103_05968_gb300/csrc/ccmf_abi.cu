@@ -22,6 +22,11 @@ template <typename T> void launch_iteration(const Ctx<T>&, cudaStream_t);
 template <typename T> void launch_iteration_range(const Ctx<T>&, int, int, cudaStream_t);
 template <typename T> void launch_iteration_timed(const Ctx<T>&, cudaStream_t, cudaEvent_t*);
 template <typename T> void launch_final(const Ctx<T>&, cudaStream_t, T*, T*);
+template <typename T> void launch_adj_restore(const Ctx<T>&, int, const double*, int, cudaStream_t);
+template <typename T> void launch_adj_seed(const Ctx<T>&, T*, T*, SolveScalars*, cudaStream_t);
+template <typename T>
+void launch_adj_step(const Ctx<T>&, const T*, T*, T*, T*, T*, T*, const T*, SolveScalars*, T*, const double*, int, int,
+                     cudaStream_t);
 }  // namespace ccmf
 
 namespace {
@@ -1061,6 +1066,228 @@ int ccmf_batch_buckets(const ccmf_batch* batch, int* buckets) {
     if (!batch || !buckets) return CCMF_ERR_INVALID_ARG;
     *buckets = (int)batch->plans.size();
     return CCMF_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Reverse mode: d gamma_eff / d gamma through K replayed updates (see the
+// header). The forward replay keeps (e, v) every ckpt_every updates; the
+// reverse sweep recomputes each segment from its checkpoint, keeping the
+// pre-projection points z^k, and runs the adjoint steps backwards.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct AdjLayout {
+    size_t sched, dummy, ckpt, z, ebar, vbar, zbar, y, my, zero, total;
+};
+
+AdjLayout adj_layout(const ccmf_plan* pl, int K, int m) {
+    AdjLayout L;
+    const size_t f6 = pl->esize * 6 * (size_t)pl->g.N * pl->batch;   // one 6-component field, all solves
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes);
+        return o;
+    };
+    L.sched = take(sizeof(double) * (size_t)K * pl->batch);
+    L.dummy = take(256 * (size_t)pl->batch);
+    L.ckpt = take(2 * f6 * (size_t)((K + m - 1) / m));
+    L.z = take(f6 * (size_t)m);
+    L.ebar = take(f6);
+    L.vbar = take(f6);
+    L.zbar = take(f6);
+    L.y = take(f6);
+    L.my = take(f6);
+    L.zero = take(f6);
+    L.total = off;
+    return L;
+}
+
+template <typename T>
+int adjoint_impl(ccmf_plan* pl, const T* gamma, long long gstride, const double* xi_host, const ccmf_params* prm,
+                 int K, int m, const double* sched_host, unsigned char* ws, unsigned char* aws, T* grad,
+                 double* rho_out, ccmf_result* results, cudaStream_t st) {
+    const Geom& g = pl->g;
+    const int B = pl->batch;
+    const AdjLayout L = adj_layout(pl, K, m);
+    std::vector<double> sched((size_t)K * B);
+    if (sched_host) {
+        memcpy(sched.data(), sched_host, sched.size() * sizeof(double));
+    } else {
+        // record the penalties of an adaptive run of K updates
+        ccmf_params rec = *prm;
+        rec.fixed_iters = K;
+        rec.check_every = K;
+        rec.resume = 0;
+        rec.history_len = K;
+        int rc = solve_impl<T>(pl, gamma, gstride, xi_host, &rec, ws, nullptr, nullptr, nullptr, st);
+        if (rc != CCMF_OK) return rc;
+        std::vector<double> hist((size_t)B * K * kHistFields);
+        int cnt = 0;
+        rc = ccmf_history_export(pl, ws, hist.data(), K, &cnt, st);
+        if (rc != CCMF_OK) return rc;
+        if (cnt != K) return CCMF_ERR_NUMERICAL;
+        for (int s = 0; s < B; ++s)
+            for (int k = 0; k < K; ++k) sched[(size_t)s * K + k] = hist[((size_t)s * K + k) * kHistFields + 1];
+    }
+    if (rho_out) memcpy(rho_out, sched.data(), sched.size() * sizeof(double));
+    double* dsched = reinterpret_cast<double*>(aws + L.sched);
+    if (cudaMemcpyAsync(dsched, sched.data(), sched.size() * sizeof(double), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+        return CCMF_ERR_CUDA;
+
+    // forward replay from e^0, v^0 with checkpoints
+    std::vector<double> xi(3 * (size_t)B);
+    for (int s = 0; s < B; ++s) {
+        const double* x = xi_host + 3 * s;
+        const double nn = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        for (int a = 0; a < 3; ++a) xi[3 * s + a] = x[a] / nn;
+    }
+    if (cudaMemcpyAsync(ws + pl->off_xi, xi.data(), xi.size() * sizeof(double), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemsetAsync(ws + pl->off_nact, 0, sizeof(int), st) != cudaSuccess)
+        return CCMF_ERR_CUDA;
+    LoopConfig cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.tol = 1.0;
+    cfg.delta = prm->delta;
+    cfg.rho0 = prm->rho0;
+    cfg.bb_corr_min = prm->bb_corr_min;
+    cfg.rho_step_max = prm->rho_step_max;
+    cfg.max_iter = K;
+    cfg.fixed_iters = K;
+    cfg.rho_rule = CCMF_RHO_CONST;
+    cfg.hist_len = 0;
+    cfg.resume = 0;
+    cfg.rho_sched = dsched;
+    cfg.sched_len = K;
+    Ctx<T> c = make_ctx<T>(pl, ws, gamma, gstride, cfg);
+    c.vec_update = false;   // the scalar update pass can also emit z
+    const size_t f6 = (size_t)6 * g.N * B;
+    T* ckpt = reinterpret_cast<T*>(aws + L.ckpt);
+    T* e_state = reinterpret_cast<T*>(ws + pl->off_e);
+    T* v_state = reinterpret_cast<T*>(ws + pl->off_v);
+    launch_init<T>(c, st);
+    for (int k = 0; k < K; ++k) {
+        if (k % m == 0) {
+            const size_t cur = (size_t)(k & 1) * f6;
+            T* slot = ckpt + (size_t)(k / m) * 2 * f6;
+            if (cudaMemcpyAsync(slot, e_state + cur, f6 * sizeof(T), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+                cudaMemcpyAsync(slot + f6, v_state + cur, f6 * sizeof(T), cudaMemcpyDeviceToDevice, st) !=
+                    cudaSuccess)
+                return CCMF_ERR_CUDA;
+        }
+        launch_iteration<T>(c, st);
+    }
+    launch_final<T>(c, st, nullptr, nullptr);
+    if (cudaGetLastError() != cudaSuccess) return CCMF_ERR_CUDA;
+    if (results) {
+        std::vector<SolveScalars> sc(B);
+        if (cudaMemcpyAsync(sc.data(), ws + pl->off_sc, sizeof(SolveScalars) * B, cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return CCMF_ERR_CUDA;
+        for (int s = 0; s < B; ++s) {
+            ccmf_result& r = results[s];
+            r.gamma_eff = sc[s].dual;
+            r.gamma_primal = sc[s].primal;
+            r.gamma_dual = sc[s].dual;
+            r.residual = sc[s].residual;
+            r.mean_v_norm = sc[s].mean_v;
+            r.rho = sc[s].rho;
+            r.iters = sc[s].iters;
+            r.converged = 0;
+            r.status = sc[s].status;
+            r.reserved = 0;
+        }
+    }
+
+    // reverse sweep
+    T* zbuf = reinterpret_cast<T*>(aws + L.z);
+    T* ebar = reinterpret_cast<T*>(aws + L.ebar);
+    T* vbar = reinterpret_cast<T*>(aws + L.vbar);
+    T* zbar = reinterpret_cast<T*>(aws + L.zbar);
+    T* y = reinterpret_cast<T*>(aws + L.y);
+    T* my = reinterpret_cast<T*>(aws + L.my);
+    T* zero = reinterpret_cast<T*>(aws + L.zero);
+    SolveScalars* dummy = reinterpret_cast<SolveScalars*>(aws + L.dummy);
+    if (cudaMemsetAsync(zero, 0, f6 * sizeof(T), st) != cudaSuccess ||
+        cudaMemsetAsync(grad, 0, sizeof(T) * (size_t)g.N * B, st) != cudaSuccess)
+        return CCMF_ERR_CUDA;
+    launch_adj_seed<T>(c, ebar, vbar, dummy, st);
+    const int nseg = (K + m - 1) / m;
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+        const int k0 = sg * m, k1 = (k0 + m < K) ? k0 + m : K;
+        const size_t cur = (size_t)(k0 & 1) * f6;
+        T* slot = ckpt + (size_t)sg * 2 * f6;
+        if (cudaMemcpyAsync(e_state + cur, slot, f6 * sizeof(T), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(v_state + cur, slot + f6, f6 * sizeof(T), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return CCMF_ERR_CUDA;
+        launch_adj_restore<T>(c, k0, dsched, K, st);
+        for (int k = k0; k < k1; ++k) {
+            Ctx<T> ck = c;
+            ck.p.zout = zbuf + (size_t)(k - k0) * f6;
+            launch_iteration<T>(ck, st);
+        }
+        for (int k = k1 - 1; k >= k0; --k)
+            launch_adj_step<T>(c, zbuf + (size_t)(k - k0) * f6, ebar, vbar, zbar, y, my, zero, dummy, grad, dsched, K,
+                               k, st);
+        if (cudaGetLastError() != cudaSuccess) return CCMF_ERR_CUDA;
+    }
+    return CCMF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ccmf_adjoint_workspace_bytes(const ccmf_plan* plan, int K, int ckpt_every, size_t* bytes) {
+    if (!plan || !bytes || K < 1 || ckpt_every < 1) return CCMF_ERR_INVALID_ARG;
+    *bytes = adj_layout(plan, K, ckpt_every).total;
+    return CCMF_OK;
+}
+
+int ccmf_adjoint(ccmf_plan* plan, const void* gamma, long long gamma_stride, const double* xi_bar,
+                 const ccmf_params* params, int K, int ckpt_every, const double* rho_schedule, void* workspace,
+                 size_t workspace_bytes, void* adj_workspace, size_t adj_workspace_bytes, void* grad_gamma,
+                 double* rho_out, ccmf_result* results, void* stream) {
+    if (!plan || !gamma || !xi_bar || !grad_gamma || gamma_stride < 0 || K < 1 || ckpt_every < 1)
+        return CCMF_ERR_INVALID_ARG;
+    if (!rho_schedule && K > kHistCap) return CCMF_ERR_INVALID_ARG;
+    ccmf_params prm;
+    if (params)
+        prm = *params;
+    else
+        ccmf_params_default(&prm);
+    if (!(prm.delta > 0.0 && prm.delta < 1.0) || prm.rho_rule < CCMF_RHO_BB || prm.rho_rule > CCMF_RHO_LTD ||
+        !(prm.rho_step_max >= 1.0))
+        return CCMF_ERR_INVALID_ARG;
+    for (int s = 0; s < plan->batch; ++s) {
+        const double* x = xi_bar + 3 * s;
+        const double nn = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+        if (!isfinite(x[0]) || !isfinite(x[1]) || !isfinite(x[2]) || !(nn > 0.0) || !isfinite(nn))
+            return CCMF_ERR_INVALID_ARG;
+    }
+    if (rho_schedule)
+        for (size_t q = 0; q < (size_t)K * plan->batch; ++q)
+            if (!(rho_schedule[q] > 0.0) || !isfinite(rho_schedule[q])) return CCMF_ERR_INVALID_ARG;
+    if (!is_device_ptr(gamma) || !is_device_ptr(grad_gamma)) return CCMF_ERR_INVALID_ARG;
+    if (!workspace || workspace_bytes < plan->total || ((uintptr_t)workspace & 255u) != 0) return CCMF_ERR_WORKSPACE;
+    const size_t need = adj_layout(plan, K, ckpt_every).total;
+    if (!adj_workspace || adj_workspace_bytes < need || ((uintptr_t)adj_workspace & 255u) != 0)
+        return CCMF_ERR_WORKSPACE;
+    if (cudaSetDevice(plan->device) != cudaSuccess) return CCMF_ERR_CUDA;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    unsigned char* ws = reinterpret_cast<unsigned char*>(workspace);
+    unsigned char* aws = reinterpret_cast<unsigned char*>(adj_workspace);
+    if (plan->prec == CCMF_FP64)
+        return adjoint_impl<double>(plan, reinterpret_cast<const double*>(gamma), gamma_stride, xi_bar, &prm, K,
+                                    ckpt_every, rho_schedule, ws, aws, reinterpret_cast<double*>(grad_gamma), rho_out,
+                                    results, st);
+    return adjoint_impl<float>(plan, reinterpret_cast<const float*>(gamma), gamma_stride, xi_bar, &prm, K, ckpt_every,
+                               rho_schedule, ws, aws, reinterpret_cast<float*>(grad_gamma), rho_out, results, st);
 }
 
 }  // extern "C"

@@ -9,4 +9,8 @@ template void launch_iteration<double>(const Ctx<double>&, cudaStream_t);
 template void launch_iteration_range<double>(const Ctx<double>&, int, int, cudaStream_t);
 template void launch_iteration_timed<double>(const Ctx<double>&, cudaStream_t, cudaEvent_t*);
 template void launch_final<double>(const Ctx<double>&, cudaStream_t, double*, double*);
+template void launch_adj_restore<double>(const Ctx<double>&, int, const double*, int, cudaStream_t);
+template void launch_adj_seed<double>(const Ctx<double>&, double*, double*, SolveScalars*, cudaStream_t);
+template void launch_adj_step<double>(const Ctx<double>&, const double*, double*, double*, double*, double*, double*, const double*, SolveScalars*, double*,
+                                   const double*, int, int, cudaStream_t);
 }  // namespace ccmf

@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kThreads) k_init_stats(Geom g, Ptrs<T> p, Loop
         if (bad > 0.0) status = 5;                        // CCMF_ERR_NUMERICAL
         else if (!(rho0 > 0.0) || !isfinite(rho0)) status = 1;  // gamma identically zero
         if (!cfg.resume) {
-            S.rho = rho0;
+            S.rho = cfg.rho_sched ? cfg.rho_sched[(size_t)s * cfg.sched_len] : rho0;
             S.iters = 0;
         }
         S.status = status;
@@ -605,7 +605,8 @@ template <typename T, bool OUT, int RULE = -1>
 __device__ __forceinline__ void voxel_step(const StepConsts<T>& K, const T (&ec)[6], const T (&vc)[6], T gm, T ph0,
                                            const T (&php)[3], const T (&phm)[3], const T (&e2p)[3],
                                            const T (&v2p)[3], const T (&e1m)[3], const T (&v1m)[3],
-                                           T (&acc)[kNSum], T (&eo)[6], T (&vo)[6], T (&flow)[3]) {
+                                           T (&acc)[kNSum], T (&eo)[6], T (&vo)[6], T (&flow)[3],
+                                           T* zo = nullptr) {
     T w[6], xh[6];
 #pragma unroll
     for (int c = 0; c < 6; ++c) w[c] = ec[c] - vc[c] * K.irho;
@@ -642,6 +643,10 @@ __device__ __forceinline__ void voxel_step(const StepConsts<T>& K, const T (&ec)
         for (int c = 0; c < 6; ++c) {
             z[c] = vc[c] + K.rho * (K.alpha * xh[c] - K.beta * ec[c]);
             nz2 += z[c] * z[c];
+        }
+        if (zo) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) zo[c] = z[c];
         }
         const T scale = Proj<T>::scale(nz2, gm);
         T dvde = T(0), dede = T(0), dvdv = T(0), vv = T(0), ee = T(0);
@@ -716,7 +721,9 @@ __device__ void update_epilogue(const Geom& g, const Ptrs<T>& p, const LoopConfi
     }
     double rho_new = rho_d;
     const double lo = rho_d / cfg.rho_step_max, hi = rho_d * cfg.rho_step_max;
-    if (cfg.rho_rule == 0) {
+    if (cfg.rho_sched) {
+        if (kk + 1 < cfg.sched_len) rho_new = cfg.rho_sched[(size_t)s * cfg.sched_len + kk + 1];
+    } else if (cfg.rho_rule == 0) {
         const double sve = sums[kSumDvDe], see = sums[kSumDeDe], svv = sums[kSumDvDv];
         if (sve > 0.0 && see > 0.0 && svv > 0.0 && sve / sqrt(svv * see) > cfg.bb_corr_min)
             rho_new = fmin(fmax(sve / see, lo), hi);
@@ -807,8 +814,15 @@ __global__ void __launch_bounds__(kThreads) k_update(Geom g, Ptrs<T> p, LoopConf
             e1m[a] = e[a * N + nb_m[a]];
             v1m[a] = v[a * N + nb_m[a]];
         }
-        T eo[6], vo[6], fl[3];
-        voxel_step<T, OUT>(K, ec, vc, gam[lin], phi[lin], php, phm, e2p, v2p, e1m, v1m, acc, eo, vo, fl);
+        T eo[6], vo[6], fl[3], zz[6];
+        voxel_step<T, OUT>(K, ec, vc, gam[lin], phi[lin], php, phm, e2p, v2p, e1m, v1m, acc, eo, vo, fl,
+                           (!OUT && p.zout) ? zz : nullptr);
+        if (!OUT && p.zout) {
+            // the pre-projection point z = v + rho xi of this update, kept for the reverse pass
+            T* zo = p.zout + (size_t)s * 6 * N;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) zo[c * N + lin] = zz[c];
+        }
         if (OUT) {
             if (p.cut) {
                 T* cut = p.cut + (size_t)s * 6 * N;
@@ -1428,6 +1442,103 @@ __global__ void __launch_bounds__(NT) k_update_pipe(Geom g, Ptrs<T> p, LoopConfi
         __syncthreads();
     }
     update_epilogue<T, false, NT>(g, p, cfg, S, s, rho_d, acc);
+}
+
+// ---------------------------------------------------------------------------
+// Reverse mode of one update with rho fixed (the derivation is in the oracle's
+// gradient module and the design notes). Per voxel, with u = vbar' - ebar'/rho:
+//   zbar = ebar'/rho + J_C(z) u,  gbar += [|z| > gamma] (z/|z|) . u,
+//   y = a rho zbar  (then My = M y by the forward passes with xi_bar = 0),
+//   ebar = My - b rho zbar,  vbar = zbar - My / rho.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_adj_pre(Geom g, const T* __restrict__ z, const T* __restrict__ gamma,
+                                                      long long gstride, const T* __restrict__ ebar,
+                                                      const T* __restrict__ vbar, const double* __restrict__ rho_k,
+                                                      int sched_len, int k, double a, T* __restrict__ zbar,
+                                                      T* __restrict__ y, T* __restrict__ gbar) {
+    const int s = blockIdx.y;
+    const long long N = g.N;
+    const T rho = (T)rho_k[(size_t)s * sched_len + k];
+    const T irho = T(1) / rho;
+    const T ar = (T)(a * (double)rho);
+    const T* zs = z + (size_t)s * 6 * N;
+    const T* es = ebar + (size_t)s * 6 * N;
+    const T* vs = vbar + (size_t)s * 6 * N;
+    const T* gs = gamma + (size_t)s * gstride;
+    T* zb = zbar + (size_t)s * 6 * N;
+    T* ys = y + (size_t)s * 6 * N;
+    T* gb = gbar + (size_t)s * N;
+    const long long stride = (long long)gridDim.x * kThreads;
+    for (long long lin = (long long)blockIdx.x * kThreads + threadIdx.x; lin < N; lin += stride) {
+        T zc[6], u[6];
+        T nz2 = T(0), zu = T(0);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            zc[c] = zs[c * N + lin];
+            u[c] = vs[c * N + lin] - es[c * N + lin] * irho;
+            nz2 += zc[c] * zc[c];
+        }
+        const T gm = gs[lin];
+        const T nz = Real<T>::sqrt_(nz2);
+        const bool clip = nz > gm;
+        if (clip) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) zu += zc[c] * u[c];
+            zu /= nz;
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            T ju = u[c];
+            if (clip) ju = (gm / nz) * (u[c] - zc[c] / nz * zu);
+            const T zbc = es[c * N + lin] * irho + ju;
+            zb[c * N + lin] = zbc;
+            ys[c * N + lin] = ar * zbc;
+        }
+        if (clip) gb[lin] += zu;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_adj_post(Geom g, const T* __restrict__ zbar, const T* __restrict__ my,
+                                                       const double* __restrict__ rho_k, int sched_len, int k,
+                                                       double b, T* __restrict__ ebar, T* __restrict__ vbar) {
+    const int s = blockIdx.y;
+    const long long N6 = 6 * g.N;
+    const T rho = (T)rho_k[(size_t)s * sched_len + k];
+    const T irho = T(1) / rho;
+    const T br = (T)(b * (double)rho);
+    const T* zb = zbar + (size_t)s * N6;
+    const T* m = my + (size_t)s * N6;
+    T* eb = ebar + (size_t)s * N6;
+    T* vb = vbar + (size_t)s * N6;
+    const long long stride = (long long)gridDim.x * kThreads;
+    for (long long q = (long long)blockIdx.x * kThreads + threadIdx.x; q < N6; q += stride) {
+        const T zq = zb[q], mq = m[q];
+        eb[q] = mq - br * zq;
+        vb[q] = zq - mq * irho;
+    }
+}
+
+// seed of the reverse pass: vbar = A xi_bar / N (gradient of <xi_bar, A* v>), ebar = 0
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_adj_seed(Geom g, const SolveScalars* __restrict__ sc, T* __restrict__ ebar,
+                                                       T* __restrict__ vbar) {
+    const int s = blockIdx.y;
+    const long long N = g.N;
+    const double h = 0.70710678118654752440084436210485 / (double)N;
+    const T a0 = (T)(sc[s].xi[0] * h), a1 = (T)(sc[s].xi[1] * h), a2 = (T)(sc[s].xi[2] * h);
+    T* eb = ebar + (size_t)s * 6 * N;
+    T* vb = vbar + (size_t)s * 6 * N;
+    const long long stride = (long long)gridDim.x * kThreads;
+    for (long long lin = (long long)blockIdx.x * kThreads + threadIdx.x; lin < N; lin += stride) {
+        const T av[3] = {a0, a1, a2};
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            eb[c * N + lin] = T(0);
+            vb[c * N + lin] = av[c % 3];
+        }
+    }
 }
 
 }  // namespace ccmf

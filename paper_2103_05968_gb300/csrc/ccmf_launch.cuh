@@ -244,4 +244,57 @@ void launch_final(const Ctx<T>& c, cudaStream_t st, T* cut, T* flow) {
     launch_passes<T, true>(c, p, st, NoHook());
 }
 
+// ---- reverse mode (adjoint) helpers ------------------------------------------
+template <typename T>
+__global__ void k_adj_restore(SolveScalars* sc, int batch, int k0, const double* __restrict__ sched, int sched_len) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= batch) return;
+    sc[s].iters = k0;
+    sc[s].call_start = 0;
+    sc[s].rho = sched[(size_t)s * sched_len + k0];
+    sc[s].active = 1;
+    sc[s].counter = 0;
+}
+
+template <typename T>
+__global__ void k_adj_dummy(SolveScalars* sc, int batch) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= batch) return;
+    SolveScalars z = {};
+    z.rho = 1.0;   // w = e - v / rho with e = y, v = 0: the passes apply M to y
+    sc[s] = z;
+}
+
+template <typename T>
+void launch_adj_restore(const Ctx<T>& c, int k0, const double* sched, int sched_len, cudaStream_t st) {
+    k_adj_restore<T><<<(unsigned)ceil_div(c.g.batch, 128), 128, 0, st>>>(c.p.sc, c.g.batch, k0, sched, sched_len);
+}
+
+template <typename T>
+void launch_adj_seed(const Ctx<T>& c, T* ebar, T* vbar, SolveScalars* dummy, cudaStream_t st) {
+    dim3 grid((unsigned)c.sh.grid_update, (unsigned)c.g.batch);
+    k_adj_seed<T><<<grid, kThreads, 0, st>>>(c.g, c.p.sc, ebar, vbar);
+    k_adj_dummy<T><<<(unsigned)ceil_div(c.g.batch, 128), 128, 0, st>>>(dummy, c.g.batch);
+}
+
+// One reverse step k: zbar, y from (ebar, vbar, z^k); M y by the forward passes
+// (final-evaluation mode, xi_bar = 0, e = y, v = 0); then ebar, vbar.
+template <typename T>
+void launch_adj_step(const Ctx<T>& c, const T* zk, T* ebar, T* vbar, T* zbar, T* y, T* my, const T* zero,
+                     SolveScalars* dummy, T* grad, const double* sched, int sched_len, int k, cudaStream_t st) {
+    const double a = 2.0 * (1.0 - c.cfg.delta), b = 1.0 - 2.0 * c.cfg.delta;
+    dim3 grid((unsigned)c.sh.grid_update, (unsigned)c.g.batch);
+    const T* gam = c.p.gptrs ? nullptr : c.p.gamma;
+    k_adj_pre<T><<<grid, kThreads, 0, st>>>(c.g, zk, gam, c.p.gstride, ebar, vbar, sched, sched_len, k, a, zbar, y,
+                                             grad);
+    Ctx<T> cm = c;
+    cm.p.e = y;
+    cm.p.v = const_cast<T*>(zero);
+    cm.p.sstride = 0;
+    cm.p.sc = dummy;
+    cm.p.zout = nullptr;
+    launch_final<T>(cm, st, my, nullptr);
+    k_adj_post<T><<<grid, kThreads, 0, st>>>(c.g, zbar, my, sched, sched_len, k, b, ebar, vbar);
+}
+
 }  // namespace ccmf

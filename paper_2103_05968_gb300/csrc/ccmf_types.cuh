@@ -46,6 +46,8 @@ static_assert(sizeof(SolveScalars) <= 256, "scalar slot");
 struct LoopConfig {
     double tol, delta, rho0, bb_corr_min, rho_step_max;
     int max_iter, fixed_iters, rho_rule, hist_len, resume;
+    const double* rho_sched;  // replayed penalties rho^k = rho_sched[s * sched_len + k] (null: adaptive rule)
+    int sched_len;
 };
 
 struct Geom {
@@ -73,6 +75,7 @@ struct Ptrs {
     T* flow;              // [batch][3][N] (final pass, may be null)
     int run_all;          // 1: passes run for every solve (final evaluation), 0: active solves only
     int s0;               // first solve of this launch (blockIdx.y counts from it)
+    T* zout;              // when not null the (scalar) update pass also writes z = v + rho xi, [batch][6][N]
 };
 
 struct LaunchShape {

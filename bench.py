@@ -244,6 +244,92 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
+def graph_ms_per_iter(plan, gamma_dev, normals, iters=30):
+    """Device time per iteration of the captured loop (CUDA events on the launching stream)."""
+    import torch
+    from paper_2103_05968_gb300 import ccmf
+    p = ccmf.Params(fixed_iters=iters, check_every=iters, resume=1, history_len=0)
+    plan.solve(gamma_dev, normals, p, want_results=False)   # capture
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(gamma_dev.device)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    plan.solve(gamma_dev, normals, p, want_results=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / iters
+
+
+def first_persistent(values, ref, rel):
+    """Number of updates after which |values[k] - ref| / |ref| <= rel holds from there on
+    (values[k] is the max-flow value at iteration k), or None if the last one misses."""
+    ok = np.abs(np.asarray(values) - ref) <= rel * abs(ref)
+    if len(ok) == 0 or not ok[-1]:
+        return None
+    bad = np.nonzero(~ok)[0]
+    return int(bad[-1] + 1) if len(bad) else 0
+
+
+def time_to_accuracy(gamma_np, normals, dev, rel=1e-5, ref_tol=1e-7, max_iter=4000):
+    """FP32-mixed against plain FP64 on the GPU at relative gamma_eff error <= rel.
+
+    Reference gamma*: the FP64 solve run to the Eq. 31 criterion with tol ref_tol. For
+    each precision the max-flow value <xi_bar, A* v^k> is read from the history ring at
+    every iteration k; the iterations to accuracy are the first k after which it stays
+    within rel of gamma*; time = iterations x device time per iteration of that precision."""
+    import torch
+    from paper_2103_05968_gb300 import ccmf
+    B = normals.shape[0]
+    hist_len = min(max_iter, 4096)
+    out = {"rel_err": rel, "ref": f"FP64 GPU solve to tol {ref_tol:g} (Eq. 31), max {max_iter} iterations"}
+    plan64 = ccmf.Plan(gamma_np.shape, batch=B, precision=ccmf.CCMF_FP64, device=dev)
+    g64 = torch.from_numpy(gamma_np.astype(np.float64)).to(dev)
+    res64, _, _ = plan64.solve(g64, normals, ccmf.Params(tol=ref_tol, max_iter=max_iter, history_len=hist_len))
+    h64 = plan64.history(hist_len)
+    ref = np.array([r["gamma_eff"] for r in res64])
+    iters_ref = max(int(r["iters"]) for r in res64)
+    ms64 = graph_ms_per_iter(plan64, g64, normals)
+    plan64.close()
+    plan32 = ccmf.Plan(gamma_np.shape, batch=B, precision=ccmf.CCMF_FP32_MIXED, device=dev)
+    g32 = torch.from_numpy(gamma_np.astype(np.float32)).to(dev)
+    res32, _, _ = plan32.solve(g32, normals, ccmf.Params(fixed_iters=iters_ref, history_len=hist_len))
+    h32 = plan32.history(hist_len)
+    ms32 = graph_ms_per_iter(plan32, g32, normals)
+    plan32.close()
+    k64 = [first_persistent(h64[s][:int(res64[s]["iters"]), 5], ref[s], rel) for s in range(B)]
+    k32 = [first_persistent(h32[s][:, 5], ref[s], rel) for s in range(B)]
+    out.update({"gamma_ref": ref.tolist(), "ref_iters": [int(r["iters"]) for r in res64],
+                "ref_gap_rel": [(r["gamma_primal"] - r["gamma_dual"]) / abs(r["gamma_dual"]) for r in res64],
+                "ref_converged": [bool(r["converged"]) for r in res64],
+                "iters_fp64": k64, "iters_fp32": k32, "ms_per_iter_fp64": ms64, "ms_per_iter_fp32": ms32,
+                "fp32_final_rel_err": [abs(r["gamma_eff"] - ref[s]) / abs(ref[s]) for s, r in enumerate(res32)]})
+    if None not in k64 and None not in k32 and max(k32) > 0:
+        t64, t32 = max(k64) * ms64, max(k32) * ms32
+        out.update({"ms_to_accuracy_fp64": t64, "ms_to_accuracy_fp32": t32, "speedup": t64 / t32})
+    else:
+        out["speedup"] = None
+    return out
+
+
+def cufft_yardstick(shape, B, dev, reps=20):
+    """cuFFT (torch.fft) R2C + C2R of the same B scalar grids: a yardstick beside the
+    solver's own FFT passes, not used by the solver."""
+    import torch
+    x = torch.randn((B,) + tuple(shape), device=dev, dtype=torch.float32)
+    for _ in range(3):
+        y = torch.fft.irfftn(torch.fft.rfftn(x, dim=(1, 2, 3)), s=shape, dim=(1, 2, 3))
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(reps):
+        y = torch.fft.irfftn(torch.fft.rfftn(x, dim=(1, 2, 3)), s=shape, dim=(1, 2, 3))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    del y
+    return ev0.elapsed_time(ev1) / reps
+
+
 def cpu_baseline(name, max_seconds=20.0):
     """The oracle as it stands on the host cores: a bounded sample of the workload
     (one solve of the same grid, as many iterations as fit in about max_seconds)."""
@@ -414,6 +500,20 @@ def run_gpu(args, world, rank, local):
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(name, max_seconds=args.cpu_seconds)
 
+    # FFT passes of the solver beside cuFFT on the same grids (yardstick only)
+    fft_cls = [k for k in kt if k.startswith("k_fft") or k.endswith("rfft_z")]
+    yard = {"cufft_r2c_c2r_ms": cufft_yardstick((n1, n2, n3), B, dev),
+            "solver_fft_passes_ms": sum(kt[k][0] / kt[k][1] for k in fft_cls),
+            "solver_passes": fft_cls,
+            "note": "cuFFT: torch.fft.rfftn + irfftn of B real grids; solver: its forward and inverse FFT "
+                    "passes per iteration (the first also reads e, v and computes the divergence; the plane "
+                    "pass also applies the Poisson symbol), sequential event timing"}
+
+    # FP32-mixed vs plain FP64 time to relative gamma_eff error 1e-5 (default workload, rank 0)
+    tta = None
+    if rank == 0 and world == 1 and name == "boolean128" and esize == 4 and not args.no_speedup:
+        tta = time_to_accuracy(gamma_np, normals, dev)
+
     # kernels launched in the timed region: per iteration one launch of each pass per graph
     # branch, plus setup and gamma statistics, plus the passes of the final evaluation
     nk = len(kt)
@@ -432,6 +532,7 @@ def run_gpu(args, world, rank, local):
                     "note": f"one ccmf_solve from pinned host gamma: H2D {esize * N} B, init, {K} iterations, "
                             "final evaluation, results D2H"},
                 "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
+                "fp32_vs_fp64": tta, "cufft_yardstick": yard,
                 "gamma_eff": [r["gamma_eff"] for r in res]}
         print(json.dumps(line), flush=True)
     plan.close()
@@ -447,6 +548,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-speedup", action="store_true",
+                    help="skip the FP32-mixed vs FP64 time-to-accuracy measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

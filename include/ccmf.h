@@ -156,8 +156,10 @@ int ccmf_state_import(const ccmf_plan* plan, void* workspace, const void* e, con
                       const double* rho, const int* iters, void* stream);
 
 /*
- * Copy the per-solve history ring to host memory: out[batch][max_entries][5]
- * with (k, rho^k, |e^k - xi^{k+1/2}|_L2, |<v^k>|, mean(gamma |xi^{k+1/2}|)) for
+ * Copy the per-solve history ring to host memory: out[batch][max_entries][6]
+ * with (k, rho^k, |e^k - xi^{k+1/2}|_L2, |<v^k>|, mean(gamma |xi^{k+1/2}|),
+ * <xi_bar, mean A* v^k>) -- the last two are the min-cut (Eq. 21) and max-flow
+ * (Eq. 12) values at iteration k -- for
  * the most recent min(max_entries, history_len, iterations) updates, oldest
  * first; *count receives the number of entries written per solve.
  * Synchronises the stream.

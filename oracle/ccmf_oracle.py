@@ -267,7 +267,7 @@ def solve(gamma, xi_bar, params=None, e0=None, v0=None, rho0_state=None, record_
         r = l2_norm(e - xi_half)
         mv = math.sqrt(sum(float(np.mean(v[c])) ** 2 for c in range(6)))
         if record_history:
-            history.append((k, rho, r, mv, mincut_objective(xi_half, gamma)))
+            history.append((k, rho, r, mv, mincut_objective(xi_half, gamma), flow_objective(op_A_adj(v), xi_bar)))
         rho_new = next_rho(rho, params.rho_rule, e, e_new, v, v_new, params)
         e, v, rho = e_new, v_new, rho_new
         k += 1

@@ -34,7 +34,7 @@ CCMF_RHO_BB = 0
 CCMF_RHO_CONST = 1
 CCMF_RHO_LTD = 2
 
-HIST_FIELDS = 5
+HIST_FIELDS = 6
 
 
 class ccmf_params(ctypes.Structure):

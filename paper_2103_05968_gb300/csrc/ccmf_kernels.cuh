@@ -718,6 +718,10 @@ __device__ void update_epilogue(const Geom& g, const Ptrs<T>& p, const LoopConfi
         hrow[2] = r;
         hrow[3] = mv;
         hrow[4] = prim;
+        const double hd = 0.70710678118654752440084436210485;
+        double dual = 0.0;   // <xi_bar, mean A* v^k>, the max-flow value of Eq. 12 at iteration k
+        for (int a = 0; a < 3; ++a) dual += S.xi[a] * hd * (sums[kSumV + a] + sums[kSumV + 3 + a]) / Nd;
+        hrow[5] = dual;
     }
     double rho_new = rho_d;
     const double lo = rho_d / cfg.rho_step_max, hi = rho_d * cfg.rho_step_max;

@@ -21,7 +21,7 @@ enum SumIndex {
     kNSum = 13
 };
 
-constexpr int kHistFields = 5;
+constexpr int kHistFields = 6;
 constexpr int kHistCap = 4096;   // history entries reserved per solve
 constexpr int kThreads = 256;
 

@@ -219,12 +219,13 @@ def test_history_matches_oracle():
     out = gpu_run(gamma, [[1, 0, 0]], ccmf.Params(fixed_iters=40), want=False)
     ref = O.solve(gamma, [1, 0, 0], O.Params(fixed_iters=40))
     h = out["plan"].history()[0]
-    assert h.shape == (40, 5)
+    assert h.shape == (40, 6)
     hr = np.array(ref.history)
     np.testing.assert_array_equal(h[:, 0], hr[:, 0])
     np.testing.assert_allclose(h[:, 1], hr[:, 1], rtol=1e-10)
     np.testing.assert_allclose(h[:, 2], hr[:, 2], rtol=1e-8, atol=1e-13)
     np.testing.assert_allclose(h[:, 4], hr[:, 4], rtol=1e-10)
+    np.testing.assert_allclose(h[:, 5], hr[:, 5], rtol=1e-10, atol=1e-14)
 
 
 def test_invalid_gamma_reported_per_solve():

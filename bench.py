@@ -288,6 +288,7 @@ def time_to_accuracy(gamma_np, normals, dev, rel=1e-5, ref_tol=1e-7, max_iter=40
     h64 = plan64.history(hist_len)
     ref = np.array([r["gamma_eff"] for r in res64])
     iters_ref = max(int(r["iters"]) for r in res64)
+    plan64.autotune(g64, normals, iters=5)   # both precisions timed in their tuned launch shapes
     ms64 = graph_ms_per_iter(plan64, g64, normals)
     plan64.close()
     plan32 = ccmf.Plan(gamma_np.shape, batch=B, precision=ccmf.CCMF_FP32_MIXED, device=dev)
@@ -431,6 +432,16 @@ def run_gpu(args, world, rank, local):
     # initial state + warm-up (W iterations), untimed
     plan.solve(gamma_dev, normals, ccmf.Params(fixed_iters=W, check_every=W))
     torch.cuda.synchronize()
+    # launch-shape autotuner (setup, outside the timed region): coordinate descent over the
+    # update-pass variant, plane pass, lines per block, graph branches and radix schedule
+    tune = None
+    if not args.no_autotune:
+        t_tune = time.perf_counter()
+        best, tune_ms = plan.autotune(gamma_dev, normals, iters=args.tune_iters)
+        tune = {"tuning": best, "ms_per_iter": tune_ms, "seconds": time.perf_counter() - t_tune,
+                "iters_per_candidate": args.tune_iters}
+    else:
+        tune = {"tuning": plan.tuning(), "note": "built-in rules (--no-autotune)"}
     stream = torch.cuda.current_stream(dev)
     p_timed = ccmf.Params(fixed_iters=K, check_every=K, resume=1)
     # capture the loop graph outside the timed region (same key as the timed call)
@@ -532,7 +543,7 @@ def run_gpu(args, world, rank, local):
                     "note": f"one ccmf_solve from pinned host gamma: H2D {esize * N} B, init, {K} iterations, "
                             "final evaluation, results D2H"},
                 "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
-                "fp32_vs_fp64": tta, "cufft_yardstick": yard,
+                "fp32_vs_fp64": tta, "cufft_yardstick": yard, "autotune": tune,
                 "gamma_eff": [r["gamma_eff"] for r in res]}
         print(json.dumps(line), flush=True)
     plan.close()
@@ -548,6 +559,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch-shape rules")
+    ap.add_argument("--tune-iters", type=int, default=10, help="iterations timed per autotuner candidate")
     ap.add_argument("--no-speedup", action="store_true",
                     help="skip the FP32-mixed vs FP64 time-to-accuracy measurement")
     args = ap.parse_args()

@@ -176,6 +176,71 @@ int ccmf_history_export(const ccmf_plan* plan, const void* workspace, double* ou
 int ccmf_kernel_times(const ccmf_plan* plan, double* ms, long long* launches, const char** names,
                       int capacity, int* count);
 
+/*
+ * Launch shape the plan chose, for tests and reports: out[0..7] = {update-pass
+ * variant (0 registers, 1 TMA rows, 2..7 pipelined TMA), plane pass fused (0 / 1),
+ * blocks sharing one (x, y) plane (1 = one block, 2..16 = a thread-block cluster),
+ * z-pass line pairs per block, y-pass lines per block, x-pass lines per block,
+ * update-pass blocks per solve, graph branches}. Writes min(capacity, 8) entries and
+ * returns 8 in *count.
+ */
+int ccmf_plan_launch_info(const ccmf_plan* plan, int* out, int capacity, int* count);
+
+/*
+ * Tuning knobs of a plan: the launch shape of the passes of one iteration (Eq. 30
+ * step) and the radix schedule of its FFTs. None of them changes what is computed;
+ * a different radix schedule or reduction grid changes the rounding only.
+ * In ccmf_plan_set_tuning a negative entry selects the built-in rule.
+ */
+typedef struct {
+    int update_variant;     /* update pass: 0 register vectors, 1 TMA rows, 2..7 pipelined TMA */
+    int plane_blocks;       /* y / x passes: 0 three strided passes, 1 one block per (x, y) plane,
+                               2, 4, 8, 16 a thread-block cluster per plane */
+    int z_pairs_per_block;  /* z passes: line pairs per block, power of two 1..16 */
+    int y_lines_per_block;  /* strided y passes: lines per block, power of two 1..16 */
+    int x_lines_per_block;  /* strided x pass: lines per block, power of two 1..16 */
+    int branches;           /* independent graph branches of a batch, 1..4 */
+    int radix_mode;         /* radix schedule of every axis: 0 radix 8 first, then 4, 2, 3, 5;
+                               1 as 0 but radix 4s in place of a radix 8 + 2 tail; 2 radix 4 at most */
+    int reserved;
+} ccmf_tuning;
+
+/* The plan's current knob values (every entry resolved, none negative). */
+int ccmf_plan_get_tuning(const ccmf_plan* plan, ccmf_tuning* out);
+
+/* Apply knob values. Returns CCMF_ERR_UNSUPPORTED_SIZE (and keeps the current
+ * tuning) when a requested value cannot run on this grid and device, e.g. a
+ * cluster size that does not divide N1 and N2 or whose blocks do not fit. */
+int ccmf_plan_set_tuning(ccmf_plan* plan, const ccmf_tuning* tuning);
+
+/*
+ * Autotuner: times `iters` iterations of the loop (CUDA events on `stream`, after
+ * one untimed run that also captures the graph) for candidate tunings and keeps the
+ * fastest. The search is coordinate descent over the knobs in the order of
+ * ccmf_tuning, starting from the current tuning. It advances the plan's ADMM state
+ * (the workspace must hold a solve of these inputs, as ccmf_solve leaves it), runs
+ * every candidate for `iters` iterations twice, and records the winner in the
+ * library's tuning table under (N1, N2, N3, batch, precision, SM count): plans
+ * created later with that key start from it.
+ *   gamma, gamma_stride, xi_bar, workspace : as for ccmf_solve
+ *   best    : optional host output, the kept tuning
+ *   best_ms : optional host output, its time per iteration in milliseconds
+ * Synchronises the stream.
+ */
+int ccmf_plan_autotune(ccmf_plan* plan, const void* gamma, long long gamma_stride, const double* xi_bar,
+                       void* workspace, size_t workspace_bytes, int iters, ccmf_tuning* best, double* best_ms,
+                       void* stream);
+
+/*
+ * The tuning table as text, one line per key
+ * ("ccmf-tuning N1 N2 N3 batch precision sms : 7 knob values"). Writes at most
+ * capacity bytes (NUL-terminated) and the full length in *length.
+ */
+int ccmf_tuning_export(char* text, size_t capacity, size_t* length);
+
+/* Add the lines of a text written by ccmf_tuning_export to the table (later lines win). */
+int ccmf_tuning_import(const char* text);
+
 /* Enable (1) or disable (0) CUDA-event timing of every loop kernel for later
  * ccmf_solve calls on this plan (events are recorded on the solve's stream
  * inside the captured graph; fixed_iters mode only). */

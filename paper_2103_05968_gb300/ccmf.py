@@ -68,6 +68,21 @@ class ccmf_result(ctypes.Structure):
     ]
 
 
+class ccmf_tuning(ctypes.Structure):
+    _fields_ = [
+        ("update_variant", ctypes.c_int),
+        ("plane_blocks", ctypes.c_int),
+        ("z_pairs_per_block", ctypes.c_int),
+        ("y_lines_per_block", ctypes.c_int),
+        ("x_lines_per_block", ctypes.c_int),
+        ("branches", ctypes.c_int),
+        ("radix_mode", ctypes.c_int),
+        ("reserved", ctypes.c_int),
+    ]
+
+
+TUNING_KEYS = tuple(f[0] for f in ccmf_tuning._fields_ if f[0] != "reserved")
+
 _lib = None
 
 # name -> (restype, argtypes); mirrors include/ccmf.h
@@ -94,6 +109,16 @@ _SIGNATURES = {
                                           ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_char_p),
                                           ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "ccmf_set_kernel_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "ccmf_plan_launch_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_int)]),
+    "ccmf_plan_get_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ccmf_tuning)]),
+    "ccmf_plan_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ccmf_tuning)]),
+    "ccmf_plan_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong,
+                                           ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_size_t,
+                                           ctypes.c_int, ctypes.POINTER(ccmf_tuning), ctypes.POINTER(ctypes.c_double),
+                                           ctypes.c_void_p]),
+    "ccmf_tuning_export": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "ccmf_tuning_import": (ctypes.c_int, [ctypes.c_char_p]),
     "ccmf_adjoint_workspace_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                                      ctypes.POINTER(ctypes.c_size_t)]),
     "ccmf_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong,
@@ -214,6 +239,54 @@ def ccmf_kernel_times(plan):
     code = load_library().ccmf_kernel_times(plan, ms, launches, names, cap, ctypes.byref(cnt))
     n = min(cnt.value, cap)
     return code, {names[i].decode(): (ms[i], launches[i]) for i in range(n)}
+
+
+LAUNCH_INFO_KEYS = ("update_variant", "plane_fused", "plane_blocks", "z_pairs_per_block", "y_lines_per_block",
+                    "x_lines_per_block", "update_blocks", "branches")
+
+
+def ccmf_plan_launch_info(plan):
+    out = (ctypes.c_int * len(LAUNCH_INFO_KEYS))()
+    cnt = ctypes.c_int()
+    code = load_library().ccmf_plan_launch_info(plan, out, len(LAUNCH_INFO_KEYS), ctypes.byref(cnt))
+    return code, {k: int(out[i]) for i, k in enumerate(LAUNCH_INFO_KEYS)}
+
+
+def ccmf_plan_get_tuning(plan):
+    t = ccmf_tuning()
+    code = load_library().ccmf_plan_get_tuning(plan, ctypes.byref(t))
+    return code, {k: getattr(t, k) for k in TUNING_KEYS}
+
+
+def ccmf_plan_set_tuning(plan, tuning):
+    """tuning: dict of knob values (missing knobs = -1, the built-in rule)."""
+    t = ccmf_tuning(**{k: int(tuning.get(k, -1)) for k in TUNING_KEYS})
+    return load_library().ccmf_plan_set_tuning(plan, ctypes.byref(t))
+
+
+def ccmf_plan_autotune(plan, gamma_ptr, gamma_stride, xi_bar, workspace_ptr, workspace_bytes, iters, stream):
+    xi = np.ascontiguousarray(xi_bar, dtype=np.float64).reshape(-1)
+    best = ccmf_tuning()
+    ms = ctypes.c_double()
+    code = load_library().ccmf_plan_autotune(plan, gamma_ptr, int(gamma_stride),
+                                             xi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), workspace_ptr,
+                                             int(workspace_bytes), int(iters), ctypes.byref(best), ctypes.byref(ms),
+                                             stream)
+    return code, {k: getattr(best, k) for k in TUNING_KEYS}, ms.value
+
+
+def ccmf_tuning_export():
+    n = ctypes.c_size_t()
+    code = load_library().ccmf_tuning_export(None, 0, ctypes.byref(n))
+    if code != CCMF_OK:
+        return code, ""
+    buf = ctypes.create_string_buffer(n.value + 1)
+    code = load_library().ccmf_tuning_export(buf, n.value + 1, ctypes.byref(n))
+    return code, buf.value.decode()
+
+
+def ccmf_tuning_import(text):
+    return load_library().ccmf_tuning_import(text.encode())
 
 
 def ccmf_set_kernel_timing(plan, enable):
@@ -416,10 +489,7 @@ class Plan:
 
     def branches(self):
         """Independent graph branches the loop runs the batch in (at most 4, one per solve)."""
-        import os
-        env = os.environ.get("CCMF_BRANCHES")
-        nb = int(env) if env else 4
-        return max(1, min(nb, 4, self.batch))
+        return int(self.tuning()["branches"])
 
     def gradient(self, gamma, normals, K, ckpt_every=20, params=None, rho_schedule=None):
         """d gamma_eff / d gamma through K replayed updates (see ccmf_adjoint in include/ccmf.h).
@@ -453,6 +523,35 @@ class Plan:
         code, t = ccmf_kernel_times(self.handle)
         _check(code, "ccmf_kernel_times")
         return t
+
+    def tuning(self):
+        """The plan's knob values (see ccmf_tuning in include/ccmf.h)."""
+        code, t = ccmf_plan_get_tuning(self.handle)
+        _check(code, "ccmf_plan_get_tuning")
+        return t
+
+    def set_tuning(self, **knobs):
+        """Set knob values by name; the others keep the built-in rule."""
+        _check(ccmf_plan_set_tuning(self.handle, knobs), "ccmf_plan_set_tuning")
+
+    def autotune(self, gamma, normals, iters=10):
+        """Time candidate tunings on this plan's current state and keep the fastest
+        (ccmf_plan_autotune); returns (tuning, ms per iteration)."""
+        torch = self.torch
+        stride = 0 if gamma.dim() == 3 else self.n_voxels
+        normals = np.asarray(normals, dtype=np.float64).reshape(self.batch, 3)
+        with torch.cuda.device(self.device):
+            code, best, ms = ccmf_plan_autotune(self.handle, ctypes.c_void_p(gamma.data_ptr()), stride, normals,
+                                                ctypes.c_void_p(self.ws_ptr), self.workspace_bytes, iters,
+                                                _stream_handle(torch, self.device))
+        _check(code, "ccmf_plan_autotune")
+        return best, ms
+
+    def launch_info(self):
+        """The launch shape the plan chose (update variant, plane pass blocks per plane, ...)."""
+        code, info = ccmf_plan_launch_info(self.handle)
+        _check(code, "ccmf_plan_launch_info")
+        return info
 
 
 class Batch:

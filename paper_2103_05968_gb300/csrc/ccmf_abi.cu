@@ -2,11 +2,15 @@
 // iteration loop (captured CUDA graphs) and state / history / timing access.
 // See include/ccmf.h for the contract of every entry point.
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "../../include/ccmf.h"
@@ -17,6 +21,7 @@ using namespace ccmf;
 namespace ccmf {
 template <typename T> cudaError_t configure_kernels(const LaunchShape&);
 template <typename T> int pipe_blocks_per_sm(int, size_t);
+template <typename T> int plane_cluster_capacity(int, size_t);
 template <typename T> void launch_init(const Ctx<T>&, cudaStream_t);
 template <typename T> void launch_iteration(const Ctx<T>&, cudaStream_t);
 template <typename T> void launch_iteration_range(const Ctx<T>&, int, int, cudaStream_t);
@@ -33,6 +38,7 @@ namespace {
 
 constexpr int kMaxN = 1024;
 constexpr size_t kSmemBudget = 96 * 1024;
+constexpr size_t kSmemMax = 200 * 1024;   // dynamic shared memory of one block, at most
 constexpr int kMaxTimedIters = 2048;
 // update-pass variant per precision, from measurements on GB300 (128^3 x 3 solves):
 // FP32 is bandwidth-bound and best with the 3-stage TMA pipeline of 128 threads,
@@ -47,9 +53,11 @@ constexpr double kPi = 3.14159265358979323846264338327950288;
 
 size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
-// Radix schedule for a line of length n (prime factors 2, 3, 5): 8s first, then
-// 4 / 2, then 3s and 5s. Returns false for unsupported n.
-bool make_axis_plan(int n, AxisPlan* ap) {
+// Radix schedule for a line of length n (prime factors 2, 3, 5). mode 0: 8s first,
+// then 4 / 2, then 3s and 5s; mode 1: as 0, but a power-of-two part of the form
+// 8^a * 2 becomes 8^(a-1) * 4 * 4; mode 2: radix 4 at most. Returns false for
+// unsupported n.
+bool make_axis_plan(int n, AxisPlan* ap, int mode = 0) {
     memset(ap, 0, sizeof(*ap));
     ap->n = n;
     int m = n, st = 0;
@@ -59,7 +67,15 @@ bool make_axis_plan(int n, AxisPlan* ap) {
         m /= r;
         return true;
     };
-    while (m % 8 == 0)
+    int p2 = 1;
+    while ((m / p2) % 2 == 0) p2 *= 2;
+    int n8 = 0, t = p2;
+    while (mode != 2 && t % 8 == 0) {
+        ++n8;
+        t /= 8;
+    }
+    if (mode == 1 && t == 2 && n8 >= 1) --n8;   // 8^a * 2 -> 8^(a-1) * 16 = 8^(a-1) * 4 * 4
+    for (int k = 0; k < n8; ++k)
         if (!push(8)) return false;
     while (m % 4 == 0)
         if (!push(4)) return false;
@@ -128,6 +144,9 @@ struct ccmf_plan {
     cudaStream_t branch_stream[kMaxBranches];
     cudaEvent_t fork_event, join_event[kMaxBranches];
     int branches;    // graph branches of the loop (1 = one chain for the whole batch)
+    int sms;         // SM count of the device
+    int part_cap;    // partial-sum slots per solve reserved in the workspace
+    ccmf_tuning tune;  // knob values of the current launch shape
     int* h_nactive;  // pinned
     // captured loop graph
     cudaGraphExec_t gexec;
@@ -145,6 +164,223 @@ struct ccmf_plan {
 namespace {
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? CCMF_OK : CCMF_ERR_CUDA; }
+
+int device_sms() {
+    int sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        sms = 152;
+    }
+    return sms;
+}
+
+void tuning_auto(ccmf_tuning* t) {
+    t->update_variant = -1;
+    t->plane_blocks = -1;
+    t->z_pairs_per_block = -1;
+    t->y_lines_per_block = -1;
+    t->x_lines_per_block = -1;
+    t->branches = -1;
+    t->radix_mode = 0;
+    t->reserved = 0;
+}
+
+bool pow2_in(int x, int lo, int hi) { return x >= lo && x <= hi && (x & (x - 1)) == 0; }
+
+// Knob values -> launch shape of the plan's grid. A negative knob takes the built-in
+// rule (the environment overrides CCMF_UPDATE_VARIANT, CCMF_PLANE_FUSED,
+// CCMF_PLANE_CLUSTER and CCMF_BRANCHES apply to those only). Returns
+// CCMF_ERR_UNSUPPORTED_SIZE when an explicit knob cannot run here; `res` receives
+// every knob resolved.
+int shape_for(const ccmf_plan* pl, const ccmf_tuning& t, LaunchShape* out, ccmf_tuning* res) {
+    const int n1 = pl->n1, n2 = pl->n2, n3 = pl->n3, batch = pl->batch;
+    const bool f64 = pl->prec == CCMF_FP64;
+    const size_t cs = 2 * pl->esize;
+    const int sms = pl->sms;
+    LaunchShape sh;
+    memset(&sh, 0, sizeof(sh));
+    ccmf_tuning r = t;
+    if (r.radix_mode < 0) r.radix_mode = 0;
+    if (r.radix_mode > 2) return CCMF_ERR_UNSUPPORTED_SIZE;
+    // FFT passes: lines per block (powers of two), shared memory = twiddles + 2 tiles
+    auto smem_lines = [&](int n, int L) { return ((size_t)n + 2 * (size_t)n * (L + 1)) * cs; };
+    auto lines_for = [&](int n) {
+        long long L = ((long long)(kSmemBudget / cs) - n) / (2LL * n) - 1;
+        return pow2_floor(L, 16);
+    };
+    auto pick = [&](int want, int n, int* L) {
+        if (want < 0) {
+            *L = lines_for(n);
+            return true;
+        }
+        if (!pow2_in(want, 1, 16) || smem_lines(n, want) > kSmemMax) return false;
+        *L = want;
+        return true;
+    };
+    if (!pick(r.z_pairs_per_block, n3, &sh.pairs_per_block) || !pick(r.y_lines_per_block, n2, &sh.lpb_y) ||
+        !pick(r.x_lines_per_block, n1, &sh.lpb_x))
+        return CCMF_ERR_UNSUPPORTED_SIZE;
+    sh.smem_z = smem_lines(n3, sh.pairs_per_block);
+    sh.smem_y = smem_lines(n2, sh.lpb_y);
+    sh.smem_x = smem_lines(n1, sh.lpb_x);
+    r.z_pairs_per_block = sh.pairs_per_block;
+    r.y_lines_per_block = sh.lpb_y;
+    r.x_lines_per_block = sh.lpb_x;
+    long long gu = (pl->g.N + kThreads - 1) / kThreads;
+    if (gu > 608) gu = 608;
+    sh.grid_update = (int)gu;
+    // TMA-staged update: tiles of J z rows with J * N3 <= 512 (FP32) / 256 (FP64) voxels,
+    // J a power of two dividing N2; two stages must fit the shared memory of a block
+    const int tv_max = f64 ? 256 : 512;
+    const int W = f64 ? 2 : 4;
+    int J = 1;
+    while (2 * J * n3 <= tv_max && n2 % (2 * J) == 0) J *= 2;
+    const size_t smem_tma = 2 * (size_t)tma_stage_elems(J * n3, n3) * pl->esize + 16;
+    sh.tma_rows = (n3 % W == 0 && smem_tma <= kSmemMax) ? J : 0;
+    sh.smem_tma = smem_tma;
+    long long ntiles = (long long)n1 * (n2 / J);
+    long long gt = (2LL * sms + batch - 1) / batch;
+    if (gt > ntiles) gt = ntiles;
+    if (gt < 1) gt = 1;
+    sh.grid_tma = (int)gt;
+    // update variant: a pipelined update tile is one W-group per thread, TV = threads * W
+    // voxels = whole z rows (or z segments)
+    int variant = r.update_variant;
+    const bool explicit_variant = variant >= 0;
+    if (!explicit_variant) {
+        const char* env = getenv("CCMF_UPDATE_VARIANT");
+        const int vdef = f64 ? kDefaultUpdateVariantF64 : kDefaultUpdateVariantF32;
+        variant = env ? atoi(env) : vdef;
+        if (variant < 0 || variant > 7) variant = vdef;
+    }
+    if (variant > 7) return CCMF_ERR_UNSUPPORTED_SIZE;
+    sh.upd_variant = 0;
+    if (variant >= 2) {
+        const int vw = f64 ? 1 : 2;
+        const int tv = kUpdatePipe[variant][0] * vw;
+        const int stages = kUpdatePipe[variant][1];
+        const bool rows_ok = n3 <= tv && tv % n3 == 0 && n2 % (tv / n3) == 0;
+        const bool seg_ok = n3 > tv && n3 % tv == 0;
+        if (n3 % W == 0 && (rows_ok || seg_ok)) {
+            const int kt = seg_ok ? tv : n3;
+            const size_t smem =
+                (size_t)stages * (size_t)pipe_stage_elems(tv, kt, seg_ok, 16 / (int)pl->esize) * pl->esize +
+                8 * stages;
+            const int nb = f64 ? pipe_blocks_per_sm<double>(variant, smem) : pipe_blocks_per_sm<float>(variant, smem);
+            if (nb > 0) {
+                sh.upd_variant = variant;
+                sh.smem_pipe = smem;
+                long long nt = (long long)n1 * (n2 / (tv / kt)) * (n3 / kt);
+                long long gp = ((long long)nb * sms + batch - 1) / batch;
+                if (gp > nt) gp = nt;
+                sh.grid_pipe = (int)(gp < 1 ? 1 : gp);
+            }
+        }
+    }
+    if (sh.upd_variant == 0 && variant >= 1 && sh.tma_rows > 0) sh.upd_variant = 1;
+    if (explicit_variant && sh.upd_variant != variant) return CCMF_ERR_UNSUPPORTED_SIZE;
+    r.update_variant = sh.upd_variant;
+    sh.grid_partials = std::max(sh.grid_update, sh.grid_tma);
+    if (sh.upd_variant >= 2) sh.grid_partials = std::max(sh.grid_partials, sh.grid_pipe);
+    // y / x passes: one block per k_z plane when the plane fits its shared memory, a
+    // cluster of C blocks (C divides n1 and n2) sharing the plane through distributed
+    // shared memory, or the three strided passes
+    sh.plane_fused = 0;
+    sh.plane_cluster = 1;
+    sh.smem_plane = 0;
+    const size_t smem1 = ((size_t)n1 + n2 + (size_t)n1 * (n2 + 1)) * cs;
+    const bool one_fits = (long long)n1 * n2 <= kPlaneMax && smem1 <= kSmemMax;
+    int pb = r.plane_blocks;
+    if (pb < 0) {
+        const char* envp = getenv("CCMF_PLANE_FUSED");
+        const char* envc = getenv("CCMF_PLANE_CLUSTER");
+        if (envp && atoi(envp) == 0)
+            pb = 0;
+        else if (envc && atoi(envc) > 0)
+            pb = atoi(envc);
+        else
+            pb = one_fits ? 1 : 0;
+    }
+    if (pb == 1) {
+        if (!one_fits) return CCMF_ERR_UNSUPPORTED_SIZE;
+        sh.plane_fused = 1;
+        sh.smem_plane = smem1;
+    } else if (pb >= 2) {
+        if (!pow2_in(pb, 2, 16) || n1 % pb != 0 || n2 % pb != 0) return CCMF_ERR_UNSUPPORTED_SIZE;
+        const long long emax = (long long)(f64 ? PlaneRegs<double>::M : PlaneRegs<float>::M) * kPlaneClusterThreads;
+        if ((long long)n1 * n2 / pb > emax) return CCMF_ERR_UNSUPPORTED_SIZE;
+        const long long r1 = n1 / pb, r2 = n2 / pb;
+        const long long tile = std::max(r1 * (n2 + 1), r2 * (n1 + 1));
+        const size_t smem = ((size_t)n1 + n2 + (size_t)tile) * cs;
+        if (smem > kSmemMax) return CCMF_ERR_UNSUPPORTED_SIZE;
+        const int cap = f64 ? plane_cluster_capacity<double>(pb, smem) : plane_cluster_capacity<float>(pb, smem);
+        if (cap < 1) return CCMF_ERR_UNSUPPORTED_SIZE;
+        sh.plane_fused = 1;
+        sh.plane_cluster = pb;
+        sh.smem_plane = smem;
+        sh.div_r1 = make_fastdiv((unsigned)r1);
+        sh.div_r2 = make_fastdiv((unsigned)r2);
+    } else if (pb != 0) {
+        return CCMF_ERR_UNSUPPORTED_SIZE;
+    }
+    r.plane_blocks = sh.plane_fused ? sh.plane_cluster : 0;
+    // graph branches of a batch (never more than the solves)
+    int nb = r.branches;
+    if (nb < 0) {
+        const char* envb = getenv("CCMF_BRANCHES");
+        nb = envb ? atoi(envb) : kMaxBranches;
+        if (nb < 1) nb = 1;
+        if (nb > kMaxBranches) nb = kMaxBranches;
+    }
+    if (nb < 1 || nb > kMaxBranches) return CCMF_ERR_UNSUPPORTED_SIZE;
+    r.branches = std::min(nb, batch);
+    r.reserved = 0;
+    *out = sh;
+    if (res) *res = r;
+    return CCMF_OK;
+}
+
+// Partial-sum slots per solve the workspace reserves: the largest grid of any update
+// variant, so that every tuning fits the same workspace.
+int partials_capacity(const ccmf_plan* pl) {
+    int cap = std::max(608, pl->sh.grid_partials);
+    for (int v = 0; v <= 7; ++v) {
+        ccmf_tuning t;
+        tuning_auto(&t);
+        t.update_variant = v;
+        LaunchShape sh;
+        if (shape_for(pl, t, &sh, nullptr) == CCMF_OK) cap = std::max(cap, sh.grid_partials);
+    }
+    return cap;
+}
+
+// ---- the tuning table: (N1, N2, N3, batch, precision, SM count) -> knob values ----
+struct TuneKey {
+    int n1, n2, n3, batch, prec, sms;
+    bool operator<(const TuneKey& o) const {
+        const int a[6] = {n1, n2, n3, batch, prec, sms}, b[6] = {o.n1, o.n2, o.n3, o.batch, o.prec, o.sms};
+        return std::lexicographical_compare(a, a + 6, b, b + 6);
+    }
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, ccmf_tuning> g_tune_table;
+
+TuneKey tune_key(const ccmf_plan* pl) { return TuneKey{pl->n1, pl->n2, pl->n3, pl->batch, pl->prec, pl->sms}; }
+
+bool tuning_lookup(const ccmf_plan* pl, ccmf_tuning* t) {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_table.find(tune_key(pl));
+    if (it == g_tune_table.end()) return false;
+    *t = it->second;
+    return true;
+}
+
+void tuning_store(const ccmf_plan* pl, const ccmf_tuning& t) {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_table[tune_key(pl)] = t;
+}
+
 
 
 bool is_device_ptr(const void* ptr) {
@@ -384,6 +620,59 @@ int solve_impl(ccmf_plan* pl, const void* gamma_in, long long gstride_in, const 
 
 }  // namespace
 
+
+// Symbol tables of the x and y axes in the digit-reversed order of the plan's radix
+// schedule, copied into the plan's existing device buffers.
+int upload_rsym(ccmf_plan* pl) {
+    const int nn[2] = {pl->n1, pl->n2};
+    for (int a = 0; a < 2; ++a) {
+        const int n = nn[a];
+        std::vector<double> rs((size_t)n);
+        for (int t = 0; t < n; ++t) {
+            const double sn = sin(kPi * (double)digit_reversed_frequency(pl->ax[a], t) / (double)n);
+            rs[t] = 4.0 * sn * sn;
+        }
+        cudaError_t e;
+        if (pl->prec == CCMF_FP64) {
+            e = cudaMemcpy(pl->rsym[a], rs.data(), rs.size() * 8, cudaMemcpyHostToDevice);
+        } else {
+            std::vector<float> rf(rs.begin(), rs.end());
+            e = cudaMemcpy(pl->rsym[a], rf.data(), rf.size() * 4, cudaMemcpyHostToDevice);
+        }
+        if (e != cudaSuccess) return CCMF_ERR_CUDA;
+    }
+    return CCMF_OK;
+}
+
+// Switch the plan to the knob values t (resolved against the built-in rules).
+int apply_tuning(ccmf_plan* pl, const ccmf_tuning& t) {
+    LaunchShape sh;
+    ccmf_tuning res;
+    int rc = shape_for(pl, t, &sh, &res);
+    if (rc != CCMF_OK) return rc;
+    if (sh.grid_partials > pl->part_cap) return CCMF_ERR_UNSUPPORTED_SIZE;
+    if (cudaSetDevice(pl->device) != cudaSuccess) return CCMF_ERR_CUDA;
+    const cudaError_t e = pl->prec == CCMF_FP64 ? configure_kernels<double>(sh) : configure_kernels<float>(sh);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return CCMF_ERR_UNSUPPORTED_SIZE;
+    }
+    if (res.radix_mode != pl->tune.radix_mode) {
+        const int nn[3] = {pl->n1, pl->n2, pl->n3};
+        AxisPlan ax[3];
+        for (int a = 0; a < 3; ++a)
+            if (!make_axis_plan(nn[a], &ax[a], res.radix_mode)) return CCMF_ERR_UNSUPPORTED_SIZE;
+        for (int a = 0; a < 3; ++a) pl->ax[a] = ax[a];
+        rc = upload_rsym(pl);
+        if (rc != CCMF_OK) return rc;
+    }
+    destroy_graph(pl);
+    pl->sh = sh;
+    pl->tune = res;
+    pl->branches = res.branches;
+    return CCMF_OK;
+}
+
 extern "C" {
 
 void ccmf_params_default(ccmf_params* p) {
@@ -449,80 +738,23 @@ int ccmf_plan_create(int n1, int n2, int n3, int batch, int precision, ccmf_plan
     g.div_n3h = make_fastdiv((unsigned)pl->n3h);
     g.div_n1 = make_fastdiv((unsigned)n1);
 
-    // launch shape
+    // launch shape: the tuning table's entry for this key, else the built-in rules
+    pl->sms = device_sms();
+    ccmf_tuning auto_t;
+    tuning_auto(&auto_t);
+    ccmf_tuning want_t = auto_t;
+    const bool cached = tuning_lookup(pl, &want_t);
+    int src = shape_for(pl, want_t, &pl->sh, &pl->tune);
+    if (src != CCMF_OK && cached) src = shape_for(pl, auto_t, &pl->sh, &pl->tune);
+    if (src != CCMF_OK) {
+        delete pl;
+        return src;
+    }
+    if (pl->tune.radix_mode != 0)
+        for (int a = 0; a < 3; ++a) make_axis_plan(nn[a], &pl->ax[a], pl->tune.radix_mode);
+    pl->part_cap = partials_capacity(pl);
     const size_t cs = 2 * pl->esize;  // complex element
     LaunchShape& sh = pl->sh;
-    {
-        // lines per block of the FFT passes: powers of two, shared memory = twiddles + 2 tiles
-        auto lines_for = [&](int n) {
-            long long L = ((long long)(kSmemBudget / cs) - n) / (2LL * n) - 1;
-            return pow2_floor(L, 16);
-        };
-        sh.pairs_per_block = lines_for(n3);
-        sh.smem_z = ((size_t)n3 + 2 * (size_t)n3 * (sh.pairs_per_block + 1)) * cs;
-        sh.lpb_y = lines_for(n2);
-        sh.lpb_x = lines_for(n1);
-        sh.smem_y = ((size_t)n2 + 2 * (size_t)n2 * (sh.lpb_y + 1)) * cs;
-        sh.smem_x = ((size_t)n1 + 2 * (size_t)n1 * (sh.lpb_x + 1)) * cs;
-        long long gu = (g.N + kThreads - 1) / kThreads;
-        if (gu > 608) gu = 608;
-        sh.grid_update = (int)gu;
-        // TMA-staged update: tiles of J z rows with J * N3 <= 512 (FP32) / 256 (FP64) voxels,
-        // J a power of two dividing N2; two stages must fit the shared memory of a block
-        int sms = 0, dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
-            sms = 152;
-        const int tv_max = precision == CCMF_FP64 ? 256 : 512;
-        const int W = precision == CCMF_FP64 ? 2 : 4;
-        int J = 1;
-        while (2 * J * n3 <= tv_max && n2 % (2 * J) == 0) J *= 2;
-        const size_t smem_tma = 2 * (size_t)tma_stage_elems(J * n3, n3) * pl->esize + 16;
-        sh.tma_rows = (n3 % W == 0 && smem_tma <= 200 * 1024) ? J : 0;
-        sh.smem_tma = smem_tma;
-        long long ntiles = (long long)n1 * (n2 / J);
-        long long gt = (2LL * sms + batch - 1) / batch;
-        if (gt > ntiles) gt = ntiles;
-        if (gt < 1) gt = 1;
-        sh.grid_tma = (int)gt;
-        // pipelined update: a tile is one W-group per thread, TV = threads * W voxels = whole z rows
-        const char* env = getenv("CCMF_UPDATE_VARIANT");
-        const int vdef = precision == CCMF_FP64 ? kDefaultUpdateVariantF64 : kDefaultUpdateVariantF32;
-        int variant = env ? atoi(env) : vdef;
-        if (variant < 0 || variant > 7) variant = vdef;
-        sh.upd_variant = 0;
-        if (variant >= 2) {
-            const int vw = precision == CCMF_FP64 ? 1 : 2;
-            const int tv = kUpdatePipe[variant][0] * vw;
-            const int stages = kUpdatePipe[variant][1];
-            const bool rows_ok = n3 <= tv && tv % n3 == 0 && n2 % (tv / n3) == 0;
-            const bool seg_ok = n3 > tv && n3 % tv == 0;
-            if (n3 % W == 0 && (rows_ok || seg_ok)) {
-                const int kt = seg_ok ? tv : n3;
-                const size_t smem = (size_t)stages * (size_t)pipe_stage_elems(tv, kt, seg_ok, 16 / (int)pl->esize) *
-                                        pl->esize + 8 * stages;
-                const int nb = precision == CCMF_FP64 ? pipe_blocks_per_sm<double>(variant, smem)
-                                                      : pipe_blocks_per_sm<float>(variant, smem);
-                if (nb > 0) {
-                    sh.upd_variant = variant;
-                    sh.smem_pipe = smem;
-                    long long nt = (long long)n1 * (n2 / (tv / kt)) * (n3 / kt);
-                    long long gp = ((long long)nb * sms + batch - 1) / batch;
-                    if (gp > nt) gp = nt;
-                    sh.grid_pipe = (int)(gp < 1 ? 1 : gp);
-                }
-            }
-        }
-        if (sh.upd_variant == 0 && variant >= 1 && sh.tma_rows > 0) sh.upd_variant = 1;
-        sh.grid_partials = sh.grid_update > sh.grid_tma ? sh.grid_update : sh.grid_tma;
-        if (sh.grid_pipe > sh.grid_partials) sh.grid_partials = sh.grid_pipe;
-        // fused plane FFT pass when the (x, y) plane of one k_z fits one block's shared memory
-        const size_t smem_plane = ((size_t)n1 + n2 + (size_t)n1 * (n2 + 1)) * cs;
-        const char* envp = getenv("CCMF_PLANE_FUSED");
-        const bool allow_plane = !(envp && atoi(envp) == 0);
-        sh.plane_fused = (allow_plane && (long long)n1 * n2 <= kPlaneMax && smem_plane <= 200 * 1024) ? 1 : 0;
-        sh.smem_plane = smem_plane;
-    }
 
     // workspace layout
     size_t off = 0;
@@ -535,7 +767,7 @@ int ccmf_plan_create(int n1, int n2, int n3, int batch, int precision, ccmf_plan
     pl->off_sc = take(256 * (size_t)batch);
     pl->off_nact = take(256);
     pl->off_xi = take(3 * sizeof(double) * batch);
-    pl->off_part = take(sizeof(double) * kNSum * (size_t)sh.grid_partials * batch);
+    pl->off_part = take(sizeof(double) * kNSum * (size_t)pl->part_cap * batch);
     pl->off_hist = take(sizeof(double) * kHistFields * (size_t)kHistCap * batch);
     pl->off_e = take(pl->esize * 6 * N * batch * 2);
     pl->off_v = take(pl->esize * 6 * N * batch * 2);
@@ -559,7 +791,7 @@ int ccmf_plan_create(int n1, int n2, int n3, int batch, int precision, ccmf_plan
             const double sn = sin(kPi * (double)t / (double)n);
             sy[t] = 4.0 * sn * sn;
         }
-        for (int t = 0; t < n; ++t) rs[t] = sy[digit_reversed_frequency(ax[a], t)];
+        for (int t = 0; t < n; ++t) rs[t] = sy[digit_reversed_frequency(pl->ax[a], t)];
         if (precision == CCMF_FP64) {
             if (cudaMalloc(&pl->tw[a], tw.size() * 8) != cudaSuccess ||
                 cudaMemcpy(pl->tw[a], tw.data(), tw.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -590,15 +822,11 @@ int ccmf_plan_create(int n1, int n2, int n3, int batch, int precision, ccmf_plan
     if (rc == CCMF_OK && cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
         rc = CCMF_ERR_CUDA;
     {
-        const char* envb = getenv("CCMF_BRANCHES");
-        int nb = envb ? atoi(envb) : kMaxBranches;
-        if (nb < 1) nb = 1;
-        if (nb > kMaxBranches) nb = kMaxBranches;
-        if (nb > batch) nb = batch;
-        pl->branches = nb;
+        // streams for every branch count a tuning may choose
+        pl->branches = pl->tune.branches;
         if (rc == CCMF_OK && cudaEventCreateWithFlags(&pl->fork_event, cudaEventDisableTiming) != cudaSuccess)
             rc = CCMF_ERR_CUDA;
-        for (int b = 0; b < nb && rc == CCMF_OK; ++b) {
+        for (int b = 0; b < std::min(kMaxBranches, batch) && rc == CCMF_OK; ++b) {
             if (cudaStreamCreateWithFlags(&pl->branch_stream[b], cudaStreamNonBlocking) != cudaSuccess ||
                 cudaEventCreateWithFlags(&pl->join_event[b], cudaEventDisableTiming) != cudaSuccess)
                 rc = CCMF_ERR_CUDA;
@@ -765,6 +993,159 @@ int ccmf_history_export(const ccmf_plan* plan, const void* workspace, double* ou
         written = n > written ? n : written;
     }
     *count = written;
+    return CCMF_OK;
+}
+
+int ccmf_plan_get_tuning(const ccmf_plan* plan, ccmf_tuning* out) {
+    if (!plan || !out) return CCMF_ERR_INVALID_ARG;
+    *out = plan->tune;
+    return CCMF_OK;
+}
+
+int ccmf_plan_set_tuning(ccmf_plan* plan, const ccmf_tuning* tuning) {
+    if (!plan || !tuning) return CCMF_ERR_INVALID_ARG;
+    const ccmf_tuning keep = plan->tune;
+    const int rc = apply_tuning(plan, *tuning);
+    if (rc != CCMF_OK && apply_tuning(plan, keep) != CCMF_OK) return CCMF_ERR_CUDA;
+    return rc;
+}
+
+int ccmf_plan_autotune(ccmf_plan* plan, const void* gamma, long long gamma_stride, const double* xi_bar,
+                       void* workspace, size_t workspace_bytes, int iters, ccmf_tuning* best, double* best_ms,
+                       void* stream) {
+    if (!plan || !gamma || !xi_bar || gamma_stride < 0 || iters < 1 || iters > 1000) return CCMF_ERR_INVALID_ARG;
+    if (!workspace || workspace_bytes < plan->total) return CCMF_ERR_WORKSPACE;
+    if (cudaSetDevice(plan->device) != cudaSuccess) return CCMF_ERR_CUDA;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    ccmf_params prm;
+    ccmf_params_default(&prm);
+    prm.fixed_iters = iters;
+    prm.check_every = iters;
+    prm.resume = 1;
+    prm.history_len = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return CCMF_ERR_CUDA;
+    }
+    // one untimed run (it also captures the graph of this tuning), then one timed run
+    auto measure = [&](double* ms) {
+        int rc = ccmf_solve(plan, gamma, gamma_stride, xi_bar, &prm, workspace, workspace_bytes, nullptr, nullptr,
+                            nullptr, stream);
+        if (rc != CCMF_OK) return rc;
+        if (cudaEventRecord(e0, st) != cudaSuccess) return CCMF_ERR_CUDA;
+        rc = ccmf_solve(plan, gamma, gamma_stride, xi_bar, &prm, workspace, workspace_bytes, nullptr, nullptr,
+                        nullptr, stream);
+        if (rc != CCMF_OK) return rc;
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return CCMF_ERR_CUDA;
+        float f = 0.f;
+        if (cudaEventElapsedTime(&f, e0, e1) != cudaSuccess) return CCMF_ERR_CUDA;
+        *ms = (double)f / iters;
+        return CCMF_OK;
+    };
+    ccmf_tuning cur = plan->tune;
+    double cur_ms = 0.0;
+    int rc = measure(&cur_ms);
+    // coordinate descent over the knobs; a candidate must win by 1 % to be kept
+    struct Knob {
+        int ccmf_tuning::*field;
+        std::vector<int> values;
+    };
+    std::vector<int> brs;
+    for (int b = 1; b <= std::min(kMaxBranches, plan->batch); ++b) brs.push_back(b);
+    const Knob knobs[] = {
+        {&ccmf_tuning::update_variant, {0, 1, 2, 3, 4, 5, 6, 7}},
+        {&ccmf_tuning::plane_blocks, {0, 1, 2, 4, 8, 16}},
+        {&ccmf_tuning::z_pairs_per_block, {1, 2, 4, 8, 16}},
+        {&ccmf_tuning::y_lines_per_block, {1, 2, 4, 8, 16}},
+        {&ccmf_tuning::x_lines_per_block, {1, 2, 4, 8, 16}},
+        {&ccmf_tuning::branches, brs},
+        {&ccmf_tuning::radix_mode, {0, 1, 2}},
+    };
+    for (const Knob& k : knobs) {
+        if (rc != CCMF_OK) break;
+        const bool strided_only = k.field == &ccmf_tuning::y_lines_per_block || k.field == &ccmf_tuning::x_lines_per_block;
+        if (strided_only && cur.plane_blocks != 0) continue;
+        for (int v : k.values) {
+            if (v == cur.*(k.field)) continue;
+            ccmf_tuning cand = cur;
+            cand.*(k.field) = v;
+            if (apply_tuning(plan, cand) != CCMF_OK) continue;
+            double ms = 0.0;
+            rc = measure(&ms);
+            if (rc != CCMF_OK) break;
+            if (ms < 0.99 * cur_ms) {
+                cur = plan->tune;
+                cur_ms = ms;
+            }
+        }
+        if (rc == CCMF_OK) rc = apply_tuning(plan, cur);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != CCMF_OK) return rc;
+    tuning_store(plan, plan->tune);
+    if (best) *best = plan->tune;
+    if (best_ms) *best_ms = cur_ms;
+    return CCMF_OK;
+}
+
+int ccmf_tuning_export(char* text, size_t capacity, size_t* length) {
+    if (!length || (capacity > 0 && !text)) return CCMF_ERR_INVALID_ARG;
+    std::string out;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        char line[256];
+        for (const auto& kv : g_tune_table) {
+            const TuneKey& k = kv.first;
+            const ccmf_tuning& t = kv.second;
+            snprintf(line, sizeof(line), "ccmf-tuning %d %d %d %d %d %d : %d %d %d %d %d %d %d\n", k.n1, k.n2, k.n3,
+                     k.batch, k.prec, k.sms, t.update_variant, t.plane_blocks, t.z_pairs_per_block,
+                     t.y_lines_per_block, t.x_lines_per_block, t.branches, t.radix_mode);
+            out += line;
+        }
+    }
+    *length = out.size();
+    if (capacity > 0) {
+        const size_t n = std::min(capacity - 1, out.size());
+        memcpy(text, out.data(), n);
+        text[n] = '\0';
+    }
+    return CCMF_OK;
+}
+
+int ccmf_tuning_import(const char* text) {
+    if (!text) return CCMF_ERR_INVALID_ARG;
+    const char* p = text;
+    std::vector<std::pair<TuneKey, ccmf_tuning>> rows;
+    while (*p) {
+        const char* eol = strchr(p, '\n');
+        const size_t len = eol ? (size_t)(eol - p) : strlen(p);
+        std::string line(p, len);
+        p += len + (eol ? 1 : 0);
+        if (line.empty()) continue;
+        TuneKey k;
+        ccmf_tuning t;
+        memset(&t, 0, sizeof(t));
+        if (sscanf(line.c_str(), "ccmf-tuning %d %d %d %d %d %d : %d %d %d %d %d %d %d", &k.n1, &k.n2, &k.n3, &k.batch,
+                   &k.prec, &k.sms, &t.update_variant, &t.plane_blocks, &t.z_pairs_per_block, &t.y_lines_per_block,
+                   &t.x_lines_per_block, &t.branches, &t.radix_mode) != 13)
+            return CCMF_ERR_INVALID_ARG;
+        rows.emplace_back(k, t);
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    for (const auto& r : rows) g_tune_table[r.first] = r.second;
+    return CCMF_OK;
+}
+
+int ccmf_plan_launch_info(const ccmf_plan* plan, int* out, int capacity, int* count) {
+    if (!plan || !count || (capacity > 0 && !out)) return CCMF_ERR_INVALID_ARG;
+    const LaunchShape& sh = plan->sh;
+    const int grid_upd = sh.upd_variant >= 2 ? sh.grid_pipe : sh.upd_variant == 1 ? sh.grid_tma : sh.grid_update;
+    const int v[8] = {sh.upd_variant, sh.plane_fused, sh.plane_fused ? sh.plane_cluster : 0, sh.pairs_per_block,
+                      sh.lpb_y, sh.lpb_x, grid_upd, plan->branches};
+    for (int i = 0; i < 8 && i < capacity; ++i) out[i] = v[i];
+    *count = 8;
     return CCMF_OK;
 }
 

@@ -23,6 +23,8 @@
 
 #include <math.h>
 
+#include <cooperative_groups.h>
+
 #include "ccmf_types.cuh"
 
 namespace ccmf {
@@ -34,6 +36,19 @@ template <> struct Real<float> {
 template <> struct Real<double> {
     __device__ __forceinline__ static double sqrt_(double x) { return sqrt(x); }
 };
+
+// Asynchronous global -> shared copy of one complex element (cp.async: the thread
+// issues all its copies before waiting, instead of one load latency per element).
+template <typename C>
+__device__ __forceinline__ void cp_async_cx(C* smem_dst, const C* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    if constexpr (sizeof(C) == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // gamma field of solve s: a per-solve pointer table when given, else base + s * stride.
 template <typename T>
@@ -415,7 +430,13 @@ __global__ void __launch_bounds__(kThreads) k_fft_strided(Geom g, Ptrs<T> p, Axi
             k2 = (int)(l - (long long)kz * g.n2);
             base = (long long)kz * plane + k2;
         }
-        for (int m = m0; m < n; m += mstep) A[m * stride + c] = valid ? spec[base + (long long)m * g.n2] : cmake<C>(T(0), T(0));
+        for (int m = m0; m < n; m += mstep) {
+            if (valid)
+                cp_async_cx(&A[m * stride + c], &spec[base + (long long)m * g.n2]);
+            else
+                A[m * stride + c] = cmake<C>(T(0), T(0));
+        }
+        cp_async_wait_all();
         __syncthreads();
         C* R = block_fft<C, LPB>(A, B, ap, twl);
         const T lam23 = valid ? sym2[k2] + sym3[kz] : T(0);
@@ -436,14 +457,21 @@ __global__ void __launch_bounds__(kThreads) k_fft_strided(Geom g, Ptrs<T> p, Axi
             const int c = (int)fdiv((unsigned)idx, g.div_n2);
             const int m = idx - c * n;
             const long long l = l0 + c;
-            C val = cmake<C>(T(0), T(0));
-            if (l < nlines) {
-                val = spec[l * n + m];
-                if (MODE == 2) val = cconj(val);
-            }
-            A[m * stride + c] = val;
+            if (l < nlines)
+                cp_async_cx(&A[m * stride + c], &spec[l * n + m]);
+            else
+                A[m * stride + c] = cmake<C>(T(0), T(0));
         }
+        cp_async_wait_all();
         __syncthreads();
+        if (MODE == 2) {   // the inverse runs as conj(FFT(conj(.)))
+            for (int idx = threadIdx.x; idx < cnt; idx += kThreads) {
+                const int c = (int)fdiv((unsigned)idx, g.div_n2);
+                const int m = idx - c * n;
+                A[m * stride + c] = cconj(A[m * stride + c]);
+            }
+            __syncthreads();
+        }
         C* R = block_fft<C, LPB>(A, B, ap, twl);
         for (int idx = threadIdx.x; idx < cnt; idx += kThreads) {
             const int c = (int)fdiv((unsigned)idx, g.div_n2);
@@ -493,8 +521,9 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) k_fft_plane(Geom g, Ptrs<T> 
     const int cnt = n1 * n2;
     for (int idx = threadIdx.x; idx < cnt; idx += kPlaneThreads) {
         const int i = (int)fdiv((unsigned)idx, g.div_n2);
-        tile[i * P2 + (idx - i * n2)] = spec[idx];
+        cp_async_cx(&tile[i * P2 + (idx - i * n2)], &spec[idx]);
     }
+    cp_async_wait_all();
     __syncthreads();
     const FastDiv dn1 = g.div_n1, dn2 = g.div_n2;
     inplace_fft<C, true, kPlaneThreads>(tile, ax2, n1, 1, P2, dn1, ty);    // y: n1 rows
@@ -518,6 +547,124 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) k_fft_plane(Geom g, Ptrs<T> 
 }
 
 // ---------------------------------------------------------------------------
+// Cluster plane pass (planes too large for one block): a thread-block cluster of
+// C blocks transforms one (x, y) plane of one k_z. Block r first holds rows
+// [r R1, (r + 1) R1) (R1 = n1 / C) as Y[rr][j] (row stride n2 + 1) and runs the
+// forward y transforms (DIF, in place). The blocks then exchange sub-blocks
+// through distributed shared memory so that block r holds columns
+// [r R2, (r + 1) R2) (R2 = n2 / C) as X[cc][i] (line stride n1 + 1): each thread
+// reads its elements from the owning blocks into registers, the cluster
+// synchronises, and each block writes its new layout over its own buffer. The
+// x transforms, the Poisson symbol (digit-reversed tables on both axes) and the
+// inverse x transforms run on X; the inverse exchange returns the rows, the
+// inverse y transforms run on Y and the rows are stored. Reads from another
+// block always walk consecutive addresses of that block's buffer.
+// ---------------------------------------------------------------------------
+template <typename T> struct PlaneRegs;
+template <> struct PlaneRegs<float> { static constexpr int M = 32; };    // elements per thread in an exchange
+template <> struct PlaneRegs<double> { static constexpr int M = 16; };
+constexpr int kPlaneClusterThreads = 512;
+
+template <typename T, int CL>
+__global__ void __launch_bounds__(kPlaneClusterThreads, 1)
+    k_fft_plane_cluster(Geom g, Ptrs<T> p, AxisPlan ax1, AxisPlan ax2, const cx<T>* __restrict__ tw1,
+                        const cx<T>* __restrict__ tw2, const T* __restrict__ rsym1, const T* __restrict__ rsym2,
+                        const T* __restrict__ sym3, T inv_n, FastDiv dr1, FastDiv dr2) {
+    using C = cx<T>;
+    namespace cg = cooperative_groups;
+    constexpr int NT = kPlaneClusterThreads;
+    constexpr int M = PlaneRegs<T>::M;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int s = blockIdx.y + p.s0;
+    // uniform over the cluster (same solve): either every block returns here or none does
+    if (!p.run_all && !p.sc[s].active) return;
+    const int r = (int)cluster.block_rank();
+    const int kz = blockIdx.x / CL;
+    const int n1 = g.n1, n2 = g.n2;
+    const int R1 = (int)dr1.d, R2 = (int)dr2.d;
+    const int P2 = n2 + 1, Q = n1 + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tx = reinterpret_cast<C*>(smem_raw);
+    C* ty = tx + n1;
+    C* buf = ty + n2;
+    for (int t = threadIdx.x; t < n1; t += NT) tx[t] = tw1[t];
+    for (int t = threadIdx.x; t < n2; t += NT) ty[t] = tw2[t];
+    C* spec = p.spec + (size_t)s * g.Nh + (long long)kz * n1 * n2 + (long long)r * R1 * n2;
+    const int E = R1 * n2;   // elements per block (= n1 * R2)
+    for (int idx = threadIdx.x; idx < E; idx += NT) {
+        const int rr = (int)fdiv((unsigned)idx, g.div_n2);
+        cp_async_cx(&buf[rr * P2 + (idx - rr * n2)], &spec[idx]);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    inplace_fft<C, true, NT>(buf, ax2, R1, 1, P2, dr1, ty);   // y, rows of this block
+    cluster.sync();
+    C v[M];
+    // rows -> columns: element (i, cc) of column block r sits in block q = i / R1, row i - q R1
+#pragma unroll
+    for (int u = 0; u < M; ++u) {
+        const int e = threadIdx.x + u * NT;
+        if (e < E) {
+            const int i = (int)fdiv((unsigned)e, dr2);
+            const int cc = e - i * R2;
+            const int q = (int)fdiv((unsigned)i, dr1);
+            const C* src = cluster.map_shared_rank(buf, q);
+            v[u] = src[(i - q * R1) * P2 + r * R2 + cc];
+        }
+    }
+    cluster.sync();
+#pragma unroll
+    for (int u = 0; u < M; ++u) {
+        const int e = threadIdx.x + u * NT;
+        if (e < E) {
+            const int i = (int)fdiv((unsigned)e, dr2);
+            buf[(e - i * R2) * Q + i] = v[u];
+        }
+    }
+    __syncthreads();
+    inplace_fft<C, true, NT>(buf, ax1, R2, 1, Q, dr2, tx);    // x, columns of this block
+    const T l3 = sym3[kz];
+    for (int e = threadIdx.x; e < E; e += NT) {
+        const int cc = (int)fdiv((unsigned)e, g.div_n1);
+        const int i = e - cc * n1;
+        const T lam = rsym1[i] + rsym2[r * R2 + cc] + l3;
+        const T gk = (lam > T(0)) ? -inv_n / lam : T(0);
+        const C z = buf[cc * Q + i];
+        buf[cc * Q + i] = cmake<C>(z.x * gk, -z.y * gk);   // conj: the inverse runs as conj(DIT(conj))
+    }
+    __syncthreads();
+    inplace_fft<C, false, NT>(buf, ax1, R2, 1, Q, dr2, tx);
+    cluster.sync();
+    // columns -> rows: element (rr, j) of row block r sits in block q = j / R2, line j - q R2, slot r R1 + rr
+#pragma unroll
+    for (int u = 0; u < M; ++u) {
+        const int e = threadIdx.x + u * NT;
+        if (e < E) {
+            const int j = (int)fdiv((unsigned)e, dr1);
+            const int rr = e - j * R1;
+            const int q = (int)fdiv((unsigned)j, dr2);
+            const C* src = cluster.map_shared_rank(buf, q);
+            v[u] = src[(j - q * R2) * Q + r * R1 + rr];
+        }
+    }
+    cluster.sync();
+#pragma unroll
+    for (int u = 0; u < M; ++u) {
+        const int e = threadIdx.x + u * NT;
+        if (e < E) {
+            const int j = (int)fdiv((unsigned)e, dr1);
+            buf[(e - j * R1) * P2 + j] = v[u];
+        }
+    }
+    __syncthreads();
+    inplace_fft<C, false, NT>(buf, ax2, R1, 1, P2, dr1, ty);
+    for (int idx = threadIdx.x; idx < E; idx += NT) {
+        const int rr = (int)fdiv((unsigned)idx, g.div_n2);
+        spec[idx] = cconj(buf[rr * P2 + (idx - rr * n2)]);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Pass 5: complex-to-real inverse FFT along z, two real lines per transform.
 // ---------------------------------------------------------------------------
 template <typename T, int P>
@@ -536,13 +683,35 @@ __global__ void __launch_bounds__(kThreads) k_irfft_z(Geom g, Ptrs<T> p, AxisPla
     const long long l0 = (long long)blockIdx.x * 2 * P;
     const C* spec = p.spec + (size_t)s * g.Nh;
     const int cnt = P * g.n3h;
+    // stage the raw slab spec[kz][l0 .. l0 + 2P) in the second buffer with asynchronous
+    // copies when it fits there (2P <= n3), then build the packed lines from shared memory
+    const bool staged = 2 * P <= g.n3;
+    if (staged) {
+        for (int idx = threadIdx.x; idx < 2 * cnt; idx += kThreads) {
+            const int kz = idx / (2 * P);
+            const int t = idx - kz * 2 * P;
+            const long long l = l0 + t;
+            if (l < L)
+                cp_async_cx(&B[idx], spec + (long long)kz * L + l);
+            else
+                B[idx] = cmake<C>(T(0), T(0));
+        }
+        cp_async_wait_all();
+        __syncthreads();
+    }
     for (int idx = threadIdx.x; idx < cnt; idx += kThreads) {
         const int kz = idx / P;
         const int c = idx - kz * P;
         const long long la = l0 + 2 * c, lb = la + 1;
         const C* src = spec + (long long)kz * L + la;
-        const C a = (la < L) ? src[0] : cmake<C>(T(0), T(0));
-        const C b = (lb < L) ? src[1] : cmake<C>(T(0), T(0));
+        C a, b;
+        if (staged) {
+            a = B[kz * 2 * P + 2 * c];
+            b = B[kz * 2 * P + 2 * c + 1];
+        } else {
+            a = (la < L) ? src[0] : cmake<C>(T(0), T(0));
+            b = (lb < L) ? src[1] : cmake<C>(T(0), T(0));
+        }
         if (kz == 0 || 2 * kz == g.n3) {
             // Z = Re(a) + i Re(b); store conj(Z)
             A[kz * stride + c] = cmake<C>(a.x, -b.x);

@@ -97,6 +97,75 @@ int pipe_blocks_per_sm(int variant, size_t smem) {
     return err == cudaSuccess ? nb : 0;
 }
 
+// Cluster plane pass: launch with a cluster of CL blocks per plane (CL = 2, 4, 8, 16).
+template <typename T, int CL>
+cudaError_t launch_plane_cluster_t(const Geom& g, const Ptrs<T>& p, const Ctx<T>& c, T inv_n, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(g.n3h * CL), (unsigned)g.batch);
+    cfg.blockDim = dim3(kPlaneClusterThreads);
+    cfg.dynamicSmemBytes = c.sh.smem_plane;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_fft_plane_cluster<T, CL>, g, p, c.ax[0], c.ax[1], c.tw[0], c.tw[1],
+                              c.rsym[0], c.rsym[1], c.sym[2], inv_n, c.sh.div_r1, c.sh.div_r2);
+}
+
+template <typename T>
+cudaError_t launch_plane_cluster(const Geom& g, const Ptrs<T>& p, const Ctx<T>& c, T inv_n, cudaStream_t st) {
+    switch (c.sh.plane_cluster) {
+        case 2: return launch_plane_cluster_t<T, 2>(g, p, c, inv_n, st);
+        case 4: return launch_plane_cluster_t<T, 4>(g, p, c, inv_n, st);
+        case 8: return launch_plane_cluster_t<T, 8>(g, p, c, inv_n, st);
+        default: return launch_plane_cluster_t<T, 16>(g, p, c, inv_n, st);
+    }
+}
+
+// Sets the launch attributes of the cluster plane pass and returns how many of its
+// clusters can be resident at once (0: this cluster size cannot be launched).
+template <typename T, int CL>
+int plane_cluster_capacity_t(size_t smem) {
+    const void* f = (const void*)k_fft_plane_cluster<T, CL>;
+    if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        (CL > 8 && cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CL * 16);
+    cfg.blockDim = dim3(kPlaneClusterThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, f, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+template <typename T>
+int plane_cluster_capacity(int cl, size_t smem) {
+    switch (cl) {
+        case 2: return plane_cluster_capacity_t<T, 2>(smem);
+        case 4: return plane_cluster_capacity_t<T, 4>(smem);
+        case 8: return plane_cluster_capacity_t<T, 8>(smem);
+        case 16: return plane_cluster_capacity_t<T, 16>(smem);
+        default: return 0;
+    }
+}
+
 template <typename T>
 cudaError_t configure_kernels(const LaunchShape& sh) {
     cudaError_t err = cudaSuccess;
@@ -114,7 +183,10 @@ cudaError_t configure_kernels(const LaunchShape& sh) {
         set((const void*)k_fft_strided<T, 2, LN>, sh.smem_y);
     });
     CCMF_DISPATCH_LINES(sh.lpb_x, { set((const void*)k_fft_strided<T, 1, LN>, sh.smem_x); });
-    if (sh.plane_fused) set((const void*)k_fft_plane<T>, sh.smem_plane);
+    if (sh.plane_fused && sh.plane_cluster <= 1) set((const void*)k_fft_plane<T>, sh.smem_plane);
+    if (sh.plane_fused && sh.plane_cluster > 1 && err == cudaSuccess &&
+        plane_cluster_capacity<T>(sh.plane_cluster, sh.smem_plane) < 1)
+        err = cudaErrorInvalidConfiguration;
     if (sh.tma_rows > 0) {
         set((const void*)k_update_tma<T, 0>, sh.smem_tma);
         set((const void*)k_update_tma<T, 1>, sh.smem_tma);
@@ -157,7 +229,10 @@ void launch_passes(const Ctx<T>& c, const Ptrs<T>& p, cudaStream_t st, F&& betwe
             k_div_rfft_z<T, LN, false><<<gz, kThreads, sh.smem_z, st>>>(g, p, c.ax[2], c.tw[2]);
     });
     between(kKDivRfftZ);
-    if (sh.plane_fused) {
+    if (sh.plane_fused && sh.plane_cluster > 1) {
+        launch_plane_cluster<T>(g, p, c, inv_n, st);
+        between(kKFftPlane);
+    } else if (sh.plane_fused) {
         k_fft_plane<T><<<dim3((unsigned)g.n3h, (unsigned)g.batch), kPlaneThreads, sh.smem_plane, st>>>(
             g, p, c.ax[0], c.ax[1], c.tw[0], c.tw[1], c.rsym[0], c.rsym[1], c.sym[2], inv_n);
         between(kKFftPlane);

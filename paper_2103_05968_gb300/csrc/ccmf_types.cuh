@@ -91,8 +91,10 @@ struct LaunchShape {
                               // 2..7 pipelined TMA (see kUpdatePipe)
     int grid_pipe;            // blocks per solve of the pipelined update
     size_t smem_pipe;         // its dynamic shared memory
-    int plane_fused;          // 1: y / x / solve / x / y in one k_fft_plane launch per iteration
-    size_t smem_plane;        // its dynamic shared memory
+    int plane_fused;          // 1: y / x / solve / x / y in one plane launch per iteration
+    size_t smem_plane;        // its dynamic shared memory (per block)
+    int plane_cluster;        // blocks sharing one plane: 1 = k_fft_plane, 2..16 = k_fft_plane_cluster
+    FastDiv div_r1, div_r2;   // rows (n1 / C) and columns (n2 / C) of one cluster block
 };
 
 // Pipelined update variants: {threads per block, stages}.

@@ -1,0 +1,93 @@
+"""The tuning knobs and the autotuner (ccmf_plan_set_tuning / ccmf_plan_autotune).
+
+Every knob changes only how the Eq. 30 step is launched (update-pass variant,
+plane pass on one block, a cluster or strided passes, lines per block, graph
+branches, radix schedule), so FP64 results under any tuning must match the
+oracle at equal iteration counts with the parity bars of the other tests."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from oracle import ccmf_oracle as O  # noqa: E402
+from paper_2103_05968_gb300 import ccmf  # noqa: E402
+from paper_2103_05968_gb300 import microstructure as M  # noqa: E402
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+TUNINGS = [
+    dict(update_variant=0, plane_blocks=0, y_lines_per_block=2, x_lines_per_block=16),
+    dict(update_variant=1, plane_blocks=1, z_pairs_per_block=1, radix_mode=1),
+    dict(update_variant=3, plane_blocks=2, z_pairs_per_block=4, radix_mode=2, branches=1),
+    dict(update_variant=7, plane_blocks=4, branches=3, radix_mode=1),
+    dict(update_variant=5, plane_blocks=0, y_lines_per_block=16, x_lines_per_block=1, radix_mode=2, branches=2),
+]
+
+
+@pytest.mark.parametrize("knobs", TUNINGS, ids=[f"t{i}" for i in range(len(TUNINGS))])
+def test_fp64_parity_under_tuning(knobs):
+    gamma = M.boolean_spheres((40, 24, 32), 3.0, 0.2, 0.3, 1.0, seed=17)[0]
+    normals = [[1, 0, 0], [0.36, 0.48, 0.8], [0, 0, 1]]
+    plan = ccmf.Plan(gamma.shape, batch=3, precision=ccmf.CCMF_FP64, device=DEV)
+    plan.set_tuning(**knobs)
+    t = plan.tuning()
+    for k, v in knobs.items():
+        assert t[k] == v
+    assert min(t.values()) >= 0
+    res, flow, cut = plan.solve(torch.from_numpy(gamma).to(DEV), normals, ccmf.Params(fixed_iters=25),
+                                want_flow=True, want_cut=True)
+    e, v, rho, _ = plan.state()
+    for s, n in enumerate(normals):
+        ref = O.solve(gamma, n, O.Params(fixed_iters=25), record_history=False)
+        assert abs(res[s]["gamma_eff"] - ref.gamma_eff) <= 1e-10 * ref.gamma_eff
+        np.testing.assert_allclose(e[s].cpu().numpy(), ref.e, rtol=0, atol=1e-9)
+        np.testing.assert_allclose(v[s].cpu().numpy(), ref.v, rtol=0, atol=1e-9)
+        np.testing.assert_allclose(cut[s].cpu().numpy(), ref.cut, rtol=0, atol=1e-9)
+    plan.close()
+
+
+def test_infeasible_tuning_is_rejected_and_kept():
+    plan = ccmf.Plan((40, 24, 12), batch=1, precision=ccmf.CCMF_FP32_MIXED, device=DEV)
+    before = plan.tuning()
+    for bad in (dict(plane_blocks=16), dict(plane_blocks=3), dict(z_pairs_per_block=3), dict(update_variant=9),
+                dict(branches=5), dict(radix_mode=7)):
+        with pytest.raises(ccmf.CCMFError) as err:
+            plan.set_tuning(**bad)
+        assert err.value.code == ccmf.CCMF_ERR_UNSUPPORTED_SIZE
+        assert plan.tuning() == before
+    plan.close()
+
+
+def test_autotune_keeps_the_fastest_and_records_it():
+    gamma = M.boolean_spheres((64, 64, 64), 4.0, 0.2, 0.3, 1.0, seed=23)[0].astype(np.float32)
+    normals = [[1, 0, 0], [0, 1, 0], [0, 0, 1]]
+    g = torch.from_numpy(gamma).to(DEV)
+    plan = ccmf.Plan(gamma.shape, batch=3, precision=ccmf.CCMF_FP32_MIXED, device=DEV)
+    plan.solve(g, normals, ccmf.Params(fixed_iters=5))
+    best, ms = plan.autotune(g, normals, iters=5)
+    assert ms > 0 and best == plan.tuning()
+    # the tuning table now holds this key: a new plan of the same key starts from it
+    again = ccmf.Plan(gamma.shape, batch=3, precision=ccmf.CCMF_FP32_MIXED, device=DEV)
+    assert again.tuning() == best
+    code, text = ccmf.ccmf_tuning_export()
+    assert code == ccmf.CCMF_OK
+    line = [x for x in text.splitlines() if x.startswith("ccmf-tuning 64 64 64 3 1 ")]
+    assert len(line) == 1
+    # the tuned plan still solves: state after 5 + autotuning updates stays feasible and finite
+    res, _, _ = again.solve(g, normals, ccmf.Params(fixed_iters=20))
+    for r in res:
+        assert r["status"] == 0 and np.isfinite(r["gamma_eff"])
+    plan.close()
+    again.close()

@@ -196,13 +196,13 @@ typedef struct {
     int update_variant;     /* update pass: 0 register vectors, 1 TMA rows, 2..7 pipelined TMA */
     int plane_blocks;       /* y / x passes: 0 three strided passes, 1 one block per (x, y) plane,
                                2, 4, 8, 16 a thread-block cluster per plane */
-    int z_pairs_per_block;  /* z passes: line pairs per block, power of two 1..16 */
+    int z_pairs_per_block;  /* divergence + forward z pass: line pairs per block, power of two 1..16 */
     int y_lines_per_block;  /* strided y passes: lines per block, power of two 1..16 */
     int x_lines_per_block;  /* strided x pass: lines per block, power of two 1..16 */
     int branches;           /* independent graph branches of a batch, 1..4 */
     int radix_mode;         /* radix schedule of every axis: 0 radix 8 first, then 4, 2, 3, 5;
                                1 as 0 but radix 4s in place of a radix 8 + 2 tail; 2 radix 4 at most */
-    int reserved;
+    int zinv_pairs_per_block; /* inverse z pass: line pairs per block, power of two 1..16 */
 } ccmf_tuning;
 
 /* The plan's current knob values (every entry resolved, none negative). */
@@ -233,7 +233,7 @@ int ccmf_plan_autotune(ccmf_plan* plan, const void* gamma, long long gamma_strid
 
 /*
  * The tuning table as text, one line per key
- * ("ccmf-tuning N1 N2 N3 batch precision sms : 7 knob values"). Writes at most
+ * ("ccmf-tuning N1 N2 N3 batch precision sms : 8 knob values"). Writes at most
  * capacity bytes (NUL-terminated) and the full length in *length.
  */
 int ccmf_tuning_export(char* text, size_t capacity, size_t* length);

@@ -77,11 +77,11 @@ class ccmf_tuning(ctypes.Structure):
         ("x_lines_per_block", ctypes.c_int),
         ("branches", ctypes.c_int),
         ("radix_mode", ctypes.c_int),
-        ("reserved", ctypes.c_int),
+        ("zinv_pairs_per_block", ctypes.c_int),
     ]
 
 
-TUNING_KEYS = tuple(f[0] for f in ccmf_tuning._fields_ if f[0] != "reserved")
+TUNING_KEYS = tuple(f[0] for f in ccmf_tuning._fields_)
 
 _lib = None
 

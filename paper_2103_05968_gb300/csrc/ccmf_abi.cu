@@ -22,6 +22,7 @@ namespace ccmf {
 template <typename T> cudaError_t configure_kernels(const LaunchShape&);
 template <typename T> int pipe_blocks_per_sm(int, size_t);
 template <typename T> int plane_cluster_capacity(int, size_t);
+template <typename T> int lines_blocks_per_sm(int, int, size_t);
 template <typename T> void launch_init(const Ctx<T>&, cudaStream_t);
 template <typename T> void launch_iteration(const Ctx<T>&, cudaStream_t);
 template <typename T> void launch_iteration_range(const Ctx<T>&, int, int, cudaStream_t);
@@ -183,7 +184,7 @@ void tuning_auto(ccmf_tuning* t) {
     t->x_lines_per_block = -1;
     t->branches = -1;
     t->radix_mode = 0;
-    t->reserved = 0;
+    t->zinv_pairs_per_block = -1;
 }
 
 bool pow2_in(int x, int lo, int hi) { return x >= lo && x <= hi && (x & (x - 1)) == 0; }
@@ -219,9 +220,11 @@ int shape_for(const ccmf_plan* pl, const ccmf_tuning& t, LaunchShape* out, ccmf_
         return true;
     };
     if (!pick(r.z_pairs_per_block, n3, &sh.pairs_per_block) || !pick(r.y_lines_per_block, n2, &sh.lpb_y) ||
-        !pick(r.x_lines_per_block, n1, &sh.lpb_x))
+        !pick(r.x_lines_per_block, n1, &sh.lpb_x) || !pick(r.zinv_pairs_per_block, n3, &sh.pairs_inv))
         return CCMF_ERR_UNSUPPORTED_SIZE;
     sh.smem_z = smem_lines(n3, sh.pairs_per_block);
+    sh.smem_zi = smem_lines(n3, sh.pairs_inv);
+    r.zinv_pairs_per_block = sh.pairs_inv;
     sh.smem_y = smem_lines(n2, sh.lpb_y);
     sh.smem_x = smem_lines(n1, sh.lpb_x);
     r.z_pairs_per_block = sh.pairs_per_block;
@@ -325,6 +328,16 @@ int shape_for(const ccmf_plan* pl, const ccmf_tuning& t, LaunchShape* out, ccmf_
         return CCMF_ERR_UNSUPPORTED_SIZE;
     }
     r.plane_blocks = sh.plane_fused ? sh.plane_cluster : 0;
+    if (!sh.plane_fused) {
+        // persistent line passes: resident blocks x SMs, shared by the solves of the batch
+        const int by = f64 ? lines_blocks_per_sm<double>(0, sh.lpb_y, sh.smem_y)
+                           : lines_blocks_per_sm<float>(0, sh.lpb_y, sh.smem_y);
+        const int bx = f64 ? lines_blocks_per_sm<double>(1, sh.lpb_x, sh.smem_x)
+                           : lines_blocks_per_sm<float>(1, sh.lpb_x, sh.smem_x);
+        if (by < 1 || bx < 1) return CCMF_ERR_UNSUPPORTED_SIZE;
+        sh.grid_y = (int)std::max(1LL, ((long long)by * sms + batch - 1) / batch);
+        sh.grid_x = (int)std::max(1LL, ((long long)bx * sms + batch - 1) / batch);
+    }
     // graph branches of a batch (never more than the solves)
     int nb = r.branches;
     if (nb < 0) {
@@ -335,7 +348,6 @@ int shape_for(const ccmf_plan* pl, const ccmf_tuning& t, LaunchShape* out, ccmf_
     }
     if (nb < 1 || nb > kMaxBranches) return CCMF_ERR_UNSUPPORTED_SIZE;
     r.branches = std::min(nb, batch);
-    r.reserved = 0;
     *out = sh;
     if (res) *res = r;
     return CCMF_OK;
@@ -1061,6 +1073,7 @@ int ccmf_plan_autotune(ccmf_plan* plan, const void* gamma, long long gamma_strid
         {&ccmf_tuning::x_lines_per_block, {1, 2, 4, 8, 16}},
         {&ccmf_tuning::branches, brs},
         {&ccmf_tuning::radix_mode, {0, 1, 2}},
+        {&ccmf_tuning::zinv_pairs_per_block, {1, 2, 4, 8, 16}},
     };
     for (const Knob& k : knobs) {
         if (rc != CCMF_OK) break;
@@ -1099,9 +1112,9 @@ int ccmf_tuning_export(char* text, size_t capacity, size_t* length) {
         for (const auto& kv : g_tune_table) {
             const TuneKey& k = kv.first;
             const ccmf_tuning& t = kv.second;
-            snprintf(line, sizeof(line), "ccmf-tuning %d %d %d %d %d %d : %d %d %d %d %d %d %d\n", k.n1, k.n2, k.n3,
-                     k.batch, k.prec, k.sms, t.update_variant, t.plane_blocks, t.z_pairs_per_block,
-                     t.y_lines_per_block, t.x_lines_per_block, t.branches, t.radix_mode);
+            snprintf(line, sizeof(line), "ccmf-tuning %d %d %d %d %d %d : %d %d %d %d %d %d %d %d\n", k.n1, k.n2,
+                     k.n3, k.batch, k.prec, k.sms, t.update_variant, t.plane_blocks, t.z_pairs_per_block,
+                     t.y_lines_per_block, t.x_lines_per_block, t.branches, t.radix_mode, t.zinv_pairs_per_block);
             out += line;
         }
     }
@@ -1127,9 +1140,10 @@ int ccmf_tuning_import(const char* text) {
         TuneKey k;
         ccmf_tuning t;
         memset(&t, 0, sizeof(t));
-        if (sscanf(line.c_str(), "ccmf-tuning %d %d %d %d %d %d : %d %d %d %d %d %d %d", &k.n1, &k.n2, &k.n3, &k.batch,
-                   &k.prec, &k.sms, &t.update_variant, &t.plane_blocks, &t.z_pairs_per_block, &t.y_lines_per_block,
-                   &t.x_lines_per_block, &t.branches, &t.radix_mode) != 13)
+        if (sscanf(line.c_str(), "ccmf-tuning %d %d %d %d %d %d : %d %d %d %d %d %d %d %d", &k.n1, &k.n2, &k.n3,
+                   &k.batch, &k.prec, &k.sms, &t.update_variant, &t.plane_blocks, &t.z_pairs_per_block,
+                   &t.y_lines_per_block, &t.x_lines_per_block, &t.branches, &t.radix_mode,
+                   &t.zinv_pairs_per_block) != 14)
             return CCMF_ERR_INVALID_ARG;
         rows.emplace_back(k, t);
     }

@@ -5,11 +5,11 @@
 //   1. k_div_rfft_z     w = e - v/rho, d = div^- A* w (Sec. 2.2, Eq. 17) fused
 //                       with the real-to-complex FFT along z (two real lines per
 //                       complex transform);
-//   2. k_fft_strided<0> forward FFT along y;
-//   3. k_fft_strided<1> forward FFT along x, Poisson solve
+//   2. k_fft_lines<0>   forward FFT along y;
+//   3. k_fft_lines<1>   forward FFT along x, Poisson solve
 //                       phi^ = d^ / (-sum_a 4 sin^2(pi k_a / N_a)), phi^(0) = 0
 //                       (the (div^- grad^+)^+ of Eq. 28), inverse FFT along x;
-//   4. k_fft_strided<2> inverse FFT along y;
+//   4. k_fft_lines<2>   inverse FFT along y;
 //   5. k_irfft_z        complex-to-real inverse FFT along z -> phi;
 //   6. k_update<false>  xi^{k+1/2} = w - A(A* w - grad^+ phi - xi_bar) (= P_K(w),
 //                       Eq. 28), over-relaxation, z = v + rho xi, node-wise
@@ -386,103 +386,132 @@ __global__ void __launch_bounds__(kThreads) k_div_rfft_z(Geom g, Ptrs<T> p, Axis
 }
 
 // ---------------------------------------------------------------------------
-// Passes 2-4: FFTs along y and x of the half spectrum, stored k_z-major as
-// [n3h][n1][n2] (a (x, y) plane per k_z is contiguous).
-// MODE 0: forward along y.  MODE 2: inverse along y.  y-lines (kz, i) are
-// contiguous runs of n2 elements, so loads and stores walk along the line.
-// MODE 1: forward along x, multiply by 1 / (N lambda(k)) with
-//         lambda(k) = -sum_a 4 sin^2(pi k_a / N_a) and 0 at k = 0, inverse along x.
-//         x-lines (kz, j) have stride n2; consecutive lines are adjacent.
-// A block transforms LPB consecutive lines.
+// Passes 2-4 for planes too large for one block: FFTs along y and x of the half
+// spectrum, stored k_z-major as [n3h][n1][n2], run in place on tiles of L lines.
+// MODE 0: forward along y as decimation in frequency; the spectrum is left in
+//         digit-reversed y order.
+// MODE 1: forward along x (DIF), multiply by 1 / (N lambda(k)) with
+//         lambda(k) = -sum_a 4 sin^2(pi k_a / N_a) and 0 at k = 0, read from
+//         digit-reversed x and y tables, then the inverse along x as
+//         conj(DIT(conj(.))); the result is stored conjugated.
+// MODE 2: inverse along y: DIT of the conjugated data, conjugated on store,
+//         which returns natural order.
+// y-lines (kz, i) are contiguous runs of n2 elements; x-lines (kz, j) have
+// stride n2 and consecutive lines are adjacent. Blocks are persistent: each
+// loops over tiles and copies the next tile into its second buffer (cp.async
+// groups) while it transforms the current one.
 // ---------------------------------------------------------------------------
-template <typename T, int MODE, int LPB>
-__global__ void __launch_bounds__(kThreads) k_fft_strided(Geom g, Ptrs<T> p, AxisPlan ap,
-                                                          const cx<T>* __restrict__ tw,
-                                                          const T* __restrict__ sym1, const T* __restrict__ sym2,
-                                                          const T* __restrict__ sym3, T inv_n) {
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+template <typename T, int MODE, int L>
+__global__ void __launch_bounds__(kThreads) k_fft_lines(Geom g, Ptrs<T> p, AxisPlan ap, const cx<T>* __restrict__ tw,
+                                                        const T* __restrict__ rsym1, const T* __restrict__ rsym2,
+                                                        const T* __restrict__ sym3, T inv_n, FastDiv dl) {
     using C = cx<T>;
-    constexpr int stride = LPB + 1;
-    constexpr int lsh = (LPB >= 16) ? 4 : (LPB >= 8) ? 3 : (LPB >= 4) ? 2 : (LPB >= 2) ? 1 : 0;
+    constexpr int stride = L + 1;
+    constexpr int lsh = (L >= 16) ? 4 : (L >= 8) ? 3 : (L >= 4) ? 2 : (L >= 2) ? 1 : 0;
+    static_assert((1 << lsh) == L, "L must be a power of two <= 16");
     const int s = blockIdx.y + p.s0;
     if (!p.run_all && !p.sc[s].active) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = ap.n;
     C* twl = reinterpret_cast<C*>(smem_raw);
-    C* A = twl + n;
-    C* B = A + (size_t)n * stride;
+    C* buf[2];
+    buf[0] = twl + n;
+    buf[1] = buf[0] + (size_t)n * stride;
     for (int t = threadIdx.x; t < n; t += kThreads) twl[t] = tw[t];
     const long long plane = (long long)g.n1 * g.n2;
     const long long nlines = (MODE == 1) ? (long long)g.n3h * g.n2 : (long long)g.n3h * g.n1;
-    const long long l0 = (long long)blockIdx.x * LPB;
+    const long long ntiles = (nlines + L - 1) / L;
     C* spec = p.spec + (size_t)s * g.Nh;
-    const int cnt = LPB * n;
-    if (MODE == 1) {
-        // line l = kz * n2 + j: elements i at base + i * n2
-        const int c = threadIdx.x & (LPB - 1);
-        const int m0 = threadIdx.x >> lsh;
-        constexpr int mstep = kThreads / LPB;
-        const long long l = l0 + c;
-        const bool valid = l < nlines;
-        int kz = 0, k2 = 0;
-        long long base = 0;
-        if (valid) {
-            kz = (int)fdiv((unsigned)l, g.div_n2);
-            k2 = (int)(l - (long long)kz * g.n2);
-            base = (long long)kz * plane + k2;
-        }
-        for (int m = m0; m < n; m += mstep) {
-            if (valid)
-                cp_async_cx(&A[m * stride + c], &spec[base + (long long)m * g.n2]);
-            else
-                A[m * stride + c] = cmake<C>(T(0), T(0));
-        }
-        cp_async_wait_all();
-        __syncthreads();
-        C* R = block_fft<C, LPB>(A, B, ap, twl);
-        const T lam23 = valid ? sym2[k2] + sym3[kz] : T(0);
-        for (int m = m0; m < n; m += mstep) {
-            const T lam = sym1[m] + lam23;
-            const T gk = (valid && lam > T(0)) ? -inv_n / lam : T(0);
-            const C z = R[m * stride + c];
-            R[m * stride + c] = cmake<C>(z.x * gk, -z.y * gk);   // conj for the inverse transform
-        }
-        __syncthreads();
-        C* other = (R == A) ? B : A;
-        R = block_fft<C, LPB>(R, other, ap, twl);
-        if (valid)
-            for (int m = m0; m < n; m += mstep) spec[base + (long long)m * g.n2] = cconj(R[m * stride + c]);
-    } else {
-        // line l = kz * n1 + i: n2 contiguous elements at l * n2
-        for (int idx = threadIdx.x; idx < cnt; idx += kThreads) {
-            const int c = (int)fdiv((unsigned)idx, g.div_n2);
-            const int m = idx - c * n;
-            const long long l = l0 + c;
-            if (l < nlines)
-                cp_async_cx(&A[m * stride + c], &spec[l * n + m]);
-            else
-                A[m * stride + c] = cmake<C>(T(0), T(0));
-        }
-        cp_async_wait_all();
-        __syncthreads();
-        if (MODE == 2) {   // the inverse runs as conj(FFT(conj(.)))
+    const int cnt = L * n;
+    // MODE 1: each thread keeps one line c of every tile and walks its elements
+    const int cl = threadIdx.x & (L - 1);
+    const int m0 = threadIdx.x >> lsh;
+    constexpr int mstep = kThreads / L;
+    auto issue = [&](long long t, C* b) {
+        const long long l0 = t * L;
+        if (MODE == 1) {
+            const long long l = l0 + cl;
+            if (l < nlines) {
+                const int kz = (int)fdiv((unsigned)l, g.div_n2);
+                const int k2 = (int)(l - (long long)kz * g.n2);
+                const C* src = spec + (long long)kz * plane + k2;
+                for (int m = m0; m < n; m += mstep) cp_async_cx(&b[m * stride + cl], src + (long long)m * g.n2);
+            } else {
+                for (int m = m0; m < n; m += mstep) b[m * stride + cl] = cmake<C>(T(0), T(0));
+            }
+        } else {
             for (int idx = threadIdx.x; idx < cnt; idx += kThreads) {
                 const int c = (int)fdiv((unsigned)idx, g.div_n2);
                 const int m = idx - c * n;
-                A[m * stride + c] = cconj(A[m * stride + c]);
+                const long long l = l0 + c;
+                if (l < nlines)
+                    cp_async_cx(&b[m * stride + c], spec + l * n + m);
+                else
+                    b[m * stride + c] = cmake<C>(T(0), T(0));
+            }
+        }
+        cp_async_commit();
+    };
+    long long t = blockIdx.x;
+    int cur = 0;
+    if (t < ntiles) issue(t, buf[0]);
+    for (; t < ntiles; t += gridDim.x) {
+        const long long tn = t + gridDim.x;
+        if (tn < ntiles)
+            issue(tn, buf[cur ^ 1]);
+        else
+            cp_async_commit();   // an empty group keeps the count of pending groups at one
+        cp_async_wait_one();
+        __syncthreads();
+        C* b = buf[cur];
+        const long long l0 = t * L;
+        if (MODE == 0) {
+            inplace_fft<C, true, kThreads>(b, ap, L, stride, 1, dl, twl);
+        } else if (MODE == 2) {
+            inplace_fft<C, false, kThreads>(b, ap, L, stride, 1, dl, twl);
+        } else {
+            inplace_fft<C, true, kThreads>(b, ap, L, stride, 1, dl, twl);
+            const long long l = l0 + cl;
+            const bool valid = l < nlines;
+            int kz = 0, k2 = 0;
+            if (valid) {
+                kz = (int)fdiv((unsigned)l, g.div_n2);
+                k2 = (int)(l - (long long)kz * g.n2);
+            }
+            const T lam23 = valid ? rsym2[k2] + sym3[kz] : T(0);
+            for (int m = m0; m < n; m += mstep) {
+                const T lam = rsym1[m] + lam23;
+                const T gk = (valid && lam > T(0)) ? -inv_n / lam : T(0);
+                const C z = b[m * stride + cl];
+                b[m * stride + cl] = cmake<C>(z.x * gk, -z.y * gk);
             }
             __syncthreads();
+            inplace_fft<C, false, kThreads>(b, ap, L, stride, 1, dl, twl);
         }
-        C* R = block_fft<C, LPB>(A, B, ap, twl);
-        for (int idx = threadIdx.x; idx < cnt; idx += kThreads) {
-            const int c = (int)fdiv((unsigned)idx, g.div_n2);
-            const int m = idx - c * n;
-            const long long l = l0 + c;
+        if (MODE == 1) {
+            const long long l = l0 + cl;
             if (l < nlines) {
-                C val = R[m * stride + c];
-                if (MODE == 2) val = cconj(val);
-                spec[l * n + m] = val;
+                const int kz = (int)fdiv((unsigned)l, g.div_n2);
+                const int k2 = (int)(l - (long long)kz * g.n2);
+                C* dst = spec + (long long)kz * plane + k2;
+                for (int m = m0; m < n; m += mstep) dst[(long long)m * g.n2] = b[m * stride + cl];
+            }
+        } else {
+            for (int idx = threadIdx.x; idx < cnt; idx += kThreads) {
+                const int c = (int)fdiv((unsigned)idx, g.div_n2);
+                const int m = idx - c * n;
+                const long long l = l0 + c;
+                if (l < nlines) {
+                    const C v = b[m * stride + c];
+                    spec[l * n + m] = (MODE == 2) ? cconj(v) : v;
+                }
             }
         }
+        __syncthreads();   // the buffer is refilled two tiles later
+        cur ^= 1;
     }
 }
 

@@ -126,6 +126,24 @@ cudaError_t launch_plane_cluster(const Geom& g, const Ptrs<T>& p, const Ctx<T>& 
     }
 }
 
+// Blocks per SM of a y / x line pass with L lines per tile (occupancy API), 0 on error.
+template <typename T>
+int lines_blocks_per_sm(int mode, int lines, size_t smem) {
+    int nb = 0;
+    cudaError_t err = cudaSuccess;
+    CCMF_DISPATCH_LINES(lines, {
+        const void* f = mode == 0 ? (const void*)k_fft_lines<T, 0, LN>
+                                  : mode == 1 ? (const void*)k_fft_lines<T, 1, LN> : (const void*)k_fft_lines<T, 2, LN>;
+        err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kThreads, smem);
+    });
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
 // Sets the launch attributes of the cluster plane pass and returns how many of its
 // clusters can be resident at once (0: this cluster size cannot be launched).
 template <typename T, int CL>
@@ -176,13 +194,13 @@ cudaError_t configure_kernels(const LaunchShape& sh) {
     CCMF_DISPATCH_LINES(sh.pairs_per_block, {
         set((const void*)k_div_rfft_z<T, LN, true>, sh.smem_z);
         set((const void*)k_div_rfft_z<T, LN, false>, sh.smem_z);
-        set((const void*)k_irfft_z<T, LN>, sh.smem_z);
     });
+    CCMF_DISPATCH_LINES(sh.pairs_inv, { set((const void*)k_irfft_z<T, LN>, sh.smem_zi); });
     CCMF_DISPATCH_LINES(sh.lpb_y, {
-        set((const void*)k_fft_strided<T, 0, LN>, sh.smem_y);
-        set((const void*)k_fft_strided<T, 2, LN>, sh.smem_y);
+        set((const void*)k_fft_lines<T, 0, LN>, sh.smem_y);
+        set((const void*)k_fft_lines<T, 2, LN>, sh.smem_y);
     });
-    CCMF_DISPATCH_LINES(sh.lpb_x, { set((const void*)k_fft_strided<T, 1, LN>, sh.smem_x); });
+    CCMF_DISPATCH_LINES(sh.lpb_x, { set((const void*)k_fft_lines<T, 1, LN>, sh.smem_x); });
     if (sh.plane_fused && sh.plane_cluster <= 1) set((const void*)k_fft_plane<T>, sh.smem_plane);
     if (sh.plane_fused && sh.plane_cluster > 1 && err == cudaSuccess &&
         plane_cluster_capacity<T>(sh.plane_cluster, sh.smem_plane) < 1)
@@ -218,8 +236,11 @@ void launch_passes(const Ctx<T>& c, const Ptrs<T>& p, cudaStream_t st, F&& betwe
     const LaunchShape& sh = c.sh;
     const long long pairs = ceil_div((long long)g.n1 * g.n2, 2);
     dim3 gz((unsigned)ceil_div(pairs, sh.pairs_per_block), (unsigned)g.batch);
-    dim3 gy((unsigned)ceil_div((long long)g.n1 * g.n3h, sh.lpb_y), (unsigned)g.batch);
-    dim3 gx((unsigned)ceil_div((long long)g.n2 * g.n3h, sh.lpb_x), (unsigned)g.batch);
+    long long ty = ceil_div((long long)g.n1 * g.n3h, sh.lpb_y), tx = ceil_div((long long)g.n2 * g.n3h, sh.lpb_x);
+    if (sh.grid_y > 0 && sh.grid_y < ty) ty = sh.grid_y;
+    if (sh.grid_x > 0 && sh.grid_x < tx) tx = sh.grid_x;
+    dim3 gy((unsigned)ty, (unsigned)g.batch);
+    dim3 gx((unsigned)tx, (unsigned)g.batch);
     dim3 gu((unsigned)sh.grid_update, (unsigned)g.batch);
     const T inv_n = (T)(1.0 / (double)g.N);
     CCMF_DISPATCH_LINES(sh.pairs_per_block, {
@@ -237,24 +258,26 @@ void launch_passes(const Ctx<T>& c, const Ptrs<T>& p, cudaStream_t st, F&& betwe
             g, p, c.ax[0], c.ax[1], c.tw[0], c.tw[1], c.rsym[0], c.rsym[1], c.sym[2], inv_n);
         between(kKFftPlane);
     } else {
+        const FastDiv dly = make_fastdiv((unsigned)sh.lpb_y), dlx = make_fastdiv((unsigned)sh.lpb_x);
         CCMF_DISPATCH_LINES(sh.lpb_y, {
-            k_fft_strided<T, 0, LN><<<gy, kThreads, sh.smem_y, st>>>(g, p, c.ax[1], c.tw[1], c.sym[0], c.sym[1],
-                                                                      c.sym[2], inv_n);
+            k_fft_lines<T, 0, LN><<<gy, kThreads, sh.smem_y, st>>>(g, p, c.ax[1], c.tw[1], c.rsym[0], c.rsym[1],
+                                                                    c.sym[2], inv_n, dly);
         });
         between(kKFftYFwd);
         CCMF_DISPATCH_LINES(sh.lpb_x, {
-            k_fft_strided<T, 1, LN><<<gx, kThreads, sh.smem_x, st>>>(g, p, c.ax[0], c.tw[0], c.sym[0], c.sym[1],
-                                                                      c.sym[2], inv_n);
+            k_fft_lines<T, 1, LN><<<gx, kThreads, sh.smem_x, st>>>(g, p, c.ax[0], c.tw[0], c.rsym[0], c.rsym[1],
+                                                                    c.sym[2], inv_n, dlx);
         });
         between(kKFftXSolve);
         CCMF_DISPATCH_LINES(sh.lpb_y, {
-            k_fft_strided<T, 2, LN><<<gy, kThreads, sh.smem_y, st>>>(g, p, c.ax[1], c.tw[1], c.sym[0], c.sym[1],
-                                                                      c.sym[2], inv_n);
+            k_fft_lines<T, 2, LN><<<gy, kThreads, sh.smem_y, st>>>(g, p, c.ax[1], c.tw[1], c.rsym[0], c.rsym[1],
+                                                                    c.sym[2], inv_n, dly);
         });
         between(kKFftYInv);
     }
-    CCMF_DISPATCH_LINES(sh.pairs_per_block,
-                        { k_irfft_z<T, LN><<<gz, kThreads, sh.smem_z, st>>>(g, p, c.ax[2], c.tw[2]); });
+    const dim3 gzi((unsigned)ceil_div(pairs, sh.pairs_inv), (unsigned)g.batch);
+    CCMF_DISPATCH_LINES(sh.pairs_inv,
+                        { k_irfft_z<T, LN><<<gzi, kThreads, sh.smem_zi, st>>>(g, p, c.ax[2], c.tw[2]); });
     between(kKIrfftZ);
     if (OUT)
         k_update<T, true><<<gu, kThreads, 0, st>>>(g, p, c.cfg);

@@ -47,11 +47,24 @@ namespace {
 
 unsigned char* g_scratch_ptr[kMaxDevices];   // device address of g_ccmf_scratch per device
 
+// Frequency held by slot p after the in-place decimation-in-frequency stages of
+// the radix schedule ap: k(p) = sum_s q_s prod_{t<s} R_t, q_s = (p / m_s) mod R_s.
+__device__ int slot_frequency(const AxisPlan& ap, int p) {
+    int k = 0, w = 1;
+    for (int t = 0; t < ap.nst; ++t) {
+        const int m = ap.span[t] / ap.rad[t];
+        k += ((p / m) % ap.rad[t]) * w;
+        w *= ap.rad[t];
+    }
+    return k;
+}
+
 // Twiddle W_n^t = exp(-2 pi i t / n) and symbol 4 sin^2(pi t / n) tables of the
-// three axes, written into the scratch area (double arithmetic, stored as T).
+// three axes, and the x and y symbols in digit-reversed slot order, written into
+// the scratch area (double arithmetic, stored as T).
 template <typename T>
-__global__ void k_static_tables(cx<T>* tw0, cx<T>* tw1, cx<T>* tw2, T* sy0, T* sy1, T* sy2, int n1, int n2,
-                                int n3) {
+__global__ void k_static_tables(cx<T>* tw0, cx<T>* tw1, cx<T>* tw2, T* sy0, T* sy1, T* sy2, T* rs0, T* rs1,
+                                AxisPlan ax0, AxisPlan ax1, int n1, int n2, int n3) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int n[3] = {n1, n2, n3};
     cx<T>* tw[3] = {tw0, tw1, tw2};
@@ -63,6 +76,14 @@ __global__ void k_static_tables(cx<T>* tw0, cx<T>* tw1, cx<T>* tw2, T* sy0, T* s
         tw[a][t] = cmake<cx<T>>((T)c, (T)s);
         const double h = sinpi((double)t / (double)n[a]);
         sy[a][t] = (T)(4.0 * h * h);
+    }
+    if (t < n1) {
+        const double h = sinpi((double)slot_frequency(ax0, t) / (double)n1);
+        rs0[t] = (T)(4.0 * h * h);
+    }
+    if (t < n2) {
+        const double h = sinpi((double)slot_frequency(ax1, t) / (double)n2);
+        rs1[t] = (T)(4.0 * h * h);
     }
 }
 
@@ -137,6 +158,8 @@ int static_solve(int n1, int n2, int n3, const T* gamma, const double* xi_bar, c
     sh.lpb_y = lines_for(n2, cs);
     sh.lpb_x = lines_for(n1, cs);
     sh.smem_z = ((size_t)n3 + 2 * (size_t)n3 * (sh.pairs_per_block + 1)) * cs;
+    sh.pairs_inv = sh.pairs_per_block;
+    sh.smem_zi = sh.smem_z;
     sh.smem_y = ((size_t)n2 + 2 * (size_t)n2 * (sh.lpb_y + 1)) * cs;
     sh.smem_x = ((size_t)n1 + 2 * (size_t)n1 * (sh.lpb_x + 1)) * cs;
     long long gu = (g.N + kThreads - 1) / kThreads;
@@ -159,6 +182,8 @@ int static_solve(int n1, int n2, int n3, const T* gamma, const double* xi_bar, c
     size_t o_tw[3], o_sy[3];
     for (int a = 0; a < 3; ++a) o_tw[a] = take(cs * (size_t)nn[a]);
     for (int a = 0; a < 3; ++a) o_sy[a] = take(sizeof(T) * (size_t)nn[a]);
+    size_t o_rs[2];
+    for (int a = 0; a < 2; ++a) o_rs[a] = take(sizeof(T) * (size_t)nn[a]);
     if (off > kStaticScratchBytes) return CCMF_ERR_UNSUPPORTED_SIZE;
 
     unsigned char* ws = nullptr;
@@ -183,6 +208,7 @@ int static_solve(int n1, int n2, int n3, const T* gamma, const double* xi_bar, c
         c.tw[a] = reinterpret_cast<const cx<T>*>(ws + o_tw[a]);
         c.sym[a] = reinterpret_cast<const T*>(ws + o_sy[a]);
     }
+    for (int a = 0; a < 2; ++a) c.rsym[a] = reinterpret_cast<const T*>(ws + o_rs[a]);
     c.xi_stage = reinterpret_cast<const double*>(ws + o_xi);
     c.p.sc = reinterpret_cast<SolveScalars*>(ws + o_sc);
     c.p.n_active = reinterpret_cast<int*>(ws + o_nact);
@@ -211,7 +237,8 @@ int static_solve(int n1, int n2, int n3, const T* gamma, const double* xi_bar, c
     k_static_tables<T><<<(nmax + 127) / 128, 128, 0, st>>>(
         reinterpret_cast<cx<T>*>(ws + o_tw[0]), reinterpret_cast<cx<T>*>(ws + o_tw[1]),
         reinterpret_cast<cx<T>*>(ws + o_tw[2]), reinterpret_cast<T*>(ws + o_sy[0]), reinterpret_cast<T*>(ws + o_sy[1]),
-        reinterpret_cast<T*>(ws + o_sy[2]), n1, n2, n3);
+        reinterpret_cast<T*>(ws + o_sy[2]), reinterpret_cast<T*>(ws + o_rs[0]), reinterpret_cast<T*>(ws + o_rs[1]),
+        c.ax[0], c.ax[1], n1, n2, n3);
     launch_init<T>(c, st);
     if (cudaGetLastError() != cudaSuccess) return CCMF_ERR_CUDA;
 

@@ -79,7 +79,9 @@ struct Ptrs {
 };
 
 struct LaunchShape {
-    int pairs_per_block;      // z passes: line pairs per block
+    int pairs_per_block;      // divergence + forward z pass: line pairs per block
+    int pairs_inv;            // inverse z pass: line pairs per block
+    size_t smem_zi;           // its dynamic shared memory
     int lpb_y, lpb_x;         // strided passes: lines per block
     int grid_update;          // blocks per solve of the voxel passes
     size_t smem_z, smem_y, smem_x;
@@ -94,6 +96,7 @@ struct LaunchShape {
     int plane_fused;          // 1: y / x / solve / x / y in one plane launch per iteration
     size_t smem_plane;        // its dynamic shared memory (per block)
     int plane_cluster;        // blocks sharing one plane: 1 = k_fft_plane, 2..16 = k_fft_plane_cluster
+    int grid_y, grid_x;       // persistent blocks per solve of the y / x line passes (0: one tile per block)
     FastDiv div_r1, div_r2;   // rows (n1 / C) and columns (n2 / C) of one cluster block
 };
 

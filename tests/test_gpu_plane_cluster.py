@@ -89,14 +89,16 @@ def test_plane_pass_choice_rules(monkeypatch):
     bad.close()
 
 
-def test_fp32_plane_512_against_fp64_oracle(monkeypatch):
-    """512 x 512 x 6 two-phase field (the 512^3 workload's plane, cluster of 16 blocks):
-    FP32-mixed fields at equal iterations within FP32 accuracy of the FP64 oracle."""
+@pytest.mark.parametrize("blocks", [16, 0], ids=["cluster16", "line_passes"])
+def test_fp32_plane_512_against_fp64_oracle(blocks, monkeypatch):
+    """512 x 512 x 6 two-phase field (the 512^3 workload's plane) through a cluster of 16
+    blocks and through the persistent line passes: FP32-mixed fields at equal iterations
+    within FP32 accuracy of the FP64 oracle."""
     gamma = M.random_two_phase((512, 512, 6), 0.3, 0.25, 1.0, 77)
     normals = [[0.36, 0.48, 0.8]]
     out = run(gamma.astype(np.float32), normals, ccmf.Params(fixed_iters=8, rho_rule=ccmf.CCMF_RHO_CONST),
-              ccmf.CCMF_FP32_MIXED, monkeypatch, 16)
-    assert out["info"]["plane_blocks"] == 16
+              ccmf.CCMF_FP32_MIXED, monkeypatch, blocks)
+    assert out["info"]["plane_blocks"] == blocks
     ref = O.solve(gamma.astype(np.float32).astype(np.float64), normals[0],
                   O.Params(fixed_iters=8, rho_rule=O.RHO_CONST), record_history=False)
     scale = max(np.abs(ref.v).max(), np.abs(ref.e).max())

@@ -244,6 +244,11 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
+def _check_tuning(code, where):
+    if code != 0:
+        raise RuntimeError(f"tuning table {where}: status {code}")
+
+
 def graph_ms_per_iter(plan, gamma_dev, normals, iters=30):
     """Device time per iteration of the captured loop (CUDA events on the launching stream)."""
     import torch
@@ -421,27 +426,43 @@ def run_gpu(args, world, rank, local):
     np_dtype = np.float64 if prec == ccmf.CCMF_FP64 else np.float32
     esize = 8 if prec == ccmf.CCMF_FP64 else 4
     gamma_np = make_gamma(name, np_dtype)
+    if args.grid:
+        # a corner block of the workload's field (smaller profiling cases of the same kernels)
+        n = [int(x) for x in args.grid.lower().split("x")]
+        gamma_np = np.ascontiguousarray(gamma_np[:n[0], :n[1], :n[2]])
     normals = np.asarray(wl["normals"], dtype=np.float64)
     B = normals.shape[0]
     n1, n2, n3 = gamma_np.shape
     N = n1 * n2 * n3
+    if args.tuning_in:
+        _check_tuning(ccmf.ccmf_tuning_import(open(args.tuning_in).read()), args.tuning_in)
     plan = ccmf.Plan(gamma_np.shape, batch=B, precision=prec, device=dev)
     gamma_dev = torch.from_numpy(gamma_np).to(dev)
     K, W = args.steps, args.warmup
 
+    if args.tuning_json:   # explicit knobs apply from the warm-up on
+        plan.set_tuning(**json.loads(args.tuning_json))
     # initial state + warm-up (W iterations), untimed
     plan.solve(gamma_dev, normals, ccmf.Params(fixed_iters=W, check_every=W))
     torch.cuda.synchronize()
     # launch-shape autotuner (setup, outside the timed region): coordinate descent over the
     # update-pass variant, plane pass, lines per block, graph branches and radix schedule
     tune = None
-    if not args.no_autotune:
+    if args.tuning_json:
+        tune = {"tuning": plan.tuning(), "note": "set from --tuning-json"}
+    elif args.tuning_in:
+        tune = {"tuning": plan.tuning(), "note": f"imported from {os.path.basename(args.tuning_in)}"}
+    elif not args.no_autotune:
         t_tune = time.perf_counter()
         best, tune_ms = plan.autotune(gamma_dev, normals, iters=args.tune_iters)
         tune = {"tuning": best, "ms_per_iter": tune_ms, "seconds": time.perf_counter() - t_tune,
                 "iters_per_candidate": args.tune_iters}
     else:
         tune = {"tuning": plan.tuning(), "note": "built-in rules (--no-autotune)"}
+    if args.tuning_out:
+        code, text = ccmf.ccmf_tuning_export()
+        _check_tuning(code, "export")
+        open(args.tuning_out, "w").write(text)
     stream = torch.cuda.current_stream(dev)
     p_timed = ccmf.Params(fixed_iters=K, check_every=K, resume=1)
     # capture the loop graph outside the timed region (same key as the timed call)
@@ -533,7 +554,8 @@ def run_gpu(args, world, rank, local):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
                 "ms_per_step": t_ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if esize == 8 else "f32", "data": "synthetic",
-                "config": {"workload": wl["desc"] + (" FP64" if esize == 8 else " FP32-mixed (FP64 reductions)"),
+                "config": {"workload": wl["desc"] + (f" -- corner block {args.grid}" if args.grid else "") +
+                                       (" FP64" if esize == 8 else " FP32-mixed (FP64 reductions)"),
                            "grid": [n1, n2, n3], "solves": B, "parallelism": f"replicas x{world}",
                            "l2": f"inputs larger than L2: state {12 * esize * N * B / 1e6:.0f} MB per step",
                            "precision": args.precision},
@@ -561,6 +583,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch-shape rules")
     ap.add_argument("--tune-iters", type=int, default=10, help="iterations timed per autotuner candidate")
+    ap.add_argument("--tuning-in", default=None, help="tuning table text to import instead of autotuning")
+    ap.add_argument("--tuning-out", default=None, help="write the tuning table text here after autotuning")
+    ap.add_argument("--tuning-json", default=None, help="knob values (JSON object) set on the plan, no autotuning")
+    ap.add_argument("--grid", default=None, help="N1xN2xN3 corner block of the workload's field (profiling cases)")
     ap.add_argument("--no-speedup", action="store_true",
                     help="skip the FP32-mixed vs FP64 time-to-accuracy measurement")
     args = ap.parse_args()

@@ -203,6 +203,8 @@ typedef struct {
     int radix_mode;         /* radix schedule of every axis: 0 radix 8 first, then 4, 2, 3, 5;
                                1 as 0 but radix 4s in place of a radix 8 + 2 tail; 2 radix 4 at most */
     int zinv_pairs_per_block; /* inverse z pass: line pairs per block, power of two 1..16 */
+    int line_engine;        /* strided y / x passes: 0 in-place radix stages per block (any length),
+                               1 one warp per line for power-of-two lengths 128..1024 */
 } ccmf_tuning;
 
 /* The plan's current knob values (every entry resolved, none negative). */
@@ -219,7 +221,8 @@ int ccmf_plan_set_tuning(ccmf_plan* plan, const ccmf_tuning* tuning);
  * fastest. The search is coordinate descent over the knobs in the order of
  * ccmf_tuning, starting from the current tuning. It advances the plan's ADMM state
  * (the workspace must hold a solve of these inputs, as ccmf_solve leaves it), runs
- * every candidate for `iters` iterations twice, and records the winner in the
+ * every candidate for `iters` iterations three times (the fastest of the last two
+ * counts; a candidate must win by 1 %), and records the winner in the
  * library's tuning table under (N1, N2, N3, batch, precision, SM count): plans
  * created later with that key start from it.
  *   gamma, gamma_stride, xi_bar, workspace : as for ccmf_solve
@@ -233,7 +236,7 @@ int ccmf_plan_autotune(ccmf_plan* plan, const void* gamma, long long gamma_strid
 
 /*
  * The tuning table as text, one line per key
- * ("ccmf-tuning N1 N2 N3 batch precision sms : 8 knob values"). Writes at most
+ * ("ccmf-tuning N1 N2 N3 batch precision sms : 9 knob values"). Writes at most
  * capacity bytes (NUL-terminated) and the full length in *length.
  */
 int ccmf_tuning_export(char* text, size_t capacity, size_t* length);

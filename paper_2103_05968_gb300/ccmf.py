@@ -78,6 +78,7 @@ class ccmf_tuning(ctypes.Structure):
         ("branches", ctypes.c_int),
         ("radix_mode", ctypes.c_int),
         ("zinv_pairs_per_block", ctypes.c_int),
+        ("line_engine", ctypes.c_int),
     ]
 
 

@@ -261,4 +261,56 @@ __device__ void inplace_fft(C* buf, const AxisPlan& ap, int nlines, int es, int 
     }
 }
 
+// Warp-local Stockham FFT of one line of compile-time length N (a power of two,
+// 64 <= N <= 1024) held in shared memory at x[m * es]: the 32 lanes of one warp
+// run the radix-8 / 4 / 2 passes (Ns = 1, R, R R', ...) alone, with __syncwarp
+// between the load and store halves of each pass, so no block barrier is needed.
+// Each lane keeps its butterflies' inputs in registers for the store half, which
+// makes the autosort pass safe in place. Forward kernel exp(-2 pi i / N);
+// natural-order input and output. tw[t] = W_N^t, t < N.
+template <typename C, int N, int NS>
+__device__ __forceinline__ void warp_stockham(C* x, int es, const C* __restrict__ tw, int lane) {
+    if constexpr (NS < N) {
+        constexpr int REM = N / NS;
+        // the largest radix that still gives every lane a butterfly
+        constexpr int R = (REM % 8 == 0 && N / 8 >= 32) ? 8 : (REM % 4 == 0 && N / 4 >= 32) ? 4 : 2;
+        constexpr int NB = N / R;                 // butterflies of the pass
+        constexpr int PER = (NB + 31) / 32;       // butterflies per lane
+        constexpr int TWS = N / (NS * R);         // twiddle table step
+        C v[PER][R];
+#pragma unroll
+        for (int b = 0; b < PER; ++b) {
+            const int j = lane + 32 * b;
+            if (NB % 32 == 0 || j < NB) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[b][r] = x[(j + r * NB) * es];
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int b = 0; b < PER; ++b) {
+            const int j = lane + 32 * b;
+            if (NB % 32 == 0 || j < NB) {
+                const int jm = j & (NS - 1);
+                if constexpr (NS > 1) {
+#pragma unroll
+                    for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], tw[jm * r * TWS]);
+                }
+                Dft<C, R>::run(v[b]);
+                const int od = (j - jm) * R + jm;
+#pragma unroll
+                for (int r = 0; r < R; ++r) x[(od + r * NS) * es] = v[b][r];
+            }
+        }
+        __syncwarp();
+        warp_stockham<C, N, NS * R>(x, es, tw, lane);
+    }
+}
+
+template <typename C, int N>
+__device__ __forceinline__ void warp_fft(C* x, int es, const C* __restrict__ tw, int lane) {
+    static_assert(N >= 64 && N <= 1024 && (N & (N - 1)) == 0, "warp FFT length");
+    warp_stockham<C, N, 1>(x, es, tw, lane);
+}
+
 }  // namespace ccmf

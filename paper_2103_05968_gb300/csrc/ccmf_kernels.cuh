@@ -5,7 +5,7 @@
 //   1. k_div_rfft_z     w = e - v/rho, d = div^- A* w (Sec. 2.2, Eq. 17) fused
 //                       with the real-to-complex FFT along z (two real lines per
 //                       complex transform);
-//   2. k_fft_lines<0>   forward FFT along y;
+//   2. k_fft_lines<0>   forward FFT along y (k_fft_wlines<0> for power-of-two n2);
 //   3. k_fft_lines<1>   forward FFT along x, Poisson solve
 //                       phi^ = d^ / (-sum_a 4 sin^2(pi k_a / N_a)), phi^(0) = 0
 //                       (the (div^- grad^+)^+ of Eq. 28), inverse FFT along x;
@@ -122,18 +122,29 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_init_stats(Geom g, Ptrs<T> p, LoopConfig cfg) {
     const int s = blockIdx.y + p.s0;
     const T* gam = gamma_of(p, s);
-    double acc_min = INFINITY, acc_max = -INFINITY, acc_sum = 0.0, acc_bad = 0.0;
+    // element type per element (min / max are exact in T); the sum goes to double every
+    // 32 elements, so FP32 plans do not pay the FP64 rate per element
+    T tmin = T(INFINITY), tmax = T(-INFINITY), csum = T(0);
+    double acc_sum = 0.0, acc_bad = 0.0;
+    int cnt = 0;
     const long long stride = (long long)gridDim.x * kThreads;
     for (long long lin = (long long)blockIdx.x * kThreads + threadIdx.x; lin < g.N; lin += stride) {
-        double x = (double)gam[lin];
-        if (!(x >= 0.0) || !isfinite(x)) {
+        const T x = gam[lin];
+        if (!(x >= T(0)) || !isfinite(x)) {
             acc_bad += 1.0;
         } else {
-            acc_min = fmin(acc_min, x);
-            acc_max = fmax(acc_max, x);
-            acc_sum += x;
+            tmin = fmin(tmin, x);
+            tmax = fmax(tmax, x);
+            csum += x;
+            if (++cnt == 32) {
+                acc_sum += (double)csum;
+                csum = T(0);
+                cnt = 0;
+            }
         }
     }
+    acc_sum += (double)csum;
+    double acc_min = (double)tmin, acc_max = (double)tmax;
     // min / max via shuffles, sums via the generic partial path
     for (int off = 16; off > 0; off >>= 1) {
         acc_min = fmin(acc_min, __shfl_xor_sync(0xffffffffu, acc_min, off));
@@ -511,6 +522,120 @@ __global__ void __launch_bounds__(kThreads) k_fft_lines(Geom g, Ptrs<T> p, AxisP
             }
         }
         __syncthreads();   // the buffer is refilled two tiles later
+        cur ^= 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The same three line passes for power-of-two line lengths N (128 ... 1024), with
+// one warp per line: a tile is 8 lines, the warps transform their lines with the
+// warp-local Stockham FFT (natural order in and out, no block barrier between
+// radix passes). Loads and stores stay cooperative and coalesced (cp.async into
+// the second buffer while the first is transformed). x lines are padded to an odd
+// stride in shared memory so the strided loads do not conflict. MODE 1 reads the
+// x symbol in natural order and the y symbol in the order the y pass left
+// (ysym: natural after this kernel's MODE 0, digit-reversed after k_fft_lines).
+// ---------------------------------------------------------------------------
+template <typename T, int MODE, int N>
+__global__ void __launch_bounds__(kThreads) k_fft_wlines(Geom g, Ptrs<T> p, const cx<T>* __restrict__ tw,
+                                                         const T* __restrict__ xsym, const T* __restrict__ ysym,
+                                                         const T* __restrict__ sym3, T inv_n) {
+    using C = cx<T>;
+    constexpr int L = kThreads / 32;              // lines per tile, one per warp
+    constexpr int LS = N + (MODE == 1 ? 1 : 0);   // line stride in shared memory
+    const int s = blockIdx.y + p.s0;
+    if (!p.run_all && !p.sc[s].active) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* twl = reinterpret_cast<C*>(smem_raw);
+    C* buf[2];
+    buf[0] = twl + N;
+    buf[1] = buf[0] + (size_t)L * LS;
+    for (int t = threadIdx.x; t < N; t += kThreads) twl[t] = tw[t];
+    const long long plane = (long long)g.n1 * g.n2;
+    const long long nlines = (MODE == 1) ? (long long)g.n3h * g.n2 : (long long)g.n3h * g.n1;
+    const long long ntiles = (nlines + L - 1) / L;
+    C* spec = p.spec + (size_t)s * g.Nh;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int cl = threadIdx.x & (L - 1);         // MODE 1: this thread's line in a tile
+    const int m0 = threadIdx.x / L;
+    constexpr int mstep = kThreads / L;
+    auto issue = [&](long long t, C* b) {
+        const long long l0 = t * L;
+        if (MODE == 1) {
+            const long long l = l0 + cl;
+            if (l < nlines) {
+                const int kz = (int)fdiv((unsigned)l, g.div_n2);
+                const int k2 = (int)(l - (long long)kz * g.n2);
+                const C* src = spec + (long long)kz * plane + k2;
+                for (int m = m0; m < N; m += mstep) cp_async_cx(&b[cl * LS + m], src + (long long)m * g.n2);
+            } else {
+                for (int m = m0; m < N; m += mstep) b[cl * LS + m] = cmake<C>(T(0), T(0));
+            }
+        } else {
+            for (int idx = threadIdx.x; idx < L * N; idx += kThreads) {
+                const int c = idx / N, m = idx % N;
+                const long long l = l0 + c;
+                if (l < nlines)
+                    cp_async_cx(&b[c * LS + m], spec + l * N + m);
+                else
+                    b[c * LS + m] = cmake<C>(T(0), T(0));
+            }
+        }
+        cp_async_commit();
+    };
+    long long t = blockIdx.x;
+    int cur = 0;
+    if (t < ntiles) issue(t, buf[0]);
+    for (; t < ntiles; t += gridDim.x) {
+        const long long tn = t + gridDim.x;
+        if (tn < ntiles)
+            issue(tn, buf[cur ^ 1]);
+        else
+            cp_async_commit();
+        cp_async_wait_one();
+        __syncthreads();
+        C* b = buf[cur];
+        const long long l0 = t * L;
+        C* x = b + warp * LS;
+        warp_fft<C, N>(x, 1, twl, lane);
+        if (MODE == 1) {
+            const long long l = l0 + warp;
+            const bool valid = l < nlines;
+            int kz = 0, k2 = 0;
+            if (valid) {
+                kz = (int)fdiv((unsigned)l, g.div_n2);
+                k2 = (int)(l - (long long)kz * g.n2);
+            }
+            const T lam23 = valid ? ysym[k2] + sym3[kz] : T(0);
+            for (int m = lane; m < N; m += 32) {
+                const T lam = xsym[m] + lam23;
+                const T gk = (valid && lam > T(0)) ? -inv_n / lam : T(0);
+                const C z = x[m];
+                x[m] = cmake<C>(z.x * gk, -z.y * gk);   // conj: the inverse runs as conj(FFT(conj(.)))
+            }
+            __syncwarp();
+            warp_fft<C, N>(x, 1, twl, lane);
+        }
+        __syncthreads();
+        if (MODE == 1) {
+            const long long l = l0 + cl;
+            if (l < nlines) {
+                const int kz = (int)fdiv((unsigned)l, g.div_n2);
+                const int k2 = (int)(l - (long long)kz * g.n2);
+                C* dst = spec + (long long)kz * plane + k2;
+                for (int m = m0; m < N; m += mstep) dst[(long long)m * g.n2] = b[cl * LS + m];
+            }
+        } else {
+            for (int idx = threadIdx.x; idx < L * N; idx += kThreads) {
+                const int c = idx / N, m = idx % N;
+                const long long l = l0 + c;
+                if (l < nlines) {
+                    const C v = b[c * LS + m];
+                    spec[l * N + m] = (MODE == 2) ? cconj(v) : v;
+                }
+            }
+        }
+        __syncthreads();
         cur ^= 1;
     }
 }
@@ -1049,13 +1174,13 @@ __global__ void __launch_bounds__(kThreads) k_update(Geom g, Ptrs<T> p, LoopConf
 
 // Vector version of the advancing update: W consecutive voxels of a z line per
 // thread, 16-byte loads and stores (N3 % W == 0, 16-byte aligned gamma).
-template <typename T>
+template <typename T, bool OUT>
 __global__ void __launch_bounds__(kThreads) k_update_vec(Geom g, Ptrs<T> p, LoopConfig cfg) {
     constexpr int W = Vec16<T>::W;
     using V = Vec16<T>;
     const int s = blockIdx.y + p.s0;
     SolveScalars& S = p.sc[s];
-    if (!S.active) return;
+    if (!OUT && !S.active) return;
     const long long N = g.N;
     const double rho_d = S.rho;
     const StepConsts<T> K = step_consts<T>(S, cfg);
@@ -1105,7 +1230,7 @@ __global__ void __launch_bounds__(kThreads) k_update_vec(Geom g, Ptrs<T> p, Loop
         const T e2z_after = __ldg(e + 5 * N + rn.row + kp), v2z_after = __ldg(v + 5 * N + rn.row + kp);
         const T e1z_before = __ldg(e + 2 * N + rn.row + km), v1z_before = __ldg(v + 2 * N + rn.row + km);
         const T ph_after = __ldg(phi + rn.row + kp), ph_before = __ldg(phi + rn.row + km);
-        T eo[6][W], vo[6][W];
+        T eo[6][W], vo[6][W], fo[3][W];
 #pragma unroll
         for (int u = 0; u < W; ++u) {
             T ecu[6], vcu[6];
@@ -1122,20 +1247,36 @@ __global__ void __launch_bounds__(kThreads) k_update_vec(Geom g, Ptrs<T> p, Loop
             const T e1m[3] = {e1x[u], e1y[u], first ? e1z_before : ec[2][(u + W - 1) % W]};
             const T v1m[3] = {v1x[u], v1y[u], first ? v1z_before : vc[2][(u + W - 1) % W]};
             T eou[6], vou[6], fl[3];
-            voxel_step<T, false>(K, ecu, vcu, gm[u], ph[u], php, phm, e2p, v2p, e1m, v1m, acc, eou, vou, fl);
+            voxel_step<T, OUT>(K, ecu, vcu, gm[u], ph[u], php, phm, e2p, v2p, e1m, v1m, acc, eou, vou, fl);
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
                 eo[c][u] = eou[c];
                 vo[c][u] = vou[c];
             }
-        }
 #pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            V::st(e_out + c * N + lin0, eo[c]);
-            V::st(v_out + c * N + lin0, vo[c]);
+            for (int a = 0; a < 3; ++a) fo[a][u] = fl[a];
+        }
+        if (OUT) {
+            // final evaluation: the cut xi^{K+1/2} and the flow A* v^K
+            if (p.cut) {
+                T* cut = p.cut + (size_t)s * 6 * N;
+#pragma unroll
+                for (int c = 0; c < 6; ++c) V::st(cut + c * N + lin0, eo[c]);
+            }
+            if (p.flow) {
+                T* flow = p.flow + (size_t)s * 3 * N;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) V::st(flow + a * N + lin0, fo[a]);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                V::st(e_out + c * N + lin0, eo[c]);
+                V::st(v_out + c * N + lin0, vo[c]);
+            }
         }
     }
-    update_epilogue<T, false>(g, p, cfg, S, s, rho_d, acc);
+    update_epilogue<T, OUT>(g, p, cfg, S, s, rho_d, acc);
 }
 
 // ---------------------------------------------------------------------------

@@ -71,6 +71,16 @@ inline long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
         default: { constexpr int LN = 1; __VA_ARGS__; } break;  \
     }
 
+// Runs the statement list with the compile-time line length NN equal to the runtime
+// power of two n (128 ... 1024, the warp-per-line passes).
+#define CCMF_DISPATCH_N(n, ...)                                   \
+    switch (n) {                                                  \
+        case 128: { constexpr int NN = 128; __VA_ARGS__; } break;  \
+        case 256: { constexpr int NN = 256; __VA_ARGS__; } break;  \
+        case 512: { constexpr int NN = 512; __VA_ARGS__; } break;  \
+        default: { constexpr int NN = 1024; __VA_ARGS__; } break;  \
+    }
+
 // Runs the statement list with compile-time ST (stages) and NTH (threads) of a
 // pipelined update variant 2..7.
 #define CCMF_DISPATCH_PIPE(VAR, ...)                                                 \
@@ -144,6 +154,24 @@ int lines_blocks_per_sm(int mode, int lines, size_t smem) {
     return nb;
 }
 
+// Blocks per SM of a warp-per-line pass of length n (power of two 128 ... 1024), 0 on error.
+template <typename T>
+int wlines_blocks_per_sm(int mode, int n, size_t smem) {
+    int nb = 0;
+    cudaError_t err = cudaSuccess;
+    CCMF_DISPATCH_N(n, {
+        const void* f = mode == 0 ? (const void*)k_fft_wlines<T, 0, NN>
+                                  : mode == 1 ? (const void*)k_fft_wlines<T, 1, NN> : (const void*)k_fft_wlines<T, 2, NN>;
+        err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kThreads, smem);
+    });
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
 // Sets the launch attributes of the cluster plane pass and returns how many of its
 // clusters can be resident at once (0: this cluster size cannot be launched).
 template <typename T, int CL>
@@ -201,6 +229,13 @@ cudaError_t configure_kernels(const LaunchShape& sh) {
         set((const void*)k_fft_lines<T, 2, LN>, sh.smem_y);
     });
     CCMF_DISPATCH_LINES(sh.lpb_x, { set((const void*)k_fft_lines<T, 1, LN>, sh.smem_x); });
+    if (sh.wl_y) {
+        CCMF_DISPATCH_N(sh.wl_y, {
+            set((const void*)k_fft_wlines<T, 0, NN>, sh.smem_wy);
+            set((const void*)k_fft_wlines<T, 2, NN>, sh.smem_wy);
+        });
+    }
+    if (sh.wl_x) { CCMF_DISPATCH_N(sh.wl_x, { set((const void*)k_fft_wlines<T, 1, NN>, sh.smem_wx); }); }
     if (sh.plane_fused && sh.plane_cluster <= 1) set((const void*)k_fft_plane<T>, sh.smem_plane);
     if (sh.plane_fused && sh.plane_cluster > 1 && err == cudaSuccess &&
         plane_cluster_capacity<T>(sh.plane_cluster, sh.smem_plane) < 1)
@@ -228,6 +263,12 @@ void launch_init(const Ctx<T>& c, cudaStream_t st) {
     if (!c.cfg.resume) k_init_state<T><<<grid, kThreads, 0, st>>>(c.g, c.p);
 }
 
+// The 16-byte final evaluation pass needs 16-byte aligned cut and flow outputs.
+template <typename T>
+bool vec_out_ok(const Ptrs<T>& p) {
+    return ((uintptr_t)p.cut % 16) == 0 && ((uintptr_t)p.flow % 16) == 0;
+}
+
 // Enqueue one ADMM iteration (or, with OUT, the final evaluation).
 // `between` is called after every kernel with its class (used to record events).
 template <typename T, bool OUT, typename F>
@@ -241,6 +282,12 @@ void launch_passes(const Ctx<T>& c, const Ptrs<T>& p, cudaStream_t st, F&& betwe
     if (sh.grid_x > 0 && sh.grid_x < tx) tx = sh.grid_x;
     dim3 gy((unsigned)ty, (unsigned)g.batch);
     dim3 gx((unsigned)tx, (unsigned)g.batch);
+    constexpr int kWarpLines = kThreads / 32;   // lines per tile of the warp-per-line passes
+    long long twy = ceil_div((long long)g.n1 * g.n3h, kWarpLines), twx = ceil_div((long long)g.n2 * g.n3h, kWarpLines);
+    if (sh.grid_y > 0 && sh.grid_y < twy) twy = sh.grid_y;
+    if (sh.grid_x > 0 && sh.grid_x < twx) twx = sh.grid_x;
+    dim3 gwy((unsigned)twy, (unsigned)g.batch);
+    dim3 gwx((unsigned)twx, (unsigned)g.batch);
     dim3 gu((unsigned)sh.grid_update, (unsigned)g.batch);
     const T inv_n = (T)(1.0 / (double)g.N);
     CCMF_DISPATCH_LINES(sh.pairs_per_block, {
@@ -259,27 +306,52 @@ void launch_passes(const Ctx<T>& c, const Ptrs<T>& p, cudaStream_t st, F&& betwe
         between(kKFftPlane);
     } else {
         const FastDiv dly = make_fastdiv((unsigned)sh.lpb_y), dlx = make_fastdiv((unsigned)sh.lpb_x);
-        CCMF_DISPATCH_LINES(sh.lpb_y, {
-            k_fft_lines<T, 0, LN><<<gy, kThreads, sh.smem_y, st>>>(g, p, c.ax[1], c.tw[1], c.rsym[0], c.rsym[1],
-                                                                    c.sym[2], inv_n, dly);
-        });
+        // the y symbol in the order the y pass leaves: natural (warp lines) or digit-reversed
+        const T* ysym = sh.wl_y ? c.sym[1] : c.rsym[1];
+        if (sh.wl_y) {
+            CCMF_DISPATCH_N(sh.wl_y, {
+                k_fft_wlines<T, 0, NN><<<gwy, kThreads, sh.smem_wy, st>>>(g, p, c.tw[1], c.sym[0], ysym, c.sym[2],
+                                                                          inv_n);
+            });
+        } else {
+            CCMF_DISPATCH_LINES(sh.lpb_y, {
+                k_fft_lines<T, 0, LN><<<gy, kThreads, sh.smem_y, st>>>(g, p, c.ax[1], c.tw[1], c.rsym[0], ysym,
+                                                                        c.sym[2], inv_n, dly);
+            });
+        }
         between(kKFftYFwd);
-        CCMF_DISPATCH_LINES(sh.lpb_x, {
-            k_fft_lines<T, 1, LN><<<gx, kThreads, sh.smem_x, st>>>(g, p, c.ax[0], c.tw[0], c.rsym[0], c.rsym[1],
-                                                                    c.sym[2], inv_n, dlx);
-        });
+        if (sh.wl_x) {
+            CCMF_DISPATCH_N(sh.wl_x, {
+                k_fft_wlines<T, 1, NN><<<gwx, kThreads, sh.smem_wx, st>>>(g, p, c.tw[0], c.sym[0], ysym, c.sym[2],
+                                                                          inv_n);
+            });
+        } else {
+            CCMF_DISPATCH_LINES(sh.lpb_x, {
+                k_fft_lines<T, 1, LN><<<gx, kThreads, sh.smem_x, st>>>(g, p, c.ax[0], c.tw[0], c.rsym[0], ysym,
+                                                                        c.sym[2], inv_n, dlx);
+            });
+        }
         between(kKFftXSolve);
-        CCMF_DISPATCH_LINES(sh.lpb_y, {
-            k_fft_lines<T, 2, LN><<<gy, kThreads, sh.smem_y, st>>>(g, p, c.ax[1], c.tw[1], c.rsym[0], c.rsym[1],
-                                                                    c.sym[2], inv_n, dly);
-        });
+        if (sh.wl_y) {
+            CCMF_DISPATCH_N(sh.wl_y, {
+                k_fft_wlines<T, 2, NN><<<gwy, kThreads, sh.smem_wy, st>>>(g, p, c.tw[1], c.sym[0], ysym, c.sym[2],
+                                                                          inv_n);
+            });
+        } else {
+            CCMF_DISPATCH_LINES(sh.lpb_y, {
+                k_fft_lines<T, 2, LN><<<gy, kThreads, sh.smem_y, st>>>(g, p, c.ax[1], c.tw[1], c.rsym[0], ysym,
+                                                                        c.sym[2], inv_n, dly);
+            });
+        }
         between(kKFftYInv);
     }
     const dim3 gzi((unsigned)ceil_div(pairs, sh.pairs_inv), (unsigned)g.batch);
     CCMF_DISPATCH_LINES(sh.pairs_inv,
                         { k_irfft_z<T, LN><<<gzi, kThreads, sh.smem_zi, st>>>(g, p, c.ax[2], c.tw[2]); });
     between(kKIrfftZ);
-    if (OUT)
+    if (OUT && c.vec_update && vec_out_ok(p))
+        k_update_vec<T, true><<<gu, kThreads, 0, st>>>(g, p, c.cfg);
+    else if (OUT)
         k_update<T, true><<<gu, kThreads, 0, st>>>(g, p, c.cfg);
     else if (c.vec_update && sh.upd_variant >= 2) {
         const dim3 gp((unsigned)sh.grid_pipe, (unsigned)g.batch);
@@ -301,7 +373,7 @@ void launch_passes(const Ctx<T>& c, const Ptrs<T>& p, cudaStream_t st, F&& betwe
             k_update_tma<T, 1><<<gt, kThreads, sh.smem_tma, st>>>(g, p, c.cfg, sh.tma_rows);
     }
     else if (c.vec_update)
-        k_update_vec<T><<<gu, kThreads, 0, st>>>(g, p, c.cfg);
+        k_update_vec<T, false><<<gu, kThreads, 0, st>>>(g, p, c.cfg);
     else
         k_update<T, false><<<gu, kThreads, 0, st>>>(g, p, c.cfg);
     between(kKUpdate);

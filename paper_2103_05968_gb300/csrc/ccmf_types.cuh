@@ -97,6 +97,8 @@ struct LaunchShape {
     size_t smem_plane;        // its dynamic shared memory (per block)
     int plane_cluster;        // blocks sharing one plane: 1 = k_fft_plane, 2..16 = k_fft_plane_cluster
     int grid_y, grid_x;       // persistent blocks per solve of the y / x line passes (0: one tile per block)
+    int wl_y, wl_x;           // > 0: the y / x line passes run one warp per line (k_fft_wlines); the line length
+    size_t smem_wy, smem_wx;  // their dynamic shared memory
     FastDiv div_r1, div_r2;   // rows (n1 / C) and columns (n2 / C) of one cluster block
 };
 

@@ -91,3 +91,25 @@ def test_autotune_keeps_the_fastest_and_records_it():
         assert r["status"] == 0 and np.isfinite(r["gamma_eff"])
     plan.close()
     again.close()
+
+
+@pytest.mark.parametrize("shape", [(128, 256, 4), (128, 96, 6), (96, 128, 6)],
+                         ids=["warp_xy", "warp_x_generic_y", "generic_x_warp_y"])
+@pytest.mark.parametrize("engine", [1, 0], ids=["warp_lines", "block_lines"])
+def test_fp64_line_passes_against_oracle(shape, engine):
+    """Strided y / x passes with one warp per power-of-two line (natural order) or in-place
+    block stages (digit-reversed order), alone and mixed per axis: FP64 parity with the oracle."""
+    gamma = M.random_two_phase(shape, 0.3, 0.25, 1.0, 13)
+    normals = [[0.36, 0.48, 0.8]]
+    plan = ccmf.Plan(shape, batch=1, precision=ccmf.CCMF_FP64, device=DEV)
+    plan.set_tuning(plane_blocks=0, line_engine=engine)
+    assert plan.tuning()["line_engine"] == engine and plan.launch_info()["plane_fused"] == 0
+    res, flow, cut = plan.solve(torch.from_numpy(gamma).to(DEV), normals, ccmf.Params(fixed_iters=20),
+                                want_flow=True, want_cut=True)
+    e, v, rho, _ = plan.state()
+    ref = O.solve(gamma, normals[0], O.Params(fixed_iters=20), record_history=False)
+    assert abs(res[0]["gamma_eff"] - ref.gamma_eff) <= 1e-10 * ref.gamma_eff
+    np.testing.assert_allclose(e[0].cpu().numpy(), ref.e, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(v[0].cpu().numpy(), ref.v, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(cut[0].cpu().numpy(), ref.cut, rtol=0, atol=1e-9)
+    plan.close()

@@ -334,9 +334,11 @@ int shape_for(const ccmf_plan* pl, const ccmf_tuning& t, LaunchShape* out, ccmf_
     // (line_engine 1), else in-place radix stages over tiles of lines
     int le = r.line_engine;
     if (le < 0) {
+        // block stages by default: on GB300 the warp-per-line passes measured no faster
+        // at 512^2 planes (y passes level, x pass slower); the autotuner tries both
         const char* env = getenv("CCMF_LINE_ENGINE");
-        le = env ? atoi(env) : 1;
-        if (le < 0 || le > 1) le = 1;
+        le = env ? atoi(env) : 0;
+        if (le < 0 || le > 1) le = 0;
     }
     if (le > 1) return CCMF_ERR_UNSUPPORTED_SIZE;
     r.line_engine = le;

@@ -91,6 +91,12 @@ def run_batch(args, world, rank, local):
     batch = ccmf.Batch(shapes, precision=prec, device=dev)
     K, W = args.steps, args.warmup
     p = ccmf.Params(fixed_iters=K, check_every=K)
+    tune = None
+    if not args.no_autotune:   # set-up: every shape group's launch shape, timed on its own solves
+        t_tune = time.perf_counter()
+        ms_groups = batch.autotune(gammas, normals, iters=args.tune_iters)
+        tune = {"ms_per_iter_groups": ms_groups, "seconds": time.perf_counter() - t_tune,
+                "iters_per_candidate": args.tune_iters}
     batch.solve(gammas, normals, ccmf.Params(fixed_iters=W, check_every=W))
     batch.solve(gammas, normals, p, want_results=False)      # capture
     torch.cuda.synchronize()
@@ -120,7 +126,7 @@ def run_batch(args, world, rank, local):
                              "unit": "GB/s", "frac": step_bytes / (t_ms / K * 1e-3) / 1e9 / peak,
                              "traffic": None, "kernel": "whole step (196 B/voxel FP32 basis)",
                              "peak_kind": peak_kind},
-                "clocks": clk}
+                "autotune": tune, "clocks": clk}
         print(json.dumps(line), flush=True)
     batch.close()
 

@@ -296,6 +296,21 @@ int ccmf_batch_destroy(ccmf_batch* batch);
 /* Bytes of device workspace ccmf_batch_solve needs. */
 int ccmf_batch_workspace_bytes(const ccmf_batch* batch, size_t* bytes);
 
+/*
+ * Autotuner of a batch: for every shape group in turn, times `iters` iterations of
+ * that group's solves alone (a captured graph of its branches, on their current
+ * state) for candidate tunings of its sub-plan and keeps the fastest, by the
+ * coordinate descent of ccmf_plan_autotune. The winners go into the tuning table,
+ * so later batches and plans with the same group shapes and sizes start from them.
+ * It first runs a 2-iteration solve of the whole batch to set up the state, and the
+ * next ccmf_batch_solve captures its graph again.
+ *   gammas, xi_bar, workspace : as for ccmf_batch_solve
+ *   ms                        : optional host [buckets], each group's time per iteration
+ * Synchronises the stream.
+ */
+int ccmf_batch_autotune(ccmf_batch* batch, const void* const* gammas, const double* xi_bar, void* workspace,
+                        size_t workspace_bytes, int iters, double* ms, void* stream);
+
 /* Number of shape groups (sub-plans) of the batch. */
 int ccmf_batch_buckets(const ccmf_batch* batch, int* buckets);
 

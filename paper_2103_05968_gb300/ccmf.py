@@ -133,6 +133,9 @@ _SIGNATURES = {
     "ccmf_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "ccmf_batch_workspace_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     "ccmf_batch_buckets": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "ccmf_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
+                                            ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_size_t,
+                                            ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "ccmf_batch_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ccmf_params),
                                          ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ccmf_result),
@@ -337,6 +340,15 @@ def ccmf_batch_buckets(batch):
     n = ctypes.c_int()
     code = load_library().ccmf_batch_buckets(batch, ctypes.byref(n))
     return code, n.value
+
+
+def ccmf_batch_autotune(batch, gamma_ptrs, xi_bar, workspace_ptr, workspace_bytes, iters, buckets, stream):
+    ptrs = (ctypes.c_void_p * len(gamma_ptrs))(*[int(p) for p in gamma_ptrs])
+    xi = np.ascontiguousarray(xi_bar, dtype=np.float64).reshape(-1)
+    ms = (ctypes.c_double * max(1, buckets))()
+    code = load_library().ccmf_batch_autotune(batch, ptrs, xi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                              workspace_ptr, int(workspace_bytes), int(iters), ms, stream)
+    return code, list(ms[:buckets])
 
 
 def ccmf_batch_solve(batch, gamma_ptrs, xi_bar, params, workspace_ptr, workspace_bytes, results, stream):
@@ -590,6 +602,18 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+    def autotune(self, gammas, normals, iters=10):
+        """Tune every shape group's launch shape on its own solves (ccmf_batch_autotune);
+        returns each group's time per iteration in ms."""
+        torch = self.torch
+        ptrs = [g.data_ptr() for g in gammas]
+        with torch.cuda.device(self.device):
+            code, ms = ccmf_batch_autotune(self.handle, ptrs, np.asarray(normals, dtype=np.float64),
+                                           ctypes.c_void_p(self.ws_ptr), self.workspace_bytes, iters, self.buckets(),
+                                           _stream_handle(torch, self.device))
+        _check(code, "ccmf_batch_autotune")
+        return ms
 
     def solve(self, gammas, normals, params=None, want_results=True):
         """gammas: list of device tensors (one per solve, may repeat); normals: (count, 3)."""

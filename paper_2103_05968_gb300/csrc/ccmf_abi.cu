@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <new>
@@ -717,6 +718,56 @@ int apply_tuning(ccmf_plan* pl, const ccmf_tuning& t) {
     return CCMF_OK;
 }
 
+
+// Coordinate descent over the tuning knobs of a plan in the order of ccmf_tuning,
+// from its current tuning; measure(&ms) times the plan as it is. A candidate must
+// win by 1 % to be kept. Leaves the plan in the best tuning found.
+int tune_descent(ccmf_plan* plan, const std::function<int(double*)>& measure, double* best_ms) {
+    ccmf_tuning cur = plan->tune;
+    double cur_ms = 0.0;
+    int rc = measure(&cur_ms);
+    // coordinate descent over the knobs; a candidate must win by 1 % to be kept
+    struct Knob {
+        int ccmf_tuning::*field;
+        std::vector<int> values;
+    };
+    std::vector<int> brs;
+    for (int b = 1; b <= std::min(kMaxBranches, plan->batch); ++b) brs.push_back(b);
+    const Knob knobs[] = {
+        {&ccmf_tuning::update_variant, {0, 1, 2, 3, 4, 5, 6, 7}},
+        {&ccmf_tuning::plane_blocks, {0, 1, 2, 4, 8, 16}},
+        {&ccmf_tuning::z_pairs_per_block, {1, 2, 4, 8, 16}},
+        {&ccmf_tuning::y_lines_per_block, {1, 2, 4, 8, 16}},
+        {&ccmf_tuning::x_lines_per_block, {1, 2, 4, 8, 16}},
+        {&ccmf_tuning::branches, brs},
+        {&ccmf_tuning::radix_mode, {0, 1, 2}},
+        {&ccmf_tuning::zinv_pairs_per_block, {1, 2, 4, 8, 16}},
+        {&ccmf_tuning::line_engine, {0, 1}},
+    };
+    for (const Knob& k : knobs) {
+        if (rc != CCMF_OK) break;
+        const bool strided_only = k.field == &ccmf_tuning::y_lines_per_block ||
+                                  k.field == &ccmf_tuning::x_lines_per_block || k.field == &ccmf_tuning::line_engine;
+        if (strided_only && cur.plane_blocks != 0) continue;
+        for (int v : k.values) {
+            if (v == cur.*(k.field)) continue;
+            ccmf_tuning cand = cur;
+            cand.*(k.field) = v;
+            if (apply_tuning(plan, cand) != CCMF_OK) continue;
+            double ms = 0.0;
+            rc = measure(&ms);
+            if (rc != CCMF_OK) break;
+            if (ms < 0.99 * cur_ms) {
+                cur = plan->tune;
+                cur_ms = ms;
+            }
+        }
+        if (rc == CCMF_OK) rc = apply_tuning(plan, cur);
+    }
+    *best_ms = cur_ms;
+    return rc;
+}
+
 extern "C" {
 
 void ccmf_params_default(ccmf_params* p) {
@@ -1093,47 +1144,8 @@ int ccmf_plan_autotune(ccmf_plan* plan, const void* gamma, long long gamma_strid
         *ms = best_run;
         return CCMF_OK;
     };
-    ccmf_tuning cur = plan->tune;
     double cur_ms = 0.0;
-    int rc = measure(&cur_ms);
-    // coordinate descent over the knobs; a candidate must win by 1 % to be kept
-    struct Knob {
-        int ccmf_tuning::*field;
-        std::vector<int> values;
-    };
-    std::vector<int> brs;
-    for (int b = 1; b <= std::min(kMaxBranches, plan->batch); ++b) brs.push_back(b);
-    const Knob knobs[] = {
-        {&ccmf_tuning::update_variant, {0, 1, 2, 3, 4, 5, 6, 7}},
-        {&ccmf_tuning::plane_blocks, {0, 1, 2, 4, 8, 16}},
-        {&ccmf_tuning::z_pairs_per_block, {1, 2, 4, 8, 16}},
-        {&ccmf_tuning::y_lines_per_block, {1, 2, 4, 8, 16}},
-        {&ccmf_tuning::x_lines_per_block, {1, 2, 4, 8, 16}},
-        {&ccmf_tuning::branches, brs},
-        {&ccmf_tuning::radix_mode, {0, 1, 2}},
-        {&ccmf_tuning::zinv_pairs_per_block, {1, 2, 4, 8, 16}},
-        {&ccmf_tuning::line_engine, {0, 1}},
-    };
-    for (const Knob& k : knobs) {
-        if (rc != CCMF_OK) break;
-        const bool strided_only = k.field == &ccmf_tuning::y_lines_per_block ||
-                                  k.field == &ccmf_tuning::x_lines_per_block || k.field == &ccmf_tuning::line_engine;
-        if (strided_only && cur.plane_blocks != 0) continue;
-        for (int v : k.values) {
-            if (v == cur.*(k.field)) continue;
-            ccmf_tuning cand = cur;
-            cand.*(k.field) = v;
-            if (apply_tuning(plan, cand) != CCMF_OK) continue;
-            double ms = 0.0;
-            rc = measure(&ms);
-            if (rc != CCMF_OK) break;
-            if (ms < 0.99 * cur_ms) {
-                cur = plan->tune;
-                cur_ms = ms;
-            }
-        }
-        if (rc == CCMF_OK) rc = apply_tuning(plan, cur);
-    }
+    const int rc = tune_descent(plan, measure, &cur_ms);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != CCMF_OK) return rc;
@@ -1390,6 +1402,97 @@ int batch_solve_impl(ccmf_batch* bt, const void* const* gammas, const double* xi
     return CCMF_OK;
 }
 
+
+// Times `iters` iterations of bucket b's solves alone (a captured graph of its
+// branches, on the solves' current state), the faster of two runs.
+template <typename T>
+int batch_time_bucket(ccmf_batch* bt, int b, unsigned char* ws, bool aligned, int iters, cudaStream_t st,
+                      cudaEvent_t e0, cudaEvent_t e1, double* ms) {
+    ccmf_plan* pl = bt->plans[b];
+    unsigned char* wsb = ws + bt->ws_off[b];
+    LoopConfig cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.tol = 1e-4;
+    cfg.delta = 0.25;
+    cfg.bb_corr_min = 0.2;
+    cfg.rho_step_max = 2.0;
+    cfg.max_iter = 1 << 30;
+    cfg.fixed_iters = 1 << 30;   // the solves stay active for the timing
+    cfg.resume = 1;
+    Ctx<T> c = make_ctx<T>(pl, wsb, nullptr, 0, cfg);
+    c.p.gptrs = reinterpret_cast<const T* const*>(ws + bt->gp_off[b]);
+    c.vec_update = c.vec_div && aligned;
+    if (cudaMemsetAsync(wsb + pl->off_nact, 0, sizeof(int), st) != cudaSuccess) return CCMF_ERR_CUDA;
+    launch_init<T>(c, st);   // resume: re-activates the solves without touching their state
+    cudaGraph_t graph;
+    if (cudaStreamBeginCapture(bt->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CCMF_ERR_CUDA;
+    cudaEventRecord(bt->fork_event, bt->cap_stream);
+    const int nbr = pl->branches;
+    for (int r = 0; r < nbr; ++r) {
+        const int s0 = (int)((long long)pl->batch * r / nbr), s1 = (int)((long long)pl->batch * (r + 1) / nbr);
+        cudaStreamWaitEvent(pl->branch_stream[r], bt->fork_event, 0);
+        for (int it = 0; it < iters; ++it) launch_iteration_range<T>(c, s0, s1 - s0, pl->branch_stream[r]);
+        cudaEventRecord(bt->join_events[r], pl->branch_stream[r]);
+        cudaStreamWaitEvent(bt->cap_stream, bt->join_events[r], 0);
+    }
+    if (cudaStreamEndCapture(bt->cap_stream, &graph) != cudaSuccess) return CCMF_ERR_CUDA;
+    cudaGraphExec_t gx;
+    const cudaError_t ie = cudaGraphInstantiate(&gx, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return CCMF_ERR_CUDA;
+    int rc = CCMF_OK;
+    double best = 0.0;
+    for (int rep = 0; rep < 3 && rc == CCMF_OK; ++rep) {
+        if (cudaEventRecord(e0, st) != cudaSuccess || cudaGraphLaunch(gx, st) != cudaSuccess ||
+            cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = CCMF_ERR_CUDA;
+            break;
+        }
+        float f = 0.f;
+        if (cudaEventElapsedTime(&f, e0, e1) != cudaSuccess) rc = CCMF_ERR_CUDA;
+        const double t = (double)f / iters;
+        if (rep == 1 || (rep == 2 && t < best)) best = t;   // the first run warms up
+    }
+    cudaGraphExecDestroy(gx);
+    *ms = best;
+    return rc;
+}
+
+template <typename T>
+int batch_autotune_impl(ccmf_batch* bt, const void* const* gammas, const double* xi_host, unsigned char* ws,
+                        int iters, double* ms_out, cudaStream_t st) {
+    // the solves' state: a short fixed-iteration run of the whole batch
+    ccmf_params prm;
+    ccmf_params_default(&prm);
+    prm.fixed_iters = 2;
+    prm.check_every = 2;
+    prm.history_len = 0;
+    int rc = batch_solve_impl<T>(bt, gammas, xi_host, &prm, ws, nullptr, st);
+    if (rc != CCMF_OK) return rc;
+    bool aligned = true;
+    for (int s = 0; s < bt->count; ++s) aligned = aligned && ((uintptr_t)gammas[s] % 16) == 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return CCMF_ERR_CUDA;
+    }
+    for (int b = 0; b < (int)bt->plans.size() && rc == CCMF_OK; ++b) {
+        ccmf_plan* pl = bt->plans[b];
+        auto measure = [&](double* ms) { return batch_time_bucket<T>(bt, b, ws, aligned, iters, st, e0, e1, ms); };
+        double ms = 0.0;
+        rc = tune_descent(pl, measure, &ms);
+        if (rc == CCMF_OK) {
+            tuning_store(pl, pl->tune);
+            if (ms_out) ms_out[b] = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (bt->have_graph) cudaGraphExecDestroy(bt->gexec);   // the batch graph is captured again
+    bt->have_graph = false;
+    return rc;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1436,7 +1539,8 @@ int ccmf_batch_create(int count, const int* shapes, int precision, ccmf_batch** 
     }
     bt->total = off;
     int nev = 0;
-    for (ccmf_plan* pl : bt->plans) nev += pl->branches;
+    // join events for the largest branch count any tuning of the buckets may choose
+    for (ccmf_plan* pl : bt->plans) nev += std::min(kMaxBranches, pl->batch);
     if (rc == CCMF_OK && cudaStreamCreateWithFlags(&bt->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
         rc = CCMF_ERR_CUDA;
     if (rc == CCMF_OK && cudaEventCreateWithFlags(&bt->fork_event, cudaEventDisableTiming) != cudaSuccess)
@@ -1496,6 +1600,24 @@ int ccmf_batch_solve(ccmf_batch* batch, const void* const* gammas, const double*
     unsigned char* ws = reinterpret_cast<unsigned char*>(workspace);
     if (batch->prec == CCMF_FP64) return batch_solve_impl<double>(batch, gammas, xi_bar, &prm, ws, results, st);
     return batch_solve_impl<float>(batch, gammas, xi_bar, &prm, ws, results, st);
+}
+
+int ccmf_batch_autotune(ccmf_batch* batch, const void* const* gammas, const double* xi_bar, void* workspace,
+                        size_t workspace_bytes, int iters, double* ms, void* stream) {
+    if (!batch || !gammas || !xi_bar || iters < 1 || iters > 1000) return CCMF_ERR_INVALID_ARG;
+    for (int s = 0; s < batch->count; ++s) {
+        const double* x = xi_bar + 3 * s;
+        const double nn = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+        if (!isfinite(nn) || !(nn > 0.0)) return CCMF_ERR_INVALID_ARG;
+        if (!gammas[s] || !is_device_ptr(gammas[s])) return CCMF_ERR_INVALID_ARG;
+    }
+    if (!workspace || workspace_bytes < batch->total || ((uintptr_t)workspace & 255u) != 0)
+        return CCMF_ERR_WORKSPACE;
+    if (cudaSetDevice(batch->plans[0]->device) != cudaSuccess) return CCMF_ERR_CUDA;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    unsigned char* ws = reinterpret_cast<unsigned char*>(workspace);
+    if (batch->prec == CCMF_FP64) return batch_autotune_impl<double>(batch, gammas, xi_bar, ws, iters, ms, st);
+    return batch_autotune_impl<float>(batch, gammas, xi_bar, ws, iters, ms, st);
 }
 
 int ccmf_batch_buckets(const ccmf_batch* batch, int* buckets) {

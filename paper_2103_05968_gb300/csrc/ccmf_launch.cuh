@@ -5,6 +5,17 @@
 
 namespace ccmf {
 
+// Raise a kernel's dynamic shared memory limit to at least `bytes`. The limit is a
+// property of the kernel, shared by every plan in the process, so it is only ever
+// raised: a plan with smaller tiles must not lower what another plan's launches need.
+inline cudaError_t raise_smem_limit(const void* f, size_t bytes) {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, f);
+    if (e != cudaSuccess) return e;
+    if ((size_t)a.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 template <typename T>
 struct Ctx {
     Geom g;
@@ -99,8 +110,7 @@ int pipe_blocks_per_sm(int variant, size_t smem) {
     int nb = 0;
     cudaError_t err = cudaSuccess;
     CCMF_DISPATCH_PIPE(variant, {
-        err = cudaFuncSetAttribute((const void*)k_update_pipe<T, 0, ST, NTH>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        err = raise_smem_limit((const void*)k_update_pipe<T, 0, ST, NTH>, smem);
         if (err == cudaSuccess)
             err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_update_pipe<T, 0, ST, NTH>, NTH, smem);
     });
@@ -144,7 +154,7 @@ int lines_blocks_per_sm(int mode, int lines, size_t smem) {
     CCMF_DISPATCH_LINES(lines, {
         const void* f = mode == 0 ? (const void*)k_fft_lines<T, 0, LN>
                                   : mode == 1 ? (const void*)k_fft_lines<T, 1, LN> : (const void*)k_fft_lines<T, 2, LN>;
-        err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        err = raise_smem_limit(f, smem);
         if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kThreads, smem);
     });
     if (err != cudaSuccess) {
@@ -162,7 +172,7 @@ int wlines_blocks_per_sm(int mode, int n, size_t smem) {
     CCMF_DISPATCH_N(n, {
         const void* f = mode == 0 ? (const void*)k_fft_wlines<T, 0, NN>
                                   : mode == 1 ? (const void*)k_fft_wlines<T, 1, NN> : (const void*)k_fft_wlines<T, 2, NN>;
-        err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        err = raise_smem_limit(f, smem);
         if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kThreads, smem);
     });
     if (err != cudaSuccess) {
@@ -177,7 +187,7 @@ int wlines_blocks_per_sm(int mode, int n, size_t smem) {
 template <typename T, int CL>
 int plane_cluster_capacity_t(size_t smem) {
     const void* f = (const void*)k_fft_plane_cluster<T, CL>;
-    if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+    if (raise_smem_limit(f, smem) != cudaSuccess ||
         (CL > 8 && cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
         cudaGetLastError();
         return 0;
@@ -217,7 +227,7 @@ cudaError_t configure_kernels(const LaunchShape& sh) {
     cudaError_t err = cudaSuccess;
     auto set = [&](const void* f, size_t bytes) {
         if (err == cudaSuccess && bytes > 48 * 1024)
-            err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+            err = raise_smem_limit(f, bytes);
     };
     CCMF_DISPATCH_LINES(sh.pairs_per_block, {
         set((const void*)k_div_rfft_z<T, LN, true>, sh.smem_z);

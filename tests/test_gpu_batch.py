@@ -83,3 +83,24 @@ def test_batch_rejects_host_gamma():
     with pytest.raises(ccmf.CCMFError) as ei:
         batch.solve(host, normals[:2], ccmf.Params(fixed_iters=2))
     assert ei.value.code == ccmf.CCMF_ERR_INVALID_ARG
+
+
+def test_batch_autotune_keeps_parity():
+    """ccmf_batch_autotune tunes each shape group on its own solves; afterwards every solve
+    still matches the FP64 oracle at equal iterations (tuning changes only the launch)."""
+    fields = [M.random_two_phase((20, 12, 10), 0.3, 0.25, 1.0, 7), M.uniform_random((10, 10, 10), 0.5, 1.5, 8)]
+    plan = [(0, [1, 0, 0]), (1, [0.36, 0.48, 0.8]), (0, [0, 0, 1]), (1, [0, 1, 0]), (0, [0.6, 0.0, 0.8])]
+    dev = [torch.from_numpy(f).to(DEV) for f in fields]
+    gammas = [dev[f] for f, _ in plan]
+    normals = np.array([n for _, n in plan], dtype=np.float64)
+    batch = ccmf.Batch([fields[f].shape for f, _ in plan], precision=ccmf.CCMF_FP64, device=DEV)
+    ms = batch.autotune(gammas, normals, iters=3)
+    assert len(ms) == batch.buckets() == 2 and min(ms) > 0
+    res = batch.solve(gammas, normals, ccmf.Params(fixed_iters=25))
+    for s, (f, n) in enumerate(plan):
+        ref = O.solve(fields[f], n, O.Params(fixed_iters=25), record_history=False)
+        assert res[s]["status"] == 0 and res[s]["iters"] == 25
+        assert abs(res[s]["gamma_eff"] - ref.gamma_eff) <= 1e-10 * abs(ref.gamma_eff)
+    code, text = ccmf.ccmf_tuning_export()
+    assert code == ccmf.CCMF_OK and "ccmf-tuning 20 12 10 3 0 " in text and "ccmf-tuning 10 10 10 2 0 " in text
+    batch.close()

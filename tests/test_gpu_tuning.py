@@ -113,3 +113,18 @@ def test_fp64_line_passes_against_oracle(shape, engine):
     np.testing.assert_allclose(v[0].cpu().numpy(), ref.v, rtol=0, atol=1e-9)
     np.testing.assert_allclose(cut[0].cpu().numpy(), ref.cut, rtol=0, atol=1e-9)
     plan.close()
+
+
+def test_plans_of_different_sizes_coexist():
+    """A kernel's dynamic shared memory limit is shared by every plan in the process: a plan
+    with smaller tiles created after a larger one must not break the larger plan's launches
+    (128^2 planes need 132 KB per block in FP32, 96^2 planes 74 KB)."""
+    big = ccmf.Plan((128, 128, 8), batch=1, precision=ccmf.CCMF_FP32_MIXED, device=DEV)
+    small = ccmf.Plan((96, 96, 8), batch=1, precision=ccmf.CCMF_FP32_MIXED, device=DEV)
+    assert big.launch_info()["plane_blocks"] == 1 and small.launch_info()["plane_blocks"] == 1
+    for plan, shape in ((big, (128, 128, 8)), (small, (96, 96, 8)), (big, (128, 128, 8))):
+        g = torch.from_numpy(M.random_two_phase(shape, 0.3, 0.25, 1.0, 5).astype(np.float32)).to(DEV)
+        res, _, _ = plan.solve(g, [[0, 0, 1]], ccmf.Params(fixed_iters=5))
+        assert res[0]["status"] == 0 and np.isfinite(res[0]["gamma_eff"])
+    big.close()
+    small.close()

@@ -335,19 +335,19 @@ int shape_for(const ccmf_plan* pl, const ccmf_tuning& t, LaunchShape* out, ccmf_
     // (line_engine 1), else in-place radix stages over tiles of lines
     int le = r.line_engine;
     if (le < 0) {
-        // block stages by default: on GB300 the warp-per-line passes measured no faster
-        // at 512^2 planes (y passes level, x pass slower); the autotuner tries both
+        // warp per line by default (GB300, 512^2 planes: y passes 0.29 ms against 0.37 ms
+        // for the block stages, x pass 0.62 against 0.64 ms); the autotuner tries both
         const char* env = getenv("CCMF_LINE_ENGINE");
-        le = env ? atoi(env) : 0;
-        if (le < 0 || le > 1) le = 0;
+        le = env ? atoi(env) : 1;
+        if (le < 0 || le > 1) le = 1;
     }
     if (le > 1) return CCMF_ERR_UNSUPPORTED_SIZE;
     r.line_engine = le;
     auto warp_len_ok = [](int n) { return n >= 128 && n <= 1024 && (n & (n - 1)) == 0; };
     sh.wl_y = sh.wl_x = 0;
     if (!sh.plane_fused && le == 1) {
-        const size_t swy = ((size_t)n2 + 2 * 8 * (size_t)n2) * cs;
-        const size_t swx = ((size_t)n1 + 2 * 8 * (size_t)(n1 + 1)) * cs;
+        const size_t swy = ((size_t)n2 + 2 * 8 * (size_t)(n2 + n2 / 16)) * cs;
+        const size_t swx = ((size_t)n1 + 2 * 8 * (size_t)(n1 + n1 / 16 + 1)) * cs;
         if (warp_len_ok(n2) && swy <= kSmemMax) {
             sh.wl_y = n2;
             sh.smem_wy = swy;

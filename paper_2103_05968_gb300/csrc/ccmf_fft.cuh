@@ -261,15 +261,20 @@ __device__ void inplace_fft(C* buf, const AxisPlan& ap, int nlines, int es, int 
     }
 }
 
+// Padded position of element i of a warp-FFT line in shared memory: one pad slot
+// every 16 elements, so that the stride-R stores of the early Stockham passes fall
+// into distinct banks (2 wavefronts per warp access instead of up to 16).
+__device__ __forceinline__ int wpad(int i) { return i + (i >> 4); }
+
 // Warp-local Stockham FFT of one line of compile-time length N (a power of two,
-// 64 <= N <= 1024) held in shared memory at x[m * es]: the 32 lanes of one warp
+// 64 <= N <= 1024) held in shared memory at x[wpad(m)]: the 32 lanes of one warp
 // run the radix-8 / 4 / 2 passes (Ns = 1, R, R R', ...) alone, with __syncwarp
 // between the load and store halves of each pass, so no block barrier is needed.
 // Each lane keeps its butterflies' inputs in registers for the store half, which
 // makes the autosort pass safe in place. Forward kernel exp(-2 pi i / N);
 // natural-order input and output. tw[t] = W_N^t, t < N.
 template <typename C, int N, int NS>
-__device__ __forceinline__ void warp_stockham(C* x, int es, const C* __restrict__ tw, int lane) {
+__device__ __forceinline__ void warp_stockham(C* x, const C* __restrict__ tw, int lane) {
     if constexpr (NS < N) {
         constexpr int REM = N / NS;
         // the largest radix that still gives every lane a butterfly
@@ -283,7 +288,7 @@ __device__ __forceinline__ void warp_stockham(C* x, int es, const C* __restrict_
             const int j = lane + 32 * b;
             if (NB % 32 == 0 || j < NB) {
 #pragma unroll
-                for (int r = 0; r < R; ++r) v[b][r] = x[(j + r * NB) * es];
+                for (int r = 0; r < R; ++r) v[b][r] = x[wpad(j + r * NB)];
             }
         }
         __syncwarp();
@@ -299,18 +304,18 @@ __device__ __forceinline__ void warp_stockham(C* x, int es, const C* __restrict_
                 Dft<C, R>::run(v[b]);
                 const int od = (j - jm) * R + jm;
 #pragma unroll
-                for (int r = 0; r < R; ++r) x[(od + r * NS) * es] = v[b][r];
+                for (int r = 0; r < R; ++r) x[wpad(od + r * NS)] = v[b][r];
             }
         }
         __syncwarp();
-        warp_stockham<C, N, NS * R>(x, es, tw, lane);
+        warp_stockham<C, N, NS * R>(x, tw, lane);
     }
 }
 
 template <typename C, int N>
-__device__ __forceinline__ void warp_fft(C* x, int es, const C* __restrict__ tw, int lane) {
+__device__ __forceinline__ void warp_fft(C* x, const C* __restrict__ tw, int lane) {
     static_assert(N >= 64 && N <= 1024 && (N & (N - 1)) == 0, "warp FFT length");
-    warp_stockham<C, N, 1>(x, es, tw, lane);
+    warp_stockham<C, N, 1>(x, tw, lane);
 }
 
 }  // namespace ccmf

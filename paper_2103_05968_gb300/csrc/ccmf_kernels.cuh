@@ -542,7 +542,7 @@ __global__ void __launch_bounds__(kThreads) k_fft_wlines(Geom g, Ptrs<T> p, cons
                                                          const T* __restrict__ sym3, T inv_n) {
     using C = cx<T>;
     constexpr int L = kThreads / 32;              // lines per tile, one per warp
-    constexpr int LS = N + (MODE == 1 ? 1 : 0);   // line stride in shared memory
+    constexpr int LS = N + N / 16 + (MODE == 1 ? 1 : 0);   // padded line (wpad), odd stride for MODE 1
     const int s = blockIdx.y + p.s0;
     if (!p.run_all && !p.sc[s].active) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -567,18 +567,18 @@ __global__ void __launch_bounds__(kThreads) k_fft_wlines(Geom g, Ptrs<T> p, cons
                 const int kz = (int)fdiv((unsigned)l, g.div_n2);
                 const int k2 = (int)(l - (long long)kz * g.n2);
                 const C* src = spec + (long long)kz * plane + k2;
-                for (int m = m0; m < N; m += mstep) cp_async_cx(&b[cl * LS + m], src + (long long)m * g.n2);
+                for (int m = m0; m < N; m += mstep) cp_async_cx(&b[cl * LS + wpad(m)], src + (long long)m * g.n2);
             } else {
-                for (int m = m0; m < N; m += mstep) b[cl * LS + m] = cmake<C>(T(0), T(0));
+                for (int m = m0; m < N; m += mstep) b[cl * LS + wpad(m)] = cmake<C>(T(0), T(0));
             }
         } else {
             for (int idx = threadIdx.x; idx < L * N; idx += kThreads) {
                 const int c = idx / N, m = idx % N;
                 const long long l = l0 + c;
                 if (l < nlines)
-                    cp_async_cx(&b[c * LS + m], spec + l * N + m);
+                    cp_async_cx(&b[c * LS + wpad(m)], spec + l * N + m);
                 else
-                    b[c * LS + m] = cmake<C>(T(0), T(0));
+                    b[c * LS + wpad(m)] = cmake<C>(T(0), T(0));
             }
         }
         cp_async_commit();
@@ -597,7 +597,7 @@ __global__ void __launch_bounds__(kThreads) k_fft_wlines(Geom g, Ptrs<T> p, cons
         C* b = buf[cur];
         const long long l0 = t * L;
         C* x = b + warp * LS;
-        warp_fft<C, N>(x, 1, twl, lane);
+        warp_fft<C, N>(x, twl, lane);
         if (MODE == 1) {
             const long long l = l0 + warp;
             const bool valid = l < nlines;
@@ -610,11 +610,11 @@ __global__ void __launch_bounds__(kThreads) k_fft_wlines(Geom g, Ptrs<T> p, cons
             for (int m = lane; m < N; m += 32) {
                 const T lam = xsym[m] + lam23;
                 const T gk = (valid && lam > T(0)) ? -inv_n / lam : T(0);
-                const C z = x[m];
-                x[m] = cmake<C>(z.x * gk, -z.y * gk);   // conj: the inverse runs as conj(FFT(conj(.)))
+                const C z = x[wpad(m)];
+                x[wpad(m)] = cmake<C>(z.x * gk, -z.y * gk);   // conj: the inverse runs as conj(FFT(conj(.)))
             }
             __syncwarp();
-            warp_fft<C, N>(x, 1, twl, lane);
+            warp_fft<C, N>(x, twl, lane);
         }
         __syncthreads();
         if (MODE == 1) {
@@ -623,14 +623,14 @@ __global__ void __launch_bounds__(kThreads) k_fft_wlines(Geom g, Ptrs<T> p, cons
                 const int kz = (int)fdiv((unsigned)l, g.div_n2);
                 const int k2 = (int)(l - (long long)kz * g.n2);
                 C* dst = spec + (long long)kz * plane + k2;
-                for (int m = m0; m < N; m += mstep) dst[(long long)m * g.n2] = b[cl * LS + m];
+                for (int m = m0; m < N; m += mstep) dst[(long long)m * g.n2] = b[cl * LS + wpad(m)];
             }
         } else {
             for (int idx = threadIdx.x; idx < L * N; idx += kThreads) {
                 const int c = idx / N, m = idx % N;
                 const long long l = l0 + c;
                 if (l < nlines) {
-                    const C v = b[c * LS + m];
+                    const C v = b[c * LS + wpad(m)];
                     spec[l * N + m] = (MODE == 2) ? cconj(v) : v;
                 }
             }

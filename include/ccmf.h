@@ -205,6 +205,9 @@ typedef struct {
     int zinv_pairs_per_block; /* inverse z pass: line pairs per block, power of two 1..16 */
     int line_engine;        /* strided y / x passes: 0 in-place radix stages per block (any length),
                                1 one warp per line for power-of-two lengths 128..1024 */
+    int z_engine;           /* z passes: 0 Stockham stages over tiles of line pairs (any N3);
+                               one warp per line pair for power-of-two N3 128..1024 in the
+                               inverse pass (1) or in both passes (2) */
 } ccmf_tuning;
 
 /* The plan's current knob values (every entry resolved, none negative). */
@@ -236,7 +239,7 @@ int ccmf_plan_autotune(ccmf_plan* plan, const void* gamma, long long gamma_strid
 
 /*
  * The tuning table as text, one line per key
- * ("ccmf-tuning N1 N2 N3 batch precision sms : 9 knob values"). Writes at most
+ * ("ccmf-tuning N1 N2 N3 batch precision sms : 10 knob values"). Writes at most
  * capacity bytes (NUL-terminated) and the full length in *length.
  */
 int ccmf_tuning_export(char* text, size_t capacity, size_t* length);

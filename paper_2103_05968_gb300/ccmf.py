@@ -79,6 +79,7 @@ class ccmf_tuning(ctypes.Structure):
         ("radix_mode", ctypes.c_int),
         ("zinv_pairs_per_block", ctypes.c_int),
         ("line_engine", ctypes.c_int),
+        ("z_engine", ctypes.c_int),
     ]
 
 

@@ -188,6 +188,7 @@ void tuning_auto(ccmf_tuning* t) {
     t->radix_mode = 0;
     t->zinv_pairs_per_block = -1;
     t->line_engine = -1;
+    t->z_engine = -1;
 }
 
 bool pow2_in(int x, int lo, int hi) { return x >= lo && x <= hi && (x & (x - 1)) == 0; }
@@ -355,6 +356,31 @@ int shape_for(const ccmf_plan* pl, const ccmf_tuning& t, LaunchShape* out, ccmf_
         if (warp_len_ok(n1) && swx <= kSmemMax) {
             sh.wl_x = n1;
             sh.smem_wx = swx;
+        }
+    }
+    // z passes: one warp per line pair for power-of-two N3 128 ... 1024: z_engine 1 the
+    // inverse pass only, 2 both passes (the divergence pass's stencil loads favour the
+    // block tiles on GB300)
+    int ze = r.z_engine;
+    if (ze < 0) {
+        const char* env = getenv("CCMF_Z_ENGINE");
+        ze = env ? atoi(env) : 1;
+        if (ze < 0 || ze > 1) ze = 1;
+    }
+    if (ze > 2) return CCMF_ERR_UNSUPPORTED_SIZE;
+    r.z_engine = ze;
+    sh.wz = sh.wzd = 0;
+    if (ze >= 1 && warp_len_ok(n3)) {
+        const size_t lsz = (size_t)n3 + n3 / 16 + 1;
+        const size_t sd = ((size_t)n3 + 8 * lsz) * cs;
+        const size_t si = ((size_t)n3 + 8 * lsz + (size_t)(n3 / 2 + 1) * 17) * cs;
+        if (si <= kSmemMax) {
+            sh.wz = n3;
+            sh.smem_wzi = si;
+        }
+        if (ze == 2 && sd <= kSmemMax) {
+            sh.wzd = n3;
+            sh.smem_wzd = sd;
         }
     }
     if (!sh.plane_fused) {
@@ -743,6 +769,7 @@ int tune_descent(ccmf_plan* plan, const std::function<int(double*)>& measure, do
         {&ccmf_tuning::radix_mode, {0, 1, 2}},
         {&ccmf_tuning::zinv_pairs_per_block, {1, 2, 4, 8, 16}},
         {&ccmf_tuning::line_engine, {0, 1}},
+        {&ccmf_tuning::z_engine, {0, 1, 2}},
     };
     for (const Knob& k : knobs) {
         if (rc != CCMF_OK) break;
@@ -1164,10 +1191,10 @@ int ccmf_tuning_export(char* text, size_t capacity, size_t* length) {
         for (const auto& kv : g_tune_table) {
             const TuneKey& k = kv.first;
             const ccmf_tuning& t = kv.second;
-            snprintf(line, sizeof(line), "ccmf-tuning %d %d %d %d %d %d : %d %d %d %d %d %d %d %d %d\n", k.n1,
+            snprintf(line, sizeof(line), "ccmf-tuning %d %d %d %d %d %d : %d %d %d %d %d %d %d %d %d %d\n", k.n1,
                      k.n2, k.n3, k.batch, k.prec, k.sms, t.update_variant, t.plane_blocks, t.z_pairs_per_block,
                      t.y_lines_per_block, t.x_lines_per_block, t.branches, t.radix_mode, t.zinv_pairs_per_block,
-                     t.line_engine);
+                     t.line_engine, t.z_engine);
             out += line;
         }
     }
@@ -1193,10 +1220,10 @@ int ccmf_tuning_import(const char* text) {
         TuneKey k;
         ccmf_tuning t;
         memset(&t, 0, sizeof(t));
-        if (sscanf(line.c_str(), "ccmf-tuning %d %d %d %d %d %d : %d %d %d %d %d %d %d %d %d", &k.n1, &k.n2,
+        if (sscanf(line.c_str(), "ccmf-tuning %d %d %d %d %d %d : %d %d %d %d %d %d %d %d %d %d", &k.n1, &k.n2,
                    &k.n3, &k.batch, &k.prec, &k.sms, &t.update_variant, &t.plane_blocks, &t.z_pairs_per_block,
                    &t.y_lines_per_block, &t.x_lines_per_block, &t.branches, &t.radix_mode,
-                   &t.zinv_pairs_per_block, &t.line_engine) != 15)
+                   &t.zinv_pairs_per_block, &t.line_engine, &t.z_engine) != 16)
             return CCMF_ERR_INVALID_ARG;
         rows.emplace_back(k, t);
     }

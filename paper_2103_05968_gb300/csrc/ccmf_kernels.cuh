@@ -819,6 +819,168 @@ __global__ void __launch_bounds__(kPlaneClusterThreads, 1)
 }
 
 // ---------------------------------------------------------------------------
+// Passes 1 and 5 for power-of-two N3 (128 ... 1024): one warp per packed complex
+// z line (two real lines), 8 warps = 16 real lines per block, with the
+// warp-local Stockham FFT on padded lines (wpad). The spectrum is read and
+// written by the whole block, 16 consecutive lines (128 contiguous bytes in FP32)
+// per k_z row, instead of a few lines per block. The divergence pass needs
+// N3 % 4 == 0 (FP32) / N3 % 2 == 0 (FP64) 16-byte groups, which power-of-two N3 >= 128 has.
+// ---------------------------------------------------------------------------
+template <typename T, int N>
+__global__ void __launch_bounds__(kThreads) k_div_rfft_wz(Geom g, Ptrs<T> p, const cx<T>* __restrict__ tw) {
+    using C = cx<T>;
+    constexpr int NW = kThreads / 32;     // packed lines per block
+    constexpr int RL = 2 * NW;            // real lines per block
+    constexpr int NH = N / 2 + 1;
+    constexpr int LS = N + N / 16 + 1;    // padded line, odd stride between lines
+    const int s = blockIdx.y + p.s0;
+    if (!p.run_all && !p.sc[s].active) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* twl = reinterpret_cast<C*>(smem_raw);
+    C* lines = twl + N;
+    for (int t = threadIdx.x; t < N; t += kThreads) twl[t] = tw[t];
+    const T irho = T(1) / (T)p.sc[s].rho;
+    const T h = T(0.70710678118654752440084436210485);
+    const long long Nv = g.N;
+    const long long cur = (long long)(p.sc[s].iters & 1) * p.sstride + (long long)s * 6 * Nv;
+    const T* __restrict__ e = p.e + cur;
+    const T* __restrict__ v = p.v + cur;
+    const long long L = (long long)g.n1 * g.n2;
+    const long long l0 = (long long)blockIdx.x * RL;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    C* x = lines + w * LS;
+    // each lane takes groups of W consecutive z (16-byte loads), groups 32 W apart
+    constexpr int W = Vec16<T>::W;
+    constexpr int G = N / (32 * W);      // groups per lane
+    static_assert(G >= 1, "line too short for the warp z pass");
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const long long l = l0 + 2 * w + q;
+        const bool valid = l < L;
+        const RowNb rn = row_neighbours(g, (unsigned)(valid ? l : 0));
+#pragma unroll
+        for (int t = 0; t < G; ++t) {
+            const int k0 = W * lane + 32 * W * t;
+            T d[W];
+#pragma unroll
+            for (int u = 0; u < W; ++u) d[u] = T(0);
+            if (valid) {
+                const int kp = (k0 + W == N) ? 0 : k0 + W;   // first voxel after the group
+                const int km = (k0 == 0) ? N - 1 : k0 - 1;   // last voxel before the group
+                T wv[6][W], te[W], tv[W];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+                    Vec16<T>::ld(e + c * Nv + rn.row + k0, te);
+                    Vec16<T>::ld(v + c * Nv + rn.row + k0, tv);
+#pragma unroll
+                    for (int u = 0; u < W; ++u) wv[c][u] = te[u] - tv[u] * irho;
+                }
+                T xp[W], xm[W], yp[W], ym[W];
+                Vec16<T>::ld(e + 3 * Nv + rn.ip + k0, te);
+                Vec16<T>::ld(v + 3 * Nv + rn.ip + k0, tv);
+#pragma unroll
+                for (int u = 0; u < W; ++u) xp[u] = te[u] - tv[u] * irho;
+                Vec16<T>::ld(e + 0 * Nv + rn.im + k0, te);
+                Vec16<T>::ld(v + 0 * Nv + rn.im + k0, tv);
+#pragma unroll
+                for (int u = 0; u < W; ++u) xm[u] = te[u] - tv[u] * irho;
+                Vec16<T>::ld(e + 4 * Nv + rn.jp + k0, te);
+                Vec16<T>::ld(v + 4 * Nv + rn.jp + k0, tv);
+#pragma unroll
+                for (int u = 0; u < W; ++u) yp[u] = te[u] - tv[u] * irho;
+                Vec16<T>::ld(e + 1 * Nv + rn.jm + k0, te);
+                Vec16<T>::ld(v + 1 * Nv + rn.jm + k0, tv);
+#pragma unroll
+                for (int u = 0; u < W; ++u) ym[u] = te[u] - tv[u] * irho;
+                const T zp = __ldg(e + 5 * Nv + rn.row + kp) - __ldg(v + 5 * Nv + rn.row + kp) * irho;
+                const T zm = __ldg(e + 2 * Nv + rn.row + km) - __ldg(v + 2 * Nv + rn.row + km) * irho;
+#pragma unroll
+                for (int u = 0; u < W; ++u) {
+                    const T w2zp = (u + 1 < W) ? wv[5][(u + 1) % W] : zp;
+                    const T w1zm = (u > 0) ? wv[2][(u + W - 1) % W] : zm;
+                    const T sx = wv[0][u] - xm[u] + xp[u] - wv[3][u];
+                    const T sy = wv[1][u] - ym[u] + yp[u] - wv[4][u];
+                    const T sz = wv[2][u] - w1zm + w2zp - wv[5][u];
+                    d[u] = h * (sx + sy + sz);
+                }
+            }
+            // line 2w + q is the real (q = 0) or imaginary (q = 1) part of packed line w
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                T* xr = reinterpret_cast<T*>(&x[wpad(k0 + u)]);
+                xr[q] = d[u];
+            }
+        }
+    }
+    __syncwarp();
+    warp_fft<C, N>(x, twl, lane);
+    __syncthreads();
+    // half spectrum, k_z-major: line pair (2c, 2c + 1) from Z(k) and conj Z(N - k) of packed line c
+    C* spec = p.spec + (size_t)s * g.Nh;
+    for (int idx = threadIdx.x; idx < NH * RL; idx += kThreads) {
+        const int kz = idx / RL, t = idx % RL;
+        const long long l = l0 + t;
+        if (l >= L) continue;
+        const C* xc = lines + (t >> 1) * LS;
+        const C Z = xc[wpad(kz)];
+        const C Zm = cconj(xc[wpad(kz == 0 ? 0 : N - kz)]);
+        const C Sm = cadd(Z, Zm), D = csub(Z, Zm);
+        spec[(long long)kz * L + l] = (t & 1) ? cmake<C>(T(0.5) * D.y, T(-0.5) * D.x)
+                                              : cmake<C>(T(0.5) * Sm.x, T(0.5) * Sm.y);
+    }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(kThreads) k_irfft_wz(Geom g, Ptrs<T> p, const cx<T>* __restrict__ tw) {
+    using C = cx<T>;
+    constexpr int NW = kThreads / 32;
+    constexpr int RL = 2 * NW;
+    constexpr int RLP = RL + 1;           // padded slab row (consecutive k_z in distinct banks)
+    constexpr int NH = N / 2 + 1;
+    constexpr int LS = N + N / 16 + 1;
+    const int s = blockIdx.y + p.s0;
+    if (!p.run_all && !p.sc[s].active) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* twl = reinterpret_cast<C*>(smem_raw);
+    C* lines = twl + N;
+    C* raw = lines + NW * LS;             // [NH][RLP]
+    for (int t = threadIdx.x; t < N; t += kThreads) twl[t] = tw[t];
+    const long long L = (long long)g.n1 * g.n2;
+    const long long l0 = (long long)blockIdx.x * RL;
+    const C* spec = p.spec + (size_t)s * g.Nh;
+    for (int idx = threadIdx.x; idx < NH * RL; idx += kThreads) {
+        const int kz = idx / RL, t = idx % RL;
+        const long long l = l0 + t;
+        if (l < L)
+            cp_async_cx(&raw[kz * RLP + t], spec + (long long)kz * L + l);
+        else
+            raw[kz * RLP + t] = cmake<C>(T(0), T(0));
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    C* x = lines + w * LS;
+    for (int kz = lane; kz < NH; kz += 32) {
+        const C a = raw[kz * RLP + 2 * w], b = raw[kz * RLP + 2 * w + 1];
+        if (kz == 0 || 2 * kz == N) {
+            x[wpad(kz)] = cmake<C>(a.x, -b.x);               // Z = Re(a) + i Re(b), stored conjugated
+        } else {
+            x[wpad(kz)] = cmake<C>(a.x - b.y, -(a.y + b.x));   // conj(a + i b)
+            x[wpad(N - kz)] = cmake<C>(a.x + b.y, a.y - b.x);  // conj(conj(a) + i conj(b))
+        }
+    }
+    __syncwarp();
+    warp_fft<C, N>(x, twl, lane);
+    T* phi = p.phi + (size_t)s * g.N;
+    const long long la = l0 + 2 * w;
+    for (int m = lane; m < N; m += 32) {
+        const C z = x[wpad(m)];
+        if (la < L) phi[la * N + m] = z.x;
+        if (la + 1 < L) phi[(la + 1) * N + m] = -z.y;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Pass 5: complex-to-real inverse FFT along z, two real lines per transform.
 // ---------------------------------------------------------------------------
 template <typename T, int P>

@@ -234,6 +234,8 @@ cudaError_t configure_kernels(const LaunchShape& sh) {
         set((const void*)k_div_rfft_z<T, LN, false>, sh.smem_z);
     });
     CCMF_DISPATCH_LINES(sh.pairs_inv, { set((const void*)k_irfft_z<T, LN>, sh.smem_zi); });
+    if (sh.wz) { CCMF_DISPATCH_N(sh.wz, { set((const void*)k_irfft_wz<T, NN>, sh.smem_wzi); }); }
+    if (sh.wzd) { CCMF_DISPATCH_N(sh.wzd, { set((const void*)k_div_rfft_wz<T, NN>, sh.smem_wzd); }); }
     CCMF_DISPATCH_LINES(sh.lpb_y, {
         set((const void*)k_fft_lines<T, 0, LN>, sh.smem_y);
         set((const void*)k_fft_lines<T, 2, LN>, sh.smem_y);
@@ -300,12 +302,17 @@ void launch_passes(const Ctx<T>& c, const Ptrs<T>& p, cudaStream_t st, F&& betwe
     dim3 gwx((unsigned)twx, (unsigned)g.batch);
     dim3 gu((unsigned)sh.grid_update, (unsigned)g.batch);
     const T inv_n = (T)(1.0 / (double)g.N);
-    CCMF_DISPATCH_LINES(sh.pairs_per_block, {
-        if (c.vec_div)
-            k_div_rfft_z<T, LN, true><<<gz, kThreads, sh.smem_z, st>>>(g, p, c.ax[2], c.tw[2]);
-        else
-            k_div_rfft_z<T, LN, false><<<gz, kThreads, sh.smem_z, st>>>(g, p, c.ax[2], c.tw[2]);
-    });
+    const dim3 gwz((unsigned)ceil_div((long long)g.n1 * g.n2, 2 * (kThreads / 32)), (unsigned)g.batch);
+    if (sh.wzd && c.vec_div) {
+        CCMF_DISPATCH_N(sh.wzd, { k_div_rfft_wz<T, NN><<<gwz, kThreads, sh.smem_wzd, st>>>(g, p, c.tw[2]); });
+    } else {
+        CCMF_DISPATCH_LINES(sh.pairs_per_block, {
+            if (c.vec_div)
+                k_div_rfft_z<T, LN, true><<<gz, kThreads, sh.smem_z, st>>>(g, p, c.ax[2], c.tw[2]);
+            else
+                k_div_rfft_z<T, LN, false><<<gz, kThreads, sh.smem_z, st>>>(g, p, c.ax[2], c.tw[2]);
+        });
+    }
     between(kKDivRfftZ);
     if (sh.plane_fused && sh.plane_cluster > 1) {
         launch_plane_cluster<T>(g, p, c, inv_n, st);
@@ -356,8 +363,12 @@ void launch_passes(const Ctx<T>& c, const Ptrs<T>& p, cudaStream_t st, F&& betwe
         between(kKFftYInv);
     }
     const dim3 gzi((unsigned)ceil_div(pairs, sh.pairs_inv), (unsigned)g.batch);
-    CCMF_DISPATCH_LINES(sh.pairs_inv,
-                        { k_irfft_z<T, LN><<<gzi, kThreads, sh.smem_zi, st>>>(g, p, c.ax[2], c.tw[2]); });
+    if (sh.wz) {
+        CCMF_DISPATCH_N(sh.wz, { k_irfft_wz<T, NN><<<gwz, kThreads, sh.smem_wzi, st>>>(g, p, c.tw[2]); });
+    } else {
+        CCMF_DISPATCH_LINES(sh.pairs_inv,
+                            { k_irfft_z<T, LN><<<gzi, kThreads, sh.smem_zi, st>>>(g, p, c.ax[2], c.tw[2]); });
+    }
     between(kKIrfftZ);
     if (OUT && c.vec_update && vec_out_ok(p))
         k_update_vec<T, true><<<gu, kThreads, 0, st>>>(g, p, c.cfg);

@@ -99,6 +99,8 @@ struct LaunchShape {
     int grid_y, grid_x;       // persistent blocks per solve of the y / x line passes (0: one tile per block)
     int wl_y, wl_x;           // > 0: the y / x line passes run one warp per line (k_fft_wlines); the line length
     size_t smem_wy, smem_wx;  // their dynamic shared memory
+    int wz, wzd;              // > 0: the inverse / divergence z pass runs one warp per line pair; N3
+    size_t smem_wzd, smem_wzi;
     FastDiv div_r1, div_r2;   // rows (n1 / C) and columns (n2 / C) of one cluster block
 };
 

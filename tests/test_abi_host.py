@@ -94,7 +94,7 @@ def test_binding_fails_loudly_without_library(tmp_path):
 def test_tuning_table_text_roundtrip(lib):
     """The tuning table's text form is parsed back exactly; malformed text is rejected."""
     from paper_2103_05968_gb300 import ccmf
-    line = "ccmf-tuning 48 40 10 3 1 152 : 3 0 8 4 16 2 1 8 1"
+    line = "ccmf-tuning 48 40 10 3 1 152 : 3 0 8 4 16 2 1 8 1 0"
     assert ccmf.ccmf_tuning_import(line + "\n") == ccmf.CCMF_OK
     code, text = ccmf.ccmf_tuning_export()
     assert code == ccmf.CCMF_OK and line in text.splitlines()

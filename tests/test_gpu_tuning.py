@@ -128,3 +128,25 @@ def test_plans_of_different_sizes_coexist():
         assert res[0]["status"] == 0 and np.isfinite(res[0]["gamma_eff"])
     big.close()
     small.close()
+
+
+@pytest.mark.parametrize("shape", [(6, 5, 128), (3, 4, 256), (5, 3, 512)], ids=["n3_128", "n3_256", "n3_512"])
+@pytest.mark.parametrize("engine", [2, 1, 0], ids=["warp_both", "warp_inverse", "block_z"])
+def test_fp64_z_passes_against_oracle(shape, engine):
+    """Divergence + R2C and C2R along z with one warp per line pair (power-of-two N3, line
+    counts that leave a partial tile of 16 lines) or Stockham tiles: FP64 parity with the oracle."""
+    gamma = M.random_two_phase(shape, 0.3, 0.25, 1.0, 17)
+    normals = [[0.36, 0.48, 0.8], [0.0, 0.0, 1.0]]
+    plan = ccmf.Plan(shape, batch=2, precision=ccmf.CCMF_FP64, device=DEV)
+    plan.set_tuning(z_engine=engine)
+    assert plan.tuning()["z_engine"] == engine
+    res, flow, cut = plan.solve(torch.from_numpy(gamma).to(DEV), normals, ccmf.Params(fixed_iters=20),
+                                want_flow=True, want_cut=True)
+    e, v, rho, _ = plan.state()
+    for s, n in enumerate(normals):
+        ref = O.solve(gamma, n, O.Params(fixed_iters=20), record_history=False)
+        assert abs(res[s]["gamma_eff"] - ref.gamma_eff) <= 1e-10 * ref.gamma_eff
+        np.testing.assert_allclose(e[s].cpu().numpy(), ref.e, rtol=0, atol=1e-9)
+        np.testing.assert_allclose(v[s].cpu().numpy(), ref.v, rtol=0, atol=1e-9)
+        np.testing.assert_allclose(flow[s].cpu().numpy(), ref.flow, rtol=0, atol=1e-9)
+    plan.close()

@@ -363,9 +363,12 @@ int shape_for(const ccmf_plan* pl, const ccmf_tuning& t, LaunchShape* out, ccmf_
     // block tiles on GB300)
     int ze = r.z_engine;
     if (ze < 0) {
+        // measured on GB300: the warp divergence pass wins at N3 = 512 (1.30 against 1.41 ms
+        // per 512^3 pass) and loses at 128; the warp inverse pass wins at both
         const char* env = getenv("CCMF_Z_ENGINE");
-        ze = env ? atoi(env) : 1;
-        if (ze < 0 || ze > 1) ze = 1;
+        const int zdef = n3 >= 512 ? 2 : 1;
+        ze = env ? atoi(env) : zdef;
+        if (ze < 0 || ze > 2) ze = zdef;
     }
     if (ze > 2) return CCMF_ERR_UNSUPPORTED_SIZE;
     r.z_engine = ze;

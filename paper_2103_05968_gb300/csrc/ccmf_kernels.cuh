@@ -858,8 +858,8 @@ __global__ void __launch_bounds__(kThreads) k_div_rfft_wz(Geom g, Ptrs<T> p, con
         const long long l = l0 + 2 * w + q;
         const bool valid = l < L;
         const RowNb rn = row_neighbours(g, (unsigned)(valid ? l : 0));
-#pragma unroll
-        for (int t = 0; t < G; ++t) {
+#pragma unroll 1
+        for (int t = 0; t < G; ++t) {   // one group at a time keeps the registers low
             const int k0 = W * lane + 32 * W * t;
             T d[W];
 #pragma unroll

@@ -147,7 +147,9 @@ def bytes_per_voxel(kernel, esize, n3):
 
 def load_traffic(kernel, workload, precision):
     """DRAM bytes per launch of a kernel from the committed ncu summaries (profiles/*.md),
-    or None when no capture of this kernel, workload and precision is recorded."""
+    or None when no capture of this kernel, workload and precision is recorded. The
+    update pass is keyed with its variant (k_update@v<variant>), so a figure measured on
+    one variant is never reported for another."""
     import glob
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         for line in open(path):
@@ -514,8 +516,11 @@ def run_gpu(args, world, rank, local):
                 "gbs": bytes_per_voxel(k, esize, n3) * N * B / (ms / n * 1e-3) / 1e9}
             for k, (ms, n) in kt.items()}
     step_bytes = sum(bytes_per_voxel(k, esize, n3) for k in kt) * N * B
+    tuned = plan.tuning()
+    traffic_key = f"{dom}@v{tuned['update_variant']}" if dom == "k_update" else dom
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": load_traffic(dom, name, args.precision), "kernel": dom, "peak_kind": peak_kind,
+                "traffic": load_traffic(traffic_key, name, args.precision) if not args.grid else None,
+                "kernel": traffic_key, "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": per_launch_bytes,
                 "kernel_times_from": f"sequential event-timed pass of the same {K} steps "
                                      f"({t_seq_ms / K:.4f} ms/step)",

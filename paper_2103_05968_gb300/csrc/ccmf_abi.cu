@@ -14,6 +14,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/ccmf.h"
 #include "ccmf_launch.cuh"
 
@@ -167,6 +169,15 @@ struct ccmf_plan {
 namespace {
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? CCMF_OK : CCMF_ERR_CUDA; }
+
+// NVTX range over a scope (host-side enqueue of a call or phase; visible in nsys / ncu
+// --nvtx; header-only, no cost without a profiler attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 int device_sms() {
     int sms = 0, dev = 0;
@@ -604,7 +615,10 @@ int solve_impl(ccmf_plan* pl, const void* gamma_in, long long gstride_in, const 
     cfg.resume = prm->resume;
     Ctx<T> c = make_ctx<T>(pl, ws, gamma, gstride, cfg);
 
-    launch_init<T>(c, st);
+    {
+        NvtxRange r("ccmf init");
+        launch_init<T>(c, st);
+    }
     if (cudaGetLastError() != cudaSuccess) return CCMF_ERR_CUDA;
 
     const bool fixed = prm->fixed_iters > 0;
@@ -624,6 +638,7 @@ int solve_impl(ccmf_plan* pl, const void* gamma_in, long long gstride_in, const 
     if (rc != CCMF_OK) return rc;
     const long long nchunks_max = ((long long)total + chunk - 1) / chunk;
     pl->launches_last = 0;
+    NvtxRange r_loop("ccmf loop");
     for (long long ch = 0; ch < nchunks_max; ++ch) {
         if (cudaGraphLaunch(pl->gexec, st) != cudaSuccess) return CCMF_ERR_CUDA;
         int cls_tmp[kNumKernelClasses];
@@ -637,6 +652,7 @@ int solve_impl(ccmf_plan* pl, const void* gamma_in, long long gstride_in, const 
         }
     }
     // final evaluation of the state (cut, flow, primal and dual objectives)
+    NvtxRange r_final("ccmf final evaluation");
     const bool cut_host = cut && !is_device_ptr(cut);
     const bool flow_host = flow && !is_device_ptr(flow);
     T* cut_d = cut_host ? reinterpret_cast<T*>(ws + pl->off_cut) : reinterpret_cast<T*>(cut);
@@ -996,6 +1012,7 @@ int ccmf_plan_workspace_bytes(const ccmf_plan* plan, size_t* bytes) {
 int ccmf_solve(ccmf_plan* plan, const void* gamma, long long gamma_stride, const double* xi_bar,
                const ccmf_params* params, void* workspace, size_t workspace_bytes, void* flow, void* cut,
                ccmf_result* results, void* stream) {
+    NvtxRange nvtx_call("ccmf_solve");
     if (!plan || !gamma || !xi_bar || gamma_stride < 0) return CCMF_ERR_INVALID_ARG;
     ccmf_params prm;
     if (params)
@@ -1138,6 +1155,7 @@ int ccmf_plan_set_tuning(ccmf_plan* plan, const ccmf_tuning* tuning) {
 int ccmf_plan_autotune(ccmf_plan* plan, const void* gamma, long long gamma_stride, const double* xi_bar,
                        void* workspace, size_t workspace_bytes, int iters, ccmf_tuning* best, double* best_ms,
                        void* stream) {
+    NvtxRange nvtx_call("ccmf_plan_autotune");
     if (!plan || !gamma || !xi_bar || gamma_stride < 0 || iters < 1 || iters > 1000) return CCMF_ERR_INVALID_ARG;
     if (!workspace || workspace_bytes < plan->total) return CCMF_ERR_WORKSPACE;
     if (cudaSetDevice(plan->device) != cudaSuccess) return CCMF_ERR_CUDA;
@@ -1603,6 +1621,7 @@ int ccmf_batch_workspace_bytes(const ccmf_batch* batch, size_t* bytes) {
 
 int ccmf_batch_solve(ccmf_batch* batch, const void* const* gammas, const double* xi_bar, const ccmf_params* params,
                      void* workspace, size_t workspace_bytes, ccmf_result* results, void* stream) {
+    NvtxRange nvtx_call("ccmf_batch_solve");
     if (!batch || !gammas || !xi_bar) return CCMF_ERR_INVALID_ARG;
     ccmf_params prm;
     if (params)
@@ -1634,6 +1653,7 @@ int ccmf_batch_solve(ccmf_batch* batch, const void* const* gammas, const double*
 
 int ccmf_batch_autotune(ccmf_batch* batch, const void* const* gammas, const double* xi_bar, void* workspace,
                         size_t workspace_bytes, int iters, double* ms, void* stream) {
+    NvtxRange nvtx_call("ccmf_batch_autotune");
     if (!batch || !gammas || !xi_bar || iters < 1 || iters > 1000) return CCMF_ERR_INVALID_ARG;
     for (int s = 0; s < batch->count; ++s) {
         const double* x = xi_bar + 3 * s;
@@ -1841,6 +1861,7 @@ int ccmf_adjoint(ccmf_plan* plan, const void* gamma, long long gamma_stride, con
                  const ccmf_params* params, int K, int ckpt_every, const double* rho_schedule, void* workspace,
                  size_t workspace_bytes, void* adj_workspace, size_t adj_workspace_bytes, void* grad_gamma,
                  double* rho_out, ccmf_result* results, void* stream) {
+    NvtxRange nvtx_call("ccmf_adjoint");
     if (!plan || !gamma || !xi_bar || !grad_gamma || gamma_stride < 0 || K < 1 || ckpt_every < 1)
         return CCMF_ERR_INVALID_ARG;
     if (!rho_schedule && K > kHistCap) return CCMF_ERR_INVALID_ARG;

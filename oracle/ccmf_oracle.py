@@ -46,6 +46,10 @@ Readings where the paper is silent (each one is listed in the design notes):
      norm. Both estimates converge to the same value (strong duality, Sec. 2.1).
   R6 P_C keeps w when |w| <= gamma (the strict '>' branch); gamma = 0 maps to 0.
   R7 the zero frequency of (div^- grad^+)^+ is set to zero (pseudo-inverse).
+  R10 residual balancing (compared in Sec. 4.3 and its appendix, defined only by
+     reference to He et al.): primal residual r = |e^k - xi^{k+1/2}| (Eq. 31),
+     dual residual s = rho^k |e^{k+1} - e^k|; rho * s_max if r > 10 s, rho / s_max
+     if s > 10 r, else rho (s_max = rho_step_max).
 """
 
 from __future__ import annotations
@@ -58,6 +62,8 @@ import numpy as np
 RHO_BB = 0
 RHO_CONST = 1
 RHO_LTD = 2
+RHO_RB = 3
+RB_MU = 10.0   # residual balancing: ratio of the residuals that triggers a change (R10)
 
 _SQRT_HALF = 1.0 / math.sqrt(2.0)
 
@@ -209,8 +215,11 @@ def initial_rho(gamma, params):
     return gmin if gmin > 0.0 else float(np.mean(gamma))
 
 
-def next_rho(rho, rule, e_old, e_new, v_old, v_new, params):
-    """Penalty update after Eq. 30 (BB or LTD scaling), with the safeguard of R3."""
+def next_rho(rho, rule, e_old, e_new, v_old, v_new, params, primal_res=None):
+    """Penalty update after Eq. 30 (BB or LTD scaling), with the safeguard of R3; or residual
+    balancing (R10, the rule the paper compares in Sec. 4.3 and its appendix): primal residual
+    r = |e^k - xi^{k+1/2}| (Eq. 31), dual residual s = rho |e^{k+1} - e^k|; rho * tau if
+    r > mu s, rho / tau if s > mu r (mu = 10, tau = rho_step_max)."""
     if rule == RHO_CONST:
         return rho
     lo, hi = rho / params.rho_step_max, rho * params.rho_step_max
@@ -228,6 +237,14 @@ def next_rho(rho, rule, e_old, e_new, v_old, v_new, params):
         ne = l2_norm(e_new)
         if nv > 0.0 and ne > 0.0:
             return min(max(nv / ne, lo), hi)
+        return rho
+    if rule == RHO_RB:
+        r = float(primal_res)
+        s = rho * l2_norm(e_new - e_old)
+        if r > RB_MU * s:
+            return hi
+        if s > RB_MU * r:
+            return lo
         return rho
     raise ValueError("unknown rho rule")
 
@@ -268,7 +285,7 @@ def solve(gamma, xi_bar, params=None, e0=None, v0=None, rho0_state=None, record_
         mv = math.sqrt(sum(float(np.mean(v[c])) ** 2 for c in range(6)))
         if record_history:
             history.append((k, rho, r, mv, mincut_objective(xi_half, gamma), flow_objective(op_A_adj(v), xi_bar)))
-        rho_new = next_rho(rho, params.rho_rule, e, e_new, v, v_new, params)
+        rho_new = next_rho(rho, params.rho_rule, e, e_new, v, v_new, params, primal_res=r)
         e, v, rho = e_new, v_new, rho_new
         k += 1
         if params.fixed_iters <= 0 and k >= 2 and r <= params.tol * mv:

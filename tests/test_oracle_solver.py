@@ -156,13 +156,13 @@ def test_resume_is_bit_identical():
 
 
 def test_penalty_rules_agree():
-    """BB and LTD (text after Eq. 30) and the constant lower-bound penalty (Sec. 4.3)
-    approach the same optimum, inside the axis-normal bounds."""
+    """BB and LTD (text after Eq. 30), the constant lower-bound penalty (Sec. 4.3) and residual
+    balancing (Sec. 4.3 appendix) approach the same optimum, inside the axis-normal bounds."""
     g, _ = M.boolean_spheres((10, 10, 10), 2.0, 0.2, 0.3, 1.0, 12)
     lo = g.min(axis=2).mean()
     hi = g.mean(axis=(0, 1)).min()
     vals = []
-    for rule in (O.RHO_BB, O.RHO_LTD, O.RHO_CONST):
+    for rule in (O.RHO_BB, O.RHO_LTD, O.RHO_CONST, O.RHO_RB):
         r = O.solve(g, [0, 0, 1], O.Params(tol=1e-4, max_iter=3000, rho_rule=rule), record_history=False)
         assert lo - 1e-9 <= r.gamma_eff and r.gamma_primal <= hi + 1e-9
         vals.append(r.gamma_eff)
@@ -174,3 +174,21 @@ def test_strong_duality_at_convergence():
     r = O.solve(g, [0, 0, 1], O.Params(tol=1e-8, max_iter=50000))
     assert r.converged
     assert abs(r.gamma_primal - r.gamma_dual) < 1e-6
+
+
+def test_residual_balancing_direction():
+    """Residual balancing (He et al., the fourth strategy of the Sec. 4.3 study): a primal
+    residual more than 10x the dual residual rho |e^{k+1} - e^k| raises rho by the step
+    factor, a dual residual more than 10x the primal one lowers it, anything between keeps it.
+    Here |e^{k+1} - e^k| = 0.5 in every component (L2 norm over 6 components: sqrt(6 * 0.25))."""
+    shape = (2, 2, 2)
+    e_old = np.zeros((6,) + shape)
+    e_new = np.full((6,) + shape, 0.5)
+    v = np.zeros((6,) + shape)
+    p = O.Params(rho_step_max=2.0)
+    rho = 0.4
+    s = rho * np.sqrt(6 * 0.25)          # dual residual, 0.4899
+    assert O.next_rho(rho, O.RHO_RB, e_old, e_new, v, v, p, primal_res=11 * s) == 0.8
+    assert O.next_rho(rho, O.RHO_RB, e_old, e_new, v, v, p, primal_res=s / 11) == 0.2
+    assert O.next_rho(rho, O.RHO_RB, e_old, e_new, v, v, p, primal_res=s) == 0.4
+    assert O.next_rho(rho, O.RHO_RB, e_old, e_new, v, v, p, primal_res=9 * s) == 0.4

@@ -64,6 +64,9 @@ extern "C" {
 #define CCMF_RHO_BB 0     /* Barzilai-Borwein scaling with safeguard (default, Sec. 4.1) */
 #define CCMF_RHO_CONST 1  /* constant rho (Sec. 4.2, Sec. 4.3: the lower bound min gamma) */
 #define CCMF_RHO_LTD 2    /* Lorenz-Tran-Dinh scaling |v| / |e| */
+#define CCMF_RHO_RB 3     /* residual balancing (compared in Sec. 4.3): rho * s if the primal residual
+                             |e^k - xi^{k+1/2}| exceeds 10 x the dual residual rho |e^{k+1} - e^k|,
+                             rho / s in the opposite case, s = rho_step_max */
 
 typedef struct ccmf_plan ccmf_plan;
 
@@ -75,7 +78,7 @@ typedef struct {
     double bb_corr_min;  /* BB safeguard: minimum correlation <dv,de>/(|dv||de|); default 0.2 */
     double rho_step_max; /* BB/LTD safeguard: rho changes by at most this factor per iteration; default 2 */
     int max_iter;        /* upper bound on ADMM updates; default 20000 */
-    int rho_rule;        /* CCMF_RHO_BB (default), CCMF_RHO_CONST or CCMF_RHO_LTD */
+    int rho_rule;        /* CCMF_RHO_BB (default), CCMF_RHO_CONST, CCMF_RHO_LTD or CCMF_RHO_RB */
     int fixed_iters;     /* > 0: run exactly this many updates and ignore tol; default 0 */
     int check_every;     /* updates per device-side loop chunk between host checks; default 32 */
     int resume;          /* 1: start from the state already in the workspace instead of e^0, v^0 */

@@ -33,6 +33,7 @@ CCMF_FP32_MIXED = 1
 CCMF_RHO_BB = 0
 CCMF_RHO_CONST = 1
 CCMF_RHO_LTD = 2
+CCMF_RHO_RB = 3
 
 HIST_FIELDS = 6
 

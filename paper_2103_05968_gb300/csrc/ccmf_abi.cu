@@ -1028,7 +1028,7 @@ int ccmf_solve(ccmf_plan* plan, const void* gamma, long long gamma_stride, const
     if (prm.fixed_iters < 0 || prm.max_iter < 1 || prm.check_every < 1) return CCMF_ERR_INVALID_ARG;
     if (prm.fixed_iters == 0 && !(prm.tol > 0.0)) return CCMF_ERR_INVALID_ARG;
     if (!(prm.delta > 0.0 && prm.delta < 1.0)) return CCMF_ERR_INVALID_ARG;
-    if (prm.rho_rule < CCMF_RHO_BB || prm.rho_rule > CCMF_RHO_LTD) return CCMF_ERR_INVALID_ARG;
+    if (prm.rho_rule < CCMF_RHO_BB || prm.rho_rule > CCMF_RHO_RB) return CCMF_ERR_INVALID_ARG;
     if (!(prm.rho_step_max >= 1.0) || !isfinite(prm.rho0) || !isfinite(prm.bb_corr_min)) return CCMF_ERR_INVALID_ARG;
     if (prm.history_len < 0 || prm.history_len > kHistCap) return CCMF_ERR_INVALID_ARG;
     if (prm.resume != 0 && prm.resume != 1) return CCMF_ERR_INVALID_ARG;
@@ -1638,7 +1638,7 @@ int ccmf_batch_solve(ccmf_batch* batch, const void* const* gammas, const double*
     if (prm.fixed_iters < 0 || prm.max_iter < 1 || prm.check_every < 1) return CCMF_ERR_INVALID_ARG;
     if (prm.fixed_iters == 0 && !(prm.tol > 0.0)) return CCMF_ERR_INVALID_ARG;
     if (!(prm.delta > 0.0 && prm.delta < 1.0)) return CCMF_ERR_INVALID_ARG;
-    if (prm.rho_rule < CCMF_RHO_BB || prm.rho_rule > CCMF_RHO_LTD) return CCMF_ERR_INVALID_ARG;
+    if (prm.rho_rule < CCMF_RHO_BB || prm.rho_rule > CCMF_RHO_RB) return CCMF_ERR_INVALID_ARG;
     if (!(prm.rho_step_max >= 1.0) || !isfinite(prm.rho0) || !isfinite(prm.bb_corr_min)) return CCMF_ERR_INVALID_ARG;
     if (prm.history_len < 0 || prm.history_len > kHistCap) return CCMF_ERR_INVALID_ARG;
     if (prm.resume != 0) return CCMF_ERR_INVALID_ARG;
@@ -1870,7 +1870,7 @@ int ccmf_adjoint(ccmf_plan* plan, const void* gamma, long long gamma_stride, con
         prm = *params;
     else
         ccmf_params_default(&prm);
-    if (!(prm.delta > 0.0 && prm.delta < 1.0) || prm.rho_rule < CCMF_RHO_BB || prm.rho_rule > CCMF_RHO_LTD ||
+    if (!(prm.delta > 0.0 && prm.delta < 1.0) || prm.rho_rule < CCMF_RHO_BB || prm.rho_rule > CCMF_RHO_RB ||
         !(prm.rho_step_max >= 1.0))
         return CCMF_ERR_INVALID_ARG;
     for (int s = 0; s < plan->batch; ++s) {

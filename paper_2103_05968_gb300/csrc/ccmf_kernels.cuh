@@ -1219,6 +1219,13 @@ __device__ void update_epilogue(const Geom& g, const Ptrs<T>& p, const LoopConfi
     } else if (cfg.rho_rule == 2) {
         const double nv = sqrt(sums[kSumVV]), ne = sqrt(sums[kSumEE]);
         if (nv > 0.0 && ne > 0.0) rho_new = fmin(fmax(nv / ne, lo), hi);
+    } else if (cfg.rho_rule == 3) {
+        // residual balancing: primal residual r (Eq. 31) against rho |e^{k+1} - e^k|
+        const double sd = rho_d * sqrt(fmax(sums[kSumDeDe], 0.0) / Nd);
+        if (r > 10.0 * sd)
+            rho_new = hi;
+        else if (sd > 10.0 * r)
+            rho_new = lo;
     }
     const int done = kk + 1 - S.call_start;
     S.iters = kk + 1;

@@ -377,7 +377,7 @@ void launch_passes(const Ctx<T>& c, const Ptrs<T>& p, cudaStream_t st, F&& betwe
     else if (c.vec_update && sh.upd_variant >= 2) {
         const dim3 gp((unsigned)sh.grid_pipe, (unsigned)g.batch);
         CCMF_DISPATCH_PIPE(sh.upd_variant, {
-            if (c.cfg.rho_rule == 0)
+            if (c.cfg.rho_rule == 0 || c.cfg.rho_rule == 3)   // BB and residual balancing need |de|^2
                 k_update_pipe<T, 0, ST, NTH><<<gp, NTH, sh.smem_pipe, st>>>(g, p, c.cfg);
             else if (c.cfg.rho_rule == 2)
                 k_update_pipe<T, 2, ST, NTH><<<gp, NTH, sh.smem_pipe, st>>>(g, p, c.cfg);
@@ -386,7 +386,7 @@ void launch_passes(const Ctx<T>& c, const Ptrs<T>& p, cudaStream_t st, F&& betwe
         });
     } else if (c.vec_update && sh.upd_variant == 1 && sh.tma_rows > 0) {
         const dim3 gt((unsigned)sh.grid_tma, (unsigned)g.batch);
-        if (c.cfg.rho_rule == 0)
+        if (c.cfg.rho_rule == 0 || c.cfg.rho_rule == 3)   // BB and residual balancing need |de|^2
             k_update_tma<T, 0><<<gt, kThreads, sh.smem_tma, st>>>(g, p, c.cfg, sh.tma_rows);
         else if (c.cfg.rho_rule == 2)
             k_update_tma<T, 2><<<gt, kThreads, sh.smem_tma, st>>>(g, p, c.cfg, sh.tma_rows);

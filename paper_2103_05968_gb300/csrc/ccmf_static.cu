@@ -311,7 +311,7 @@ extern "C" int ccmf_solve_static(int n1, int n2, int n3, int precision, const vo
     if (prm.fixed_iters < 0 || prm.max_iter < 1 || prm.check_every < 1) return CCMF_ERR_INVALID_ARG;
     if (prm.fixed_iters == 0 && !(prm.tol > 0.0)) return CCMF_ERR_INVALID_ARG;
     if (!(prm.delta > 0.0 && prm.delta < 1.0)) return CCMF_ERR_INVALID_ARG;
-    if (prm.rho_rule < CCMF_RHO_BB || prm.rho_rule > CCMF_RHO_LTD) return CCMF_ERR_INVALID_ARG;
+    if (prm.rho_rule < CCMF_RHO_BB || prm.rho_rule > CCMF_RHO_RB) return CCMF_ERR_INVALID_ARG;
     if (!(prm.rho_step_max >= 1.0) || !isfinite(prm.rho0) || !isfinite(prm.bb_corr_min)) return CCMF_ERR_INVALID_ARG;
     if (prm.history_len < 0 || prm.history_len > kHistCap) return CCMF_ERR_INVALID_ARG;
     if (prm.resume != 0) return CCMF_ERR_INVALID_ARG;   // the scratch keeps no state between calls

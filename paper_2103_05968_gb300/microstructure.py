@@ -28,6 +28,7 @@ __all__ = [
     "laminate",
     "random_two_phase",
     "uniform_random",
+    "disks_2d",
     "config_single_sphere_32",
     "config_boolean_spheres_128",
     "config_short_fibres_512",
@@ -259,6 +260,43 @@ def uniform_random(n, lo, hi, seed, dtype=np.float64):
     rng = np.random.default_rng(seed)
     return rng.uniform(lo, hi, size=tuple(n)).astype(dtype)
 
+
+
+def disks_2d(n, count, area_fraction, gamma_disk, gamma_matrix, seed, max_attempts=2_000_000, dtype=np.float64):
+    """Two-dimensional periodic cell (n x n x 1) of `count` non-overlapping equal disks whose
+    total area is `area_fraction` of the cell, placed by random sequential addition.
+
+    Stands in for the paper's unidirectional fibre composite of Sec. 4.3 (128^2 voxels,
+    32 circular inclusions, 50 % filler, generated there by mechanical contraction, which is
+    not available here). The crack normal of interest lies in the plane.
+    Returns (gamma, centres).
+    """
+    radius = math.sqrt(area_fraction * n * n / (count * math.pi))
+    rng = np.random.default_rng(seed)
+    centres = np.zeros((0, 2))
+    attempts = 0
+    while len(centres) < count:
+        attempts += 1
+        if attempts > max_attempts:
+            raise RuntimeError("random sequential addition did not place all disks")
+        c = rng.random(2) * n
+        if len(centres):
+            d = np.abs(centres - c)
+            d = np.minimum(d, n - d)
+            if np.min(np.sum(d * d, axis=1)) < (2.0 * radius) ** 2:
+                continue
+        centres = np.vstack([centres, c])
+    x = np.arange(n) + 0.5
+    X, Y = np.meshgrid(x, x, indexing="ij")
+    inside = np.zeros((n, n), dtype=bool)
+    for cx, cy in centres:
+        dx = np.abs(X - cx)
+        dx = np.minimum(dx, n - dx)
+        dy = np.abs(Y - cy)
+        dy = np.minimum(dy, n - dy)
+        inside |= dx * dx + dy * dy < radius * radius
+    gamma = np.where(inside, gamma_disk, gamma_matrix).astype(dtype)[:, :, None]
+    return gamma, centres
 
 def config_single_sphere_32():
     """32^3 cell, gamma 1.0 matrix, one ball of radius 8 centred at (16, 16, 16) with gamma 0.1."""

@@ -83,7 +83,7 @@ def test_fp64_equal_iterations(name, build, normals, iters):
     assert_parity(out, refs)
 
 
-@pytest.mark.parametrize("rule", [ccmf.CCMF_RHO_CONST, ccmf.CCMF_RHO_LTD, ccmf.CCMF_RHO_BB])
+@pytest.mark.parametrize("rule", [ccmf.CCMF_RHO_CONST, ccmf.CCMF_RHO_LTD, ccmf.CCMF_RHO_BB, ccmf.CCMF_RHO_RB])
 def test_fp64_penalty_rules_and_damping(rule):
     # rho^0 below min(gamma): with rho^0 = min(gamma) the first update meets |z| = gamma exactly
     # at the weakest voxels, where rounding decides whether |e^1| is 0 or 1e-16, and the LTD

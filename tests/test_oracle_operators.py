@@ -9,6 +9,7 @@ import pytest
 
 from oracle import ccmf_oracle as O
 from oracle import dense_maxflow as D
+from paper_2103_05968_gb300 import microstructure as M
 
 SHAPES = [(4, 5, 6), (3, 1, 7), (8, 8, 8)]
 
@@ -113,3 +114,16 @@ def test_project_C():
         q = rng.standard_normal((6,) + shape)
         q *= (gamma * rng.random(shape) / np.sqrt(np.sum(q * q, axis=0)))[None]
         assert np.all(np.sum((z - p) ** 2, axis=0) <= np.sum((z - q) ** 2, axis=0) + 1e-12)
+
+
+def test_disk_composite_generator():
+    """The 2-D stand-in of the Sec. 4.3 composite: 32 disks, no two closer than a diameter
+    (periodic distance), voxel filler fraction within 1 % of the requested 50 %."""
+    g, c = M.disks_2d(128, 32, 0.5, 10.0, 1.0, seed=599)
+    assert g.shape == (128, 128, 1) and len(c) == 32
+    r = np.sqrt(0.5 * 128 * 128 / (32 * np.pi))
+    d = np.abs(c[:, None, :] - c[None, :, :])
+    d = np.minimum(d, 128 - d)
+    dist = np.sqrt((d ** 2).sum(-1))[np.triu_indices(32, 1)]
+    assert dist.min() >= 2 * r
+    assert abs(float((g > 1).mean()) - 0.5) < 0.01

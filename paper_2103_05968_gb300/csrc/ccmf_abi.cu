@@ -613,6 +613,12 @@ int solve_impl(ccmf_plan* pl, const void* gamma_in, long long gstride_in, const 
     cfg.rho_rule = prm->rho_rule;
     cfg.hist_len = prm->history_len;
     cfg.resume = prm->resume;
+    {
+        // debug only: a tiny budget for the bounded device waits makes them give up, to test
+        // the CCMF_ERR_TIMEOUT path; the waits for copies still in flight keep the full budget
+        const char* env = getenv("CCMF_DEBUG_SPIN_LIMIT");
+        cfg.spin_limit = env ? (unsigned)strtoul(env, nullptr, 10) + 1u : 0u;
+    }
     Ctx<T> c = make_ctx<T>(pl, ws, gamma, gstride, cfg);
 
     {

@@ -1497,8 +1497,9 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
 }
 
 // Bounded wait for the phase with the given parity; false if it gave up.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
-    for (unsigned spin = 0; spin < kSpinLimit; ++spin)
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity,
+                                                  unsigned limit = kSpinLimit) {
+    for (unsigned spin = 0; spin < limit; ++spin)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -1616,7 +1617,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_update_tma(Geom g, Ptrs<T> p, L
     for (int tile = t0; tile < ntiles; tile += tstep, ++it) {
         const int st = it & 1;
         const unsigned ph = st ? phase1 : phase0;
-        const bool ok = mbar_wait_bounded(&bars[st], ph);
+        const bool ok = mbar_wait_bounded(&bars[st], ph, cfg.spin_limit ? cfg.spin_limit - 1 : kSpinLimit);
         if (__syncthreads_or(!ok)) {
             failed = true;
             break;
@@ -1858,7 +1859,7 @@ __global__ void __launch_bounds__(NT) k_update_pipe(Geom g, Ptrs<T> p, LoopConfi
     for (int tile = t0; tile < ntiles; tile += tstep, ++it) {
         const int st = it % STAGES;
         const unsigned ph = (unsigned)(it / STAGES) & 1u;
-        const bool ok = mbar_wait_bounded(&bars[st], ph);
+        const bool ok = mbar_wait_bounded(&bars[st], ph, cfg.spin_limit ? cfg.spin_limit - 1 : kSpinLimit);
         if (__syncthreads_or(!ok)) {
             failed = true;
             break;

@@ -48,6 +48,9 @@ struct LoopConfig {
     int max_iter, fixed_iters, rho_rule, hist_len, resume;
     const double* rho_sched;  // replayed penalties rho^k = rho_sched[s * sched_len + k] (null: adaptive rule)
     int sched_len;
+    unsigned spin_limit;      // 0: the default budget of a bounded device wait; n > 0: n - 1 polls, only to
+                              // test the timeout path (CCMF_DEBUG_SPIN_LIMIT; each poll may itself block
+                              // for a while, so 0 polls is the budget that reliably gives up)
 };
 
 struct Geom {

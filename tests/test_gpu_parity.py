@@ -290,3 +290,22 @@ def test_kernel_timing_mode():
     plan.set_kernel_timing(False)
     res2, _, _ = plan.solve(g, [[0, 0, 1]], ccmf.Params(fixed_iters=10))
     assert res2[0]["gamma_eff"] == res[0]["gamma_eff"]
+
+
+@pytest.mark.parametrize("variant", [1, 3], ids=["tma_rows", "tma_pipe"])
+def test_device_wait_timeout_reported(variant, monkeypatch):
+    """A bounded device wait that gives up is reported, not hung or faulted: with a zero-poll
+    budget (debug setting) the TMA-staged update passes give up on their first tile, drain
+    their copies in flight with the full budget, and the solve returns CCMF_ERR_TIMEOUT.
+    The next solve on the same plan, with the normal budget, is healthy."""
+    gamma = M.random_two_phase((64, 64, 64), 0.3, 0.25, 1.0, 71).astype(np.float32)
+    plan = ccmf.Plan(gamma.shape, batch=1, precision=ccmf.CCMF_FP32_MIXED, device=DEV)
+    plan.set_tuning(update_variant=variant)
+    g = torch.from_numpy(gamma).to(DEV)
+    monkeypatch.setenv("CCMF_DEBUG_SPIN_LIMIT", "0")
+    res, _, _ = plan.solve(g, [[0, 0, 1]], ccmf.Params(fixed_iters=3))
+    assert res[0]["status"] == ccmf.CCMF_ERR_TIMEOUT
+    monkeypatch.delenv("CCMF_DEBUG_SPIN_LIMIT")
+    res, _, _ = plan.solve(g, [[0, 0, 1]], ccmf.Params(fixed_iters=3))
+    assert res[0]["status"] == 0 and res[0]["iters"] == 3 and np.isfinite(res[0]["gamma_eff"])
+    plan.close()

@@ -127,3 +127,16 @@ def test_disk_composite_generator():
     dist = np.sqrt((d ** 2).sum(-1))[np.triu_indices(32, 1)]
     assert dist.min() >= 2 * r
     assert abs(float((g > 1).mean()) - 0.5) < 0.01
+
+
+def test_boolean_and_fibre_generators():
+    """Generator statistics: the voxel volume fraction is reached and overshot by at most about
+    one added body (balls of the Boolean model, fibres of the random sequential addition)."""
+    g, nb = M.boolean_spheres((48, 48, 48), 4.0, 0.2, 0.3, 1.0, seed=7)
+    frac = float((g < 1.0).mean())
+    ball = 4.0 / 3.0 * np.pi * 4.0 ** 3 / 48 ** 3
+    assert 0.2 <= frac <= 0.2 + ball
+    gf, nf = M.short_fibres((64, 64, 64), 4.0, 8.0, 0.06, 3.0, 1.0, seed=5)
+    ff = float((gf > 1.0).mean())
+    cyl = np.pi * 2.0 ** 2 * 32.0 / 64 ** 3
+    assert nf > 0 and 0.06 <= ff <= 0.06 + 1.5 * cyl

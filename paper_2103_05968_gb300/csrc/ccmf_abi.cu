@@ -358,8 +358,9 @@ int shape_for(const ccmf_plan* pl, const ccmf_tuning& t, LaunchShape* out, ccmf_
     auto warp_len_ok = [](int n) { return n >= 128 && n <= 1024 && (n & (n - 1)) == 0; };
     sh.wl_y = sh.wl_x = 0;
     if (!sh.plane_fused && le == 1) {
-        const size_t swy = ((size_t)n2 + 2 * 8 * (size_t)(n2 + n2 / 16)) * cs;
-        const size_t swx = ((size_t)n1 + 2 * 8 * (size_t)(n1 + n1 / 16 + 1)) * cs;
+        // y: twiddles + one padded line per warp; x: twiddles + two tiles of 8 lines
+        const size_t swy = ((size_t)n2 + 8 * (size_t)(n2 + n2 / 16)) * cs;
+        const size_t swx = ((size_t)n1 + 2 * 8 * (size_t)(n1 + n1 / 16 + 2)) * cs;
         if (warp_len_ok(n2) && swy <= kSmemMax) {
             sh.wl_y = n2;
             sh.smem_wy = swy;

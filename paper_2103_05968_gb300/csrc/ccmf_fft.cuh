@@ -265,57 +265,173 @@ __device__ void inplace_fft(C* buf, const AxisPlan& ap, int nlines, int es, int 
 // every 16 elements, so that the stride-R stores of the early Stockham passes fall
 // into distinct banks (2 wavefronts per warp access instead of up to 16).
 __device__ __forceinline__ int wpad(int i) { return i + (i >> 4); }
+// The same for a compile-time multiple of 16: wpad(a + k) = wpad(a) + cpad(k) for a >= 0.
+__host__ __device__ constexpr int cpad(int k) { return k + k / 16; }
+
+// Radix of the warp Stockham pass that starts at sub-transform length NS: the largest
+// radix (8, 4, 2) that divides N / NS and still gives every lane a butterfly.
+template <int N, int NS>
+__host__ __device__ constexpr int warp_radix() {
+    return ((N / NS) % 8 == 0 && N / 8 >= 32) ? 8 : ((N / NS) % 4 == 0 && N / 4 >= 32) ? 4 : 2;
+}
+
+// Twiddle table of the warp FFT, per pass: the pass at NS > 1 owns (R - 1) NS
+// entries, entry (r - 1) NS + j = W_N^{j r N / (NS R)} for j < NS, 1 <= r < R, so
+// that a lane reads its R - 1 twiddles at fixed offsets from one address and
+// consecutive lanes read consecutive entries. At most N entries for N = 128 ... 1024.
+template <int N, int NS = 1>
+__host__ __device__ constexpr int warp_tw_count() {
+    if constexpr (NS >= N) {
+        return 0;
+    } else {
+        constexpr int R = warp_radix<N, NS>();
+        return (NS > 1 ? (R - 1) * NS : 0) + warp_tw_count<N, NS * R>();
+    }
+}
+
+// Fills the per-pass table from tw[t] = W_N^t (t < N); called by the whole block.
+template <typename C, int N, int NS = 1, int OFF = 0>
+__device__ __forceinline__ void warp_tw_fill(C* twl, const C* __restrict__ tw) {
+    if constexpr (NS < N) {
+        constexpr int R = warp_radix<N, NS>();
+        if constexpr (NS > 1) {
+            constexpr int TWS = N / (NS * R);
+            for (int q = threadIdx.x; q < (R - 1) * NS; q += blockDim.x) {
+                const int r = 1 + q / NS, j = q % NS;
+                twl[OFF + q] = tw[j * r * TWS];
+            }
+            warp_tw_fill<C, N, NS * R, OFF + (R - 1) * NS>(twl, tw);
+        } else {
+            warp_tw_fill<C, N, NS * R, OFF>(twl, tw);
+        }
+    }
+}
 
 // Warp-local Stockham FFT of one line of compile-time length N (a power of two,
-// 64 <= N <= 1024) held in shared memory at x[wpad(m)]: the 32 lanes of one warp
+// 128 <= N <= 1024) held in shared memory at x[wpad(m)]: the 32 lanes of one warp
 // run the radix-8 / 4 / 2 passes (Ns = 1, R, R R', ...) alone, with __syncwarp
 // between the load and store halves of each pass, so no block barrier is needed.
 // Each lane keeps its butterflies' inputs in registers for the store half, which
 // makes the autosort pass safe in place. Forward kernel exp(-2 pi i / N);
-// natural-order input and output. tw[t] = W_N^t, t < N.
-template <typename C, int N, int NS>
-__device__ __forceinline__ void warp_stockham(C* x, const C* __restrict__ tw, int lane) {
+// natural-order input and output; twl is the per-pass table of warp_tw_fill.
+//
+// Addressing: butterfly j = lane + 32 b of a pass reads elements j + r N/R and
+// writes od + r NS, od = (j - j mod NS) R + j mod NS. For the lengths used every
+// such padded position is a per-lane base plus a compile-time offset: the loads
+// from wpad(lane); the stores from wpad(lane R) (NS = 1), wpad(od of b = 0)
+// (1 < NS < 32, where j mod NS = lane mod NS and NS R >= 16 keeps the pad of
+// od + r NS separable) or wpad(lane) (NS >= 32). So every shared-memory access
+// of a pass is one instruction with an immediate offset.
+//
+// GIN: the first pass reads the line from gin (global memory, natural order,
+// unpadded; consecutive lanes read consecutive elements). GOUT: the last pass
+// (NS >= 32, outputs lane + const) writes it to gout, conjugated if CONJ. Both
+// skip a shared-memory round trip of the whole line.
+template <typename C, int N, int NS, int OFF, bool GIN = false, bool GOUT = false, bool CONJ = false>
+__device__ __forceinline__ void warp_stockham(C* x, const C* __restrict__ twl, int lane, const C* gin = nullptr,
+                                              C* gout = nullptr) {
     if constexpr (NS < N) {
-        constexpr int REM = N / NS;
-        // the largest radix that still gives every lane a butterfly
-        constexpr int R = (REM % 8 == 0 && N / 8 >= 32) ? 8 : (REM % 4 == 0 && N / 4 >= 32) ? 4 : 2;
+        constexpr int R = warp_radix<N, NS>();
         constexpr int NB = N / R;                 // butterflies of the pass
-        constexpr int PER = (NB + 31) / 32;       // butterflies per lane
-        constexpr int TWS = N / (NS * R);         // twiddle table step
+        constexpr int PER = NB / 32;              // butterflies per lane
+        constexpr bool FROM_G = GIN && NS == 1;
+        constexpr bool TO_G = GOUT && NS * R == N;
+        static_assert(NB % 32 == 0, "every lane takes whole butterflies");
+        static_assert(NS == 1 || NS >= 16 || NS * R >= 16, "separable store offsets");
+        static_assert(!TO_G || NS >= 32, "the last pass writes lane + const");
         C v[PER][R];
+        if constexpr (FROM_G) {
+            const C* gl = gin + lane;
 #pragma unroll
-        for (int b = 0; b < PER; ++b) {
-            const int j = lane + 32 * b;
-            if (NB % 32 == 0 || j < NB) {
+            for (int b = 0; b < PER; ++b) {
 #pragma unroll
-                for (int r = 0; r < R; ++r) v[b][r] = x[wpad(j + r * NB)];
+                for (int r = 0; r < R; ++r) v[b][r] = gl[32 * b + r * NB];
+            }
+            __syncwarp();   // the warp's previous line has been read out of x
+        } else {
+            const C* xl = x + wpad(lane);
+#pragma unroll
+            for (int b = 0; b < PER; ++b) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[b][r] = xl[cpad(32 * b + r * NB)];
+            }
+            __syncwarp();
+        }
+        if constexpr (NS > 1) {
+            // twiddles W_N^{jm r N/(NS R)} with jm = j mod NS
+            const C* tl = twl + OFF + (NS <= 32 ? (lane & (NS - 1)) : lane);
+#pragma unroll
+            for (int b = 0; b < PER; ++b) {
+                const int jb = (NS <= 32) ? 0 : ((32 * b) & (NS - 1));
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], tl[jb + (r - 1) * NS]);
             }
         }
-        __syncwarp();
 #pragma unroll
-        for (int b = 0; b < PER; ++b) {
-            const int j = lane + 32 * b;
-            if (NB % 32 == 0 || j < NB) {
-                const int jm = j & (NS - 1);
-                if constexpr (NS > 1) {
+        for (int b = 0; b < PER; ++b) Dft<C, R>::run(v[b]);
+        if constexpr (TO_G) {
+            C* gl = gout + lane;
 #pragma unroll
-                    for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], tw[jm * r * TWS]);
+            for (int b = 0; b < PER; ++b) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int kb = ((32 * b) & ~(NS - 1)) * R + ((32 * b) & (NS - 1));
+                    gl[kb + r * NS] = CONJ ? cmake<C>(v[b][r].x, -v[b][r].y) : v[b][r];
                 }
-                Dft<C, R>::run(v[b]);
-                const int od = (j - jm) * R + jm;
-#pragma unroll
-                for (int r = 0; r < R; ++r) x[wpad(od + r * NS)] = v[b][r];
             }
+        } else {
+            if constexpr (NS == 1) {
+                C* xs = x + wpad(lane * R);
+#pragma unroll
+                for (int b = 0; b < PER; ++b) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) xs[cpad(32 * b * R) + r] = v[b][r];
+                }
+            } else if constexpr (NS < 32) {
+                const int jm = lane & (NS - 1);
+                C* xs = x + wpad((lane - jm) * R + jm);
+#pragma unroll
+                for (int b = 0; b < PER; ++b) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        if constexpr (NS < 16)
+                            xs[cpad(32 * b * R) + r * NS + (r * NS) / 16] = v[b][r];
+                        else
+                            xs[cpad(32 * b * R) + cpad(r * NS)] = v[b][r];
+                    }
+                }
+            } else {
+                C* xs = x + wpad(lane);
+#pragma unroll
+                for (int b = 0; b < PER; ++b) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const int kb = ((32 * b) & ~(NS - 1)) * R + ((32 * b) & (NS - 1));
+                        xs[cpad(kb + r * NS)] = v[b][r];
+                    }
+                }
+            }
+            __syncwarp();
         }
-        __syncwarp();
-        warp_stockham<C, N, NS * R>(x, tw, lane);
+        warp_stockham<C, N, NS * R, (NS > 1 ? OFF + (R - 1) * NS : OFF), GIN, GOUT, CONJ>(x, twl, lane, gin, gout);
     }
 }
 
 template <typename C, int N>
-__device__ __forceinline__ void warp_fft(C* x, const C* __restrict__ tw, int lane) {
-    static_assert(N >= 64 && N <= 1024 && (N & (N - 1)) == 0, "warp FFT length");
-    warp_stockham<C, N, 1>(x, tw, lane);
+__device__ __forceinline__ void warp_fft(C* x, const C* __restrict__ twl, int lane) {
+    static_assert(N >= 128 && N <= 1024 && (N & (N - 1)) == 0, "warp FFT length");
+    static_assert(warp_tw_count<N>() <= N, "twiddle table fits N entries");
+    warp_stockham<C, N, 1, 0>(x, twl, lane);
+}
+
+// The same transform from global line gin to global line gout (conjugated if
+// CONJ; gin == gout allowed: the whole line is in registers or x in between),
+// with x as the warp's shared-memory scratch line.
+template <typename C, int N, bool CONJ>
+__device__ __forceinline__ void warp_fft_global(const C* gin, C* gout, C* x, const C* __restrict__ twl, int lane) {
+    static_assert(N >= 128 && N <= 1024 && (N & (N - 1)) == 0, "warp FFT length");
+    static_assert(warp_tw_count<N>() <= N, "twiddle table fits N entries");
+    warp_stockham<C, N, 1, 0, true, true, CONJ>(x, twl, lane, gin, gout);
 }
 
 }  // namespace ccmf

@@ -528,115 +528,129 @@ __global__ void __launch_bounds__(kThreads) k_fft_lines(Geom g, Ptrs<T> p, AxisP
 
 // ---------------------------------------------------------------------------
 // The same three line passes for power-of-two line lengths N (128 ... 1024), with
-// one warp per line: a tile is 8 lines, the warps transform their lines with the
-// warp-local Stockham FFT (natural order in and out, no block barrier between
-// radix passes). Loads and stores stay cooperative and coalesced (cp.async into
-// the second buffer while the first is transformed). x lines are padded to an odd
-// stride in shared memory so the strided loads do not conflict. MODE 1 reads the
-// x symbol in natural order and the y symbol in the order the y pass left
-// (ysym: natural after this kernel's MODE 0, digit-reversed after k_fft_lines).
+// one warp per line and the warp-local Stockham FFT (natural order in and out, no
+// block barrier between radix passes).
+// MODE 0 / 2 (y lines, contiguous): every warp takes lines on its own; the first
+// radix pass reads the line from global memory and the last one writes it back
+// (MODE 2 conjugated), so the line crosses shared memory only between passes.
+// Latency is hidden by the resident warps (the line's loads of all lanes are in
+// flight together).
+// MODE 1 (x lines, stride n2): tiles of 8 lines are copied through shared memory
+// cooperatively (8 adjacent lines give 64-byte row segments; cp.async into the
+// second buffer while the first is transformed); the line stride is 2 mod 4
+// elements so the tile copies do not conflict. MODE 1 reads the x symbol in
+// natural order and the y symbol in the order the y pass left (ysym: natural
+// after this kernel's MODE 0, digit-reversed after k_fft_lines).
 // ---------------------------------------------------------------------------
+// Blocks per SM the register budget is sized for (FP32 at N <= 512: 71-80
+// registers, no spills; FP64 and N = 1024 lines leave room for fewer).
+template <typename T, int N>
+constexpr int wlines_min_blocks() { return (sizeof(T) == 4 && N <= 512) ? 3 : 1; }
+
+template <int MODE, int N>
+__host__ __device__ constexpr int wlines_stride() { return N + N / 16 + (MODE == 1 ? 2 : 0); }
+
+// -inv_n / lambda of the Poisson solve: the fast division in FP32 (relative error
+// 2 ulp, far below the FP32 field noise), IEEE division in FP64.
+__device__ __forceinline__ float poisson_gain(float inv_n, float lam) { return __fdividef(-inv_n, lam); }
+__device__ __forceinline__ double poisson_gain(double inv_n, double lam) { return -inv_n / lam; }
+
 template <typename T, int MODE, int N>
-__global__ void __launch_bounds__(kThreads) k_fft_wlines(Geom g, Ptrs<T> p, const cx<T>* __restrict__ tw,
-                                                         const T* __restrict__ xsym, const T* __restrict__ ysym,
-                                                         const T* __restrict__ sym3, T inv_n) {
+__global__ void __launch_bounds__(kThreads, wlines_min_blocks<T, N>())
+    k_fft_wlines(Geom g, Ptrs<T> p, const cx<T>* __restrict__ tw, const T* __restrict__ xsym,
+                 const T* __restrict__ ysym, const T* __restrict__ sym3, T inv_n) {
     using C = cx<T>;
-    constexpr int L = kThreads / 32;              // lines per tile, one per warp
-    constexpr int LS = N + N / 16 + (MODE == 1 ? 1 : 0);   // padded line (wpad), odd stride for MODE 1
+    constexpr int L = kThreads / 32;              // warps per block
+    constexpr int LS = wlines_stride<MODE, N>();  // padded line (wpad)
     const int s = blockIdx.y + p.s0;
     if (!p.run_all && !p.sc[s].active) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* twl = reinterpret_cast<C*>(smem_raw);
-    C* buf[2];
-    buf[0] = twl + N;
-    buf[1] = buf[0] + (size_t)L * LS;
-    for (int t = threadIdx.x; t < N; t += kThreads) twl[t] = tw[t];
-    const long long plane = (long long)g.n1 * g.n2;
-    const long long nlines = (MODE == 1) ? (long long)g.n3h * g.n2 : (long long)g.n3h * g.n1;
-    const long long ntiles = (nlines + L - 1) / L;
+    warp_tw_fill<C, N>(twl, tw);
     C* spec = p.spec + (size_t)s * g.Nh;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int cl = threadIdx.x & (L - 1);         // MODE 1: this thread's line in a tile
-    const int m0 = threadIdx.x / L;
-    constexpr int mstep = kThreads / L;
-    auto issue = [&](long long t, C* b) {
-        const long long l0 = t * L;
-        if (MODE == 1) {
-            const long long l = l0 + cl;
+    if constexpr (MODE != 1) {
+        __syncthreads();
+        C* x = twl + N + warp * LS;
+        const long long nlines = (long long)g.n3h * g.n1;
+        const long long wstep = (long long)gridDim.x * L;
+        for (long long l = (long long)blockIdx.x * L + warp; l < nlines; l += wstep) {
+            C* line = spec + l * N;
+            warp_fft_global<C, N, MODE == 2>(line, line, x, twl, lane);
+        }
+    } else {
+        C* const buf0 = twl + N;
+        C* const buf1 = buf0 + (size_t)L * LS;
+        const long long plane = (long long)g.n1 * g.n2;
+        const long long nlines = (long long)g.n3h * g.n2;
+        const long long ntiles = (nlines + L - 1) / L;
+        // thread (cl, m0) moves elements m0 + 32 i of line cl of a tile (64-byte row
+        // segments per 8 threads): a per-thread base plus compile-time offsets
+        constexpr int MSTEP = kThreads / L;
+        const int cl = threadIdx.x & (L - 1);
+        const int m0 = threadIdx.x / L;
+        const int sb = cl * LS + wpad(m0);
+        auto issue = [&](long long t, C* b) {
+            const long long l = t * L + cl;
             if (l < nlines) {
                 const int kz = (int)fdiv((unsigned)l, g.div_n2);
                 const int k2 = (int)(l - (long long)kz * g.n2);
-                const C* src = spec + (long long)kz * plane + k2;
-                for (int m = m0; m < N; m += mstep) cp_async_cx(&b[cl * LS + wpad(m)], src + (long long)m * g.n2);
+                const C* src = spec + (long long)kz * plane + k2 + (long long)m0 * g.n2;
+                const long long st = (long long)MSTEP * g.n2;
+#pragma unroll
+                for (int i = 0; i < N / MSTEP; ++i) cp_async_cx(&b[sb + cpad(MSTEP * i)], src + i * st);
             } else {
-                for (int m = m0; m < N; m += mstep) b[cl * LS + wpad(m)] = cmake<C>(T(0), T(0));
+#pragma unroll
+                for (int i = 0; i < N / MSTEP; ++i) b[sb + cpad(MSTEP * i)] = cmake<C>(T(0), T(0));
             }
-        } else {
-            for (int idx = threadIdx.x; idx < L * N; idx += kThreads) {
-                const int c = idx / N, m = idx % N;
-                const long long l = l0 + c;
-                if (l < nlines)
-                    cp_async_cx(&b[c * LS + wpad(m)], spec + l * N + m);
-                else
-                    b[c * LS + wpad(m)] = cmake<C>(T(0), T(0));
-            }
-        }
-        cp_async_commit();
-    };
-    long long t = blockIdx.x;
-    int cur = 0;
-    if (t < ntiles) issue(t, buf[0]);
-    for (; t < ntiles; t += gridDim.x) {
-        const long long tn = t + gridDim.x;
-        if (tn < ntiles)
-            issue(tn, buf[cur ^ 1]);
-        else
             cp_async_commit();
-        cp_async_wait_one();
-        __syncthreads();
-        C* b = buf[cur];
-        const long long l0 = t * L;
-        C* x = b + warp * LS;
-        warp_fft<C, N>(x, twl, lane);
-        if (MODE == 1) {
-            const long long l = l0 + warp;
-            const bool valid = l < nlines;
+        };
+        long long t = blockIdx.x;
+        bool cur = false;
+        if (t < ntiles) issue(t, buf0);
+        for (; t < ntiles; t += gridDim.x) {
+            C* const b = cur ? buf1 : buf0;
+            const long long tn = t + gridDim.x;
+            if (tn < ntiles)
+                issue(tn, cur ? buf0 : buf1);
+            else
+                cp_async_commit();
+            cp_async_wait_one();
+            __syncthreads();
+            const long long l0 = t * L;
+            C* x = b + warp * LS;
+            warp_fft<C, N>(x, twl, lane);
+            const long long lw = l0 + warp;
+            const bool valid = lw < nlines;
             int kz = 0, k2 = 0;
             if (valid) {
-                kz = (int)fdiv((unsigned)l, g.div_n2);
-                k2 = (int)(l - (long long)kz * g.n2);
+                kz = (int)fdiv((unsigned)lw, g.div_n2);
+                k2 = (int)(lw - (long long)kz * g.n2);
             }
             const T lam23 = valid ? ysym[k2] + sym3[kz] : T(0);
-            for (int m = lane; m < N; m += 32) {
-                const T lam = xsym[m] + lam23;
-                const T gk = (valid && lam > T(0)) ? -inv_n / lam : T(0);
-                const C z = x[wpad(m)];
-                x[wpad(m)] = cmake<C>(z.x * gk, -z.y * gk);   // conj: the inverse runs as conj(FFT(conj(.)))
+            C* xl = x + wpad(lane);
+#pragma unroll 4
+            for (int i = 0; i < N / 32; ++i) {
+                const T lam = xsym[lane + 32 * i] + lam23;
+                const T gk = (valid && lam > T(0)) ? poisson_gain(inv_n, lam) : T(0);
+                const C z = xl[cpad(32 * i)];
+                xl[cpad(32 * i)] = cmake<C>(z.x * gk, -z.y * gk);   // conj: the inverse runs as conj(FFT(conj(.)))
             }
             __syncwarp();
             warp_fft<C, N>(x, twl, lane);
-        }
-        __syncthreads();
-        if (MODE == 1) {
+            __syncthreads();
             const long long l = l0 + cl;
             if (l < nlines) {
-                const int kz = (int)fdiv((unsigned)l, g.div_n2);
-                const int k2 = (int)(l - (long long)kz * g.n2);
-                C* dst = spec + (long long)kz * plane + k2;
-                for (int m = m0; m < N; m += mstep) dst[(long long)m * g.n2] = b[cl * LS + wpad(m)];
+                const int kzs = (int)fdiv((unsigned)l, g.div_n2);
+                const int k2s = (int)(l - (long long)kzs * g.n2);
+                C* dst = spec + (long long)kzs * plane + k2s + (long long)m0 * g.n2;
+                const long long st = (long long)MSTEP * g.n2;
+#pragma unroll
+                for (int i = 0; i < N / MSTEP; ++i) dst[i * st] = b[sb + cpad(MSTEP * i)];
             }
-        } else {
-            for (int idx = threadIdx.x; idx < L * N; idx += kThreads) {
-                const int c = idx / N, m = idx % N;
-                const long long l = l0 + c;
-                if (l < nlines) {
-                    const C v = b[c * LS + wpad(m)];
-                    spec[l * N + m] = (MODE == 2) ? cconj(v) : v;
-                }
-            }
+            __syncthreads();
+            cur = !cur;
         }
-        __syncthreads();
-        cur ^= 1;
     }
 }
 
@@ -838,7 +852,7 @@ __global__ void __launch_bounds__(kThreads) k_div_rfft_wz(Geom g, Ptrs<T> p, con
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* twl = reinterpret_cast<C*>(smem_raw);
     C* lines = twl + N;
-    for (int t = threadIdx.x; t < N; t += kThreads) twl[t] = tw[t];
+    warp_tw_fill<C, N>(twl, tw);
     const T irho = T(1) / (T)p.sc[s].rho;
     const T h = T(0.70710678118654752440084436210485);
     const long long Nv = g.N;
@@ -944,7 +958,7 @@ __global__ void __launch_bounds__(kThreads) k_irfft_wz(Geom g, Ptrs<T> p, const 
     C* twl = reinterpret_cast<C*>(smem_raw);
     C* lines = twl + N;
     C* raw = lines + NW * LS;             // [NH][RLP]
-    for (int t = threadIdx.x; t < N; t += kThreads) twl[t] = tw[t];
+    warp_tw_fill<C, N>(twl, tw);
     const long long L = (long long)g.n1 * g.n2;
     const long long l0 = (long long)blockIdx.x * RL;
     const C* spec = p.spec + (size_t)s * g.Nh;

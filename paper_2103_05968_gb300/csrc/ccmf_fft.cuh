@@ -323,24 +323,29 @@ __device__ __forceinline__ void warp_tw_fill(C* twl, const C* __restrict__ tw) {
 // od + r NS separable) or wpad(lane) (NS >= 32). So every shared-memory access
 // of a pass is one instruction with an immediate offset.
 //
-// GIN: the first pass reads the line from gin (global memory, natural order,
-// unpadded; consecutive lanes read consecutive elements). GOUT: the last pass
-// (NS >= 32, outputs lane + const) writes it to gout, conjugated if CONJ. Both
-// skip a shared-memory round trip of the whole line.
-template <typename C, int N, int NS, int OFF, bool GIN = false, bool GOUT = false, bool CONJ = false>
-__device__ __forceinline__ void warp_stockham(C* x, const C* __restrict__ twl, int lane, const C* gin = nullptr,
-                                              C* gout = nullptr) {
+// Where the first pass reads the line and the last pass writes it (IN, OUT):
+// kIoSmem: x itself. kIoGlobal: gin / gout in global memory (natural order,
+// unpadded; consecutive lanes take consecutive elements; gout conjugated if
+// CONJ). kIoReg: the register array u of the lane, u[k] = element lane + 32 k
+// (the last pass has NS >= 32, so its outputs are exactly those elements, and
+// the first pass reads exactly those elements). kIoGlobal and kIoReg skip a
+// shared-memory round trip of the whole line.
+constexpr int kIoSmem = 0, kIoGlobal = 1, kIoReg = 2;
+
+template <typename C, int N, int NS, int OFF, int IN = kIoSmem, int OUT = kIoSmem, bool CONJ = false>
+__device__ __forceinline__ void warp_stockham(C* x, const C* __restrict__ twl, int lane, C (&u)[N / 32],
+                                              const C* gin = nullptr, C* gout = nullptr) {
     if constexpr (NS < N) {
         constexpr int R = warp_radix<N, NS>();
         constexpr int NB = N / R;                 // butterflies of the pass
         constexpr int PER = NB / 32;              // butterflies per lane
-        constexpr bool FROM_G = GIN && NS == 1;
-        constexpr bool TO_G = GOUT && NS * R == N;
+        constexpr int SRC = NS == 1 ? IN : kIoSmem;
+        constexpr int DST = NS * R == N ? OUT : kIoSmem;
         static_assert(NB % 32 == 0, "every lane takes whole butterflies");
         static_assert(NS == 1 || NS >= 16 || NS * R >= 16, "separable store offsets");
-        static_assert(!TO_G || NS >= 32, "the last pass writes lane + const");
+        static_assert(DST == kIoSmem || NS >= 32, "the last pass writes lane + const");
         C v[PER][R];
-        if constexpr (FROM_G) {
+        if constexpr (SRC == kIoGlobal) {
             const C* gl = gin + lane;
 #pragma unroll
             for (int b = 0; b < PER; ++b) {
@@ -348,6 +353,12 @@ __device__ __forceinline__ void warp_stockham(C* x, const C* __restrict__ twl, i
                 for (int r = 0; r < R; ++r) v[b][r] = gl[32 * b + r * NB];
             }
             __syncwarp();   // the warp's previous line has been read out of x
+        } else if constexpr (SRC == kIoReg) {
+#pragma unroll
+            for (int b = 0; b < PER; ++b) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[b][r] = u[(32 * b + r * NB) / 32];
+            }
         } else {
             const C* xl = x + wpad(lane);
 #pragma unroll
@@ -369,14 +380,17 @@ __device__ __forceinline__ void warp_stockham(C* x, const C* __restrict__ twl, i
         }
 #pragma unroll
         for (int b = 0; b < PER; ++b) Dft<C, R>::run(v[b]);
-        if constexpr (TO_G) {
+        if constexpr (DST == kIoGlobal || DST == kIoReg) {
             C* gl = gout + lane;
 #pragma unroll
             for (int b = 0; b < PER; ++b) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const int kb = ((32 * b) & ~(NS - 1)) * R + ((32 * b) & (NS - 1));
-                    gl[kb + r * NS] = CONJ ? cmake<C>(v[b][r].x, -v[b][r].y) : v[b][r];
+                    if constexpr (DST == kIoReg)
+                        u[(kb + r * NS) / 32] = v[b][r];
+                    else
+                        gl[kb + r * NS] = CONJ ? cmake<C>(v[b][r].x, -v[b][r].y) : v[b][r];
                 }
             }
         } else {
@@ -413,25 +427,51 @@ __device__ __forceinline__ void warp_stockham(C* x, const C* __restrict__ twl, i
             }
             __syncwarp();
         }
-        warp_stockham<C, N, NS * R, (NS > 1 ? OFF + (R - 1) * NS : OFF), GIN, GOUT, CONJ>(x, twl, lane, gin, gout);
+        warp_stockham<C, N, NS * R, (NS > 1 ? OFF + (R - 1) * NS : OFF), IN, OUT, CONJ>(x, twl, lane, u, gin, gout);
     }
 }
 
-template <typename C, int N>
-__device__ __forceinline__ void warp_fft(C* x, const C* __restrict__ twl, int lane) {
-    static_assert(N >= 128 && N <= 1024 && (N & (N - 1)) == 0, "warp FFT length");
-    static_assert(warp_tw_count<N>() <= N, "twiddle table fits N entries");
-    warp_stockham<C, N, 1, 0>(x, twl, lane);
+template <int N>
+__host__ __device__ constexpr bool warp_fft_ok() {
+    return N >= 128 && N <= 1024 && (N & (N - 1)) == 0 && warp_tw_count<N>() <= N;
 }
 
-// The same transform from global line gin to global line gout (conjugated if
-// CONJ; gin == gout allowed: the whole line is in registers or x in between),
-// with x as the warp's shared-memory scratch line.
+// Shared-memory line x[wpad(m)] in and out.
+template <typename C, int N>
+__device__ __forceinline__ void warp_fft(C* x, const C* __restrict__ twl, int lane) {
+    static_assert(warp_fft_ok<N>(), "warp FFT length");
+    C u[N / 32];
+    warp_stockham<C, N, 1, 0>(x, twl, lane, u);
+}
+
+// Global line gin to global line gout (conjugated if CONJ; gin == gout allowed:
+// the whole line is in registers or x in between), x as the warp's scratch line.
 template <typename C, int N, bool CONJ>
 __device__ __forceinline__ void warp_fft_global(const C* gin, C* gout, C* x, const C* __restrict__ twl, int lane) {
-    static_assert(N >= 128 && N <= 1024 && (N & (N - 1)) == 0, "warp FFT length");
-    static_assert(warp_tw_count<N>() <= N, "twiddle table fits N entries");
-    warp_stockham<C, N, 1, 0, true, true, CONJ>(x, twl, lane, gin, gout);
+    static_assert(warp_fft_ok<N>(), "warp FFT length");
+    C u[N / 32];
+    warp_stockham<C, N, 1, 0, kIoGlobal, kIoGlobal, CONJ>(x, twl, lane, u, gin, gout);
+}
+
+// Shared-memory line in, result in registers: u[k] = X[lane + 32 k].
+template <typename C, int N>
+__device__ __forceinline__ void warp_fft_to_regs(C* x, const C* __restrict__ twl, int lane, C (&u)[N / 32]) {
+    static_assert(warp_fft_ok<N>(), "warp FFT length");
+    warp_stockham<C, N, 1, 0, kIoSmem, kIoReg>(x, twl, lane, u);
+}
+
+// Registers in and out (u[k] = element lane + 32 k), x as scratch between passes.
+template <typename C, int N>
+__device__ __forceinline__ void warp_fft_regs(C* x, const C* __restrict__ twl, int lane, C (&u)[N / 32]) {
+    static_assert(warp_fft_ok<N>(), "warp FFT length");
+    warp_stockham<C, N, 1, 0, kIoReg, kIoReg>(x, twl, lane, u);
+}
+
+// Registers in (u[k] = x[lane + 32 k]), result in the shared-memory line x.
+template <typename C, int N>
+__device__ __forceinline__ void warp_fft_from_regs(C* x, const C* __restrict__ twl, int lane, C (&u)[N / 32]) {
+    static_assert(warp_fft_ok<N>(), "warp FFT length");
+    warp_stockham<C, N, 1, 0, kIoReg, kIoSmem>(x, twl, lane, u);
 }
 
 }  // namespace ccmf

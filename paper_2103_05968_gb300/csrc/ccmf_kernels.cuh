@@ -542,10 +542,15 @@ __global__ void __launch_bounds__(kThreads) k_fft_lines(Geom g, Ptrs<T> p, AxisP
 // natural order and the y symbol in the order the y pass left (ysym: natural
 // after this kernel's MODE 0, digit-reversed after k_fft_lines).
 // ---------------------------------------------------------------------------
-// Blocks per SM the register budget is sized for (FP32 at N <= 512: 71-80
-// registers, no spills; FP64 and N = 1024 lines leave room for fewer).
-template <typename T, int N>
-constexpr int wlines_min_blocks() { return (sizeof(T) == 4 && N <= 512) ? 3 : 1; }
+// Blocks per SM the register budget is sized for. FP32 y passes at N <= 512 fit
+// 3 blocks without spills. The x pass at N = 512 holds the whole transformed
+// line in registers between its two FFTs: capped for 3 blocks it spills, and on
+// GB300 2 blocks without spills are 13 % faster. FP64 and N = 1024 leave room for
+// fewer blocks.
+template <typename T, int MODE, int N>
+constexpr int wlines_min_blocks() {
+    return (sizeof(T) == 4 && N <= 512) ? ((MODE == 1 && N == 512) ? 2 : 3) : 1;
+}
 
 template <int MODE, int N>
 __host__ __device__ constexpr int wlines_stride() { return N + N / 16 + (MODE == 1 ? 2 : 0); }
@@ -556,7 +561,7 @@ __device__ __forceinline__ float poisson_gain(float inv_n, float lam) { return _
 __device__ __forceinline__ double poisson_gain(double inv_n, double lam) { return -inv_n / lam; }
 
 template <typename T, int MODE, int N>
-__global__ void __launch_bounds__(kThreads, wlines_min_blocks<T, N>())
+__global__ void __launch_bounds__(kThreads, wlines_min_blocks<T, MODE, N>())
     k_fft_wlines(Geom g, Ptrs<T> p, const cx<T>* __restrict__ tw, const T* __restrict__ xsym,
                  const T* __restrict__ ysym, const T* __restrict__ sym3, T inv_n) {
     using C = cx<T>;
@@ -619,7 +624,11 @@ __global__ void __launch_bounds__(kThreads, wlines_min_blocks<T, N>())
             __syncthreads();
             const long long l0 = t * L;
             C* x = b + warp * LS;
-            warp_fft<C, N>(x, twl, lane);
+            // forward x FFT into registers (u[k] = X[lane + 32 k]), the Poisson gain,
+            // then the inverse from the same registers: the spectrum line does not
+            // go through shared memory in between
+            C u[N / 32];
+            warp_fft_to_regs<C, N>(x, twl, lane, u);
             const long long lw = l0 + warp;
             const bool valid = lw < nlines;
             int kz = 0, k2 = 0;
@@ -628,16 +637,13 @@ __global__ void __launch_bounds__(kThreads, wlines_min_blocks<T, N>())
                 k2 = (int)(lw - (long long)kz * g.n2);
             }
             const T lam23 = valid ? ysym[k2] + sym3[kz] : T(0);
-            C* xl = x + wpad(lane);
-#pragma unroll 4
-            for (int i = 0; i < N / 32; ++i) {
-                const T lam = xsym[lane + 32 * i] + lam23;
+#pragma unroll
+            for (int k = 0; k < N / 32; ++k) {
+                const T lam = xsym[lane + 32 * k] + lam23;
                 const T gk = (valid && lam > T(0)) ? poisson_gain(inv_n, lam) : T(0);
-                const C z = xl[cpad(32 * i)];
-                xl[cpad(32 * i)] = cmake<C>(z.x * gk, -z.y * gk);   // conj: the inverse runs as conj(FFT(conj(.)))
+                u[k] = cmake<C>(u[k].x * gk, -u[k].y * gk);   // conj: the inverse runs as conj(FFT(conj(.)))
             }
-            __syncwarp();
-            warp_fft<C, N>(x, twl, lane);
+            warp_fft_from_regs<C, N>(x, twl, lane, u);
             __syncthreads();
             const long long l = l0 + cl;
             if (l < nlines) {
@@ -974,23 +980,31 @@ __global__ void __launch_bounds__(kThreads) k_irfft_wz(Geom g, Ptrs<T> p, const 
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     C* x = lines + w * LS;
-    for (int kz = lane; kz < NH; kz += 32) {
-        const C a = raw[kz * RLP + 2 * w], b = raw[kz * RLP + 2 * w + 1];
-        if (kz == 0 || 2 * kz == N) {
-            x[wpad(kz)] = cmake<C>(a.x, -b.x);               // Z = Re(a) + i Re(b), stored conjugated
+    // element m = lane + 32 k of packed line w, straight into registers:
+    // Z(m) = conj(a + i b) from slab row m for m <= N / 2 (a, b the spectra of the
+    // line pair), conj(conj(a) + i conj(b)) from row N - m above
+    C u[N / 32];
+#pragma unroll
+    for (int k = 0; k < N / 32; ++k) {
+        const int m = lane + 32 * k;
+        if (2 * m <= N) {
+            const C a = raw[m * RLP + 2 * w], b = raw[m * RLP + 2 * w + 1];
+            u[k] = (m == 0 || 2 * m == N) ? cmake<C>(a.x, -b.x)                   // Z = Re(a) + i Re(b), conjugated
+                                          : cmake<C>(a.x - b.y, -(a.y + b.x));
         } else {
-            x[wpad(kz)] = cmake<C>(a.x - b.y, -(a.y + b.x));   // conj(a + i b)
-            x[wpad(N - kz)] = cmake<C>(a.x + b.y, a.y - b.x);  // conj(conj(a) + i conj(b))
+            const int mm = N - m;
+            const C a = raw[mm * RLP + 2 * w], b = raw[mm * RLP + 2 * w + 1];
+            u[k] = cmake<C>(a.x + b.y, a.y - b.x);
         }
     }
-    __syncwarp();
-    warp_fft<C, N>(x, twl, lane);
+    warp_fft_regs<C, N>(x, twl, lane, u);
+    // real line 2w is Re, line 2w + 1 is -Im of the result (the conjugated inverse)
     T* phi = p.phi + (size_t)s * g.N;
     const long long la = l0 + 2 * w;
-    for (int m = lane; m < N; m += 32) {
-        const C z = x[wpad(m)];
-        if (la < L) phi[la * N + m] = z.x;
-        if (la + 1 < L) phi[(la + 1) * N + m] = -z.y;
+#pragma unroll
+    for (int k = 0; k < N / 32; ++k) {
+        if (la < L) phi[la * N + lane + 32 * k] = u[k].x;
+        if (la + 1 < L) phi[(la + 1) * N + lane + 32 * k] = -u[k].y;
     }
 }
 

@@ -388,7 +388,8 @@ int shape_for(const ccmf_plan* pl, const ccmf_tuning& t, LaunchShape* out, ccmf_
     if (ze >= 1 && warp_len_ok(n3)) {
         const size_t lsz = (size_t)n3 + n3 / 16 + 1;
         const size_t sd = ((size_t)n3 + 8 * lsz) * cs;
-        const size_t si = ((size_t)n3 + 8 * lsz + (size_t)(n3 / 2 + 1) * 17) * cs;
+        // inverse: twiddles + the larger of the slab of 16 spectrum rows and the 8 scratch lines
+        const size_t si = ((size_t)n3 + std::max(8 * lsz, (size_t)(n3 / 2 + 1) * 17)) * cs;
         if (si <= kSmemMax) {
             sh.wz = n3;
             sh.smem_wzi = si;

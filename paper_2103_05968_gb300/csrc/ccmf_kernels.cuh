@@ -962,8 +962,10 @@ __global__ void __launch_bounds__(kThreads) k_irfft_wz(Geom g, Ptrs<T> p, const 
     if (!p.run_all && !p.sc[s].active) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* twl = reinterpret_cast<C*>(smem_raw);
-    C* lines = twl + N;
-    C* raw = lines + NW * LS;             // [NH][RLP]
+    // the slab [NH][RLP] of the block's spectrum rows; once the lanes hold their
+    // elements in registers the same memory serves as the warps' scratch lines
+    C* raw = twl + N;
+    C* lines = raw;
     warp_tw_fill<C, N>(twl, tw);
     const long long L = (long long)g.n1 * g.n2;
     const long long l0 = (long long)blockIdx.x * RL;
@@ -997,6 +999,7 @@ __global__ void __launch_bounds__(kThreads) k_irfft_wz(Geom g, Ptrs<T> p, const 
             u[k] = cmake<C>(a.x + b.y, a.y - b.x);
         }
     }
+    __syncthreads();   // the slab is read out: its memory becomes the scratch lines
     warp_fft_regs<C, N>(x, twl, lane, u);
     // real line 2w is Re, line 2w + 1 is -Im of the result (the conjugated inverse)
     T* phi = p.phi + (size_t)s * g.N;

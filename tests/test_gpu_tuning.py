@@ -135,8 +135,8 @@ def test_plans_of_different_sizes_coexist():
 @pytest.mark.parametrize("engine", [2, 1, 0], ids=["warp_both", "warp_inverse", "block_z"])
 def test_fp64_z_passes_against_oracle(shape, engine):
     """Divergence + R2C and C2R along z with one warp per line pair (power-of-two N3, line
-    counts that leave a partial tile of 16 lines; the divergence pass's 2 x 8 line tiles ragged
-    in x and y) or Stockham tiles: FP64 parity with the oracle."""
+    counts that leave a partial tile of 16 lines, several tiles with neighbour rows in other
+    tiles) or Stockham tiles: FP64 parity with the oracle."""
     gamma = M.random_two_phase(shape, 0.3, 0.25, 1.0, 17)
     normals = [[0.36, 0.48, 0.8], [0.0, 0.0, 1.0]]
     plan = ccmf.Plan(shape, batch=2, precision=ccmf.CCMF_FP64, device=DEV)

@@ -301,6 +301,8 @@ int shape_for(const ccmf_plan* pl, const ccmf_tuning& t, LaunchShape* out, ccmf_
     r.update_variant = sh.upd_variant;
     sh.grid_partials = std::max(sh.grid_update, sh.grid_tma);
     if (sh.upd_variant >= 2) sh.grid_partials = std::max(sh.grid_partials, sh.grid_pipe);
+    // the vector update pass (variant 0 and every final evaluation) keeps one slot per chunk
+    sh.grid_partials = (int)std::max<long long>(sh.grid_partials, vec_update_chunks(pl->g.N, f64 ? 2 : 4));
     // y / x passes: one block per k_z plane when the plane fits its shared memory, a
     // cluster of C blocks (C divides n1 and n2) sharing the plane through distributed
     // shared memory, or the three strided passes

@@ -63,14 +63,11 @@ __device__ __forceinline__ T warp_sum(T x) {
     return x;
 }
 
-// Block reduction of kNSum per-thread values (T) into one double each, written
-// to partial[b * kNSum + q]; returns true in every thread of the block that
-// finishes last for this solve (its partials are then visible to it).
+// Block reduction of NQ per-thread values (T) into one double each, written to
+// partial[b * NQ + q] (fixed order: warp shuffles, then the warps in turn).
 template <typename T, int NQ, int NT = kThreads>
-__device__ bool block_partials(T (&acc)[NQ], double* __restrict__ partial, unsigned int* counter,
-                               int nblocks, int b) {
+__device__ void block_store_partial(const T (&acc)[NQ], double* __restrict__ partial, long long b) {
     __shared__ double red[NT / 32][NQ];
-    __shared__ int last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
@@ -81,8 +78,15 @@ __device__ bool block_partials(T (&acc)[NQ], double* __restrict__ partial, unsig
     if (threadIdx.x < NQ) {
         double s = 0.0;
         for (int w = 0; w < NT / 32; ++w) s += red[w][threadIdx.x];
-        partial[(size_t)b * NQ + threadIdx.x] = s;
+        partial[b * NQ + threadIdx.x] = s;
     }
+}
+
+// Ticket of a block that has stored its partials: true in every thread of the block
+// that finishes last of nblocks (every partial is then visible to it).
+template <int NT = kThreads>
+__device__ bool block_ticket(unsigned int* counter, int nblocks) {
+    __shared__ int last;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -91,6 +95,14 @@ __device__ bool block_partials(T (&acc)[NQ], double* __restrict__ partial, unsig
     }
     __syncthreads();
     return last != 0;
+}
+
+// Both: the block's partials, then its ticket.
+template <typename T, int NQ, int NT = kThreads>
+__device__ bool block_partials(T (&acc)[NQ], double* __restrict__ partial, unsigned int* counter,
+                               int nblocks, int b) {
+    block_store_partial<T, NQ, NT>(acc, partial, b);
+    return block_ticket<NT>(counter, nblocks);
 }
 
 // Deterministic double reduction of nblocks x NQ partials by one block.
@@ -873,13 +885,24 @@ __global__ void __launch_bounds__(kThreads) k_div_rfft_wz(Geom g, Ptrs<T> p, con
     constexpr int W = Vec16<T>::W;
     constexpr int G = N / (32 * W);      // groups per lane
     static_assert(G >= 1, "line too short for the warp z pass");
+    // Group by group, both lines of the pair: a line's y-neighbour rows are the other line of
+    // the pair and the neighbouring warps' lines, so they are read again while still in cache.
+    // (Line by line, at N3 = 512 the y-neighbour rows were evicted between the neighbour read and
+    // the line's own read and came back from DRAM.)
+    RowNb rnq[2];
+    bool validq[2];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
         const long long l = l0 + 2 * w + q;
-        const bool valid = l < L;
-        const RowNb rn = row_neighbours(g, (unsigned)(valid ? l : 0));
+        validq[q] = l < L;
+        rnq[q] = row_neighbours(g, (unsigned)(validq[q] ? l : 0));
+    }
 #pragma unroll 1
-        for (int t = 0; t < G; ++t) {   // one group at a time keeps the registers low
+    for (int t = 0; t < G; ++t) {   // one group at a time keeps the registers low
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const bool valid = validq[q];
+            const RowNb& rn = rnq[q];
             const int k0 = W * lane + 32 * W * t;
             T d[W];
 #pragma unroll
@@ -1194,16 +1217,29 @@ __device__ __forceinline__ void voxel_step(const StepConsts<T>& K, const T (&ec)
 // Reduction epilogue of the update pass: block partials, then the last block of
 // the solve reduces them in double and runs the penalty / history / stop logic.
 template <typename T, bool OUT, int NT = kThreads>
+__device__ void update_finish(const Geom& g, const Ptrs<T>& p, const LoopConfig& cfg, SolveScalars& S, int s,
+                              double rho_d, const double* part, int nparts);
+
+template <typename T, bool OUT, int NT = kThreads>
 __device__ void update_epilogue(const Geom& g, const Ptrs<T>& p, const LoopConfig& cfg, SolveScalars& S, int s,
                                 double rho_d, T (&acc)[kNSum]) {
     const int nblocks = gridDim.x;
     double* part = p.partial + (size_t)s * nblocks * kNSum;
     const bool last = block_partials<T, kNSum, NT>(acc, part, &S.counter, nblocks, blockIdx.x);
     if (!last) return;
+    update_finish<T, OUT, NT>(g, p, cfg, S, s, rho_d, part, nblocks);
+}
+
+// The last block of a solve's update pass: reduce the nparts partials in a fixed
+// order, then the penalty rule, the history row and the stop decision.
+template <typename T, bool OUT, int NT>
+__device__ void update_finish(const Geom& g, const Ptrs<T>& p, const LoopConfig& cfg, SolveScalars& S, int s,
+                              double rho_d, const double* part, int nparts) {
     double sums[kNSum];
-    reduce_partials<kNSum, NT>(part, nblocks, sums);
+    reduce_partials<kNSum, NT>(part, nparts, sums);
     if (threadIdx.x != 0) return;
     S.counter = 0;
+    S.chunk = 0;   // every block has left its work loop: the next launch starts from ticket 0
     const double Nd = (double)g.N;
     bool finite = true;
     for (int q = 0; q < kNSum; ++q) {
@@ -1391,93 +1427,117 @@ __global__ void __launch_bounds__(kThreads) k_update_vec(Geom g, Ptrs<T> p, Loop
     T* __restrict__ v_out = p.v + (long long)(1 - par) * p.sstride + (long long)s * 6 * N;
     const T* __restrict__ phi = p.phi + (size_t)s * N;
     const T* __restrict__ gam = gamma_of(p, s);
-    T acc[kNSum];
-#pragma unroll
-    for (int q = 0; q < kNSum; ++q) acc[q] = T(0);
     const long long ngroups = N / W;
-    const long long gstride = (long long)gridDim.x * kThreads;
-    for (long long q = (long long)blockIdx.x * kThreads + threadIdx.x; q < ngroups; q += gstride) {
-        const long long lin0 = q * W;
-        const unsigned row = fdiv((unsigned)lin0, g.div_n3);
-        const int k0 = (int)(lin0 - (long long)row * g.n3);
-        const RowNb rn = row_neighbours(g, row);
-        const int kp = (k0 + W == g.n3) ? 0 : k0 + W;
-        const int km = (k0 == 0) ? g.n3 - 1 : k0 - 1;
-        T ec[6][W], vc[6][W];
+    // Dynamic schedule: blocks take chunks of kVecChunkGroups x kThreads groups (32 rows at
+    // N3 = 512) in order from a per-solve ticket counter, the next ticket fetched while the
+    // current chunk runs. The chunks in flight then form one narrow front through the grid, and
+    // the x- and y-neighbour rows a chunk reads were read as other chunks' own rows moments
+    // before, so they come from L2. (With a grid-stride loop the blocks drift apart over a long
+    // pass; at 512^3, 42 % more than the algorithmic reads came from DRAM.) Each chunk stores its
+    // own partial sums and the last block reduces them in chunk order, so the result does not
+    // depend on which block took which chunk.
+    const long long nchunks = vec_update_chunks(N, W);
+    double* part = p.partial + (size_t)s * nchunks * kNSum;
+    __shared__ unsigned ticket[2];
+    if (threadIdx.x == 0) ticket[0] = atomicAdd(&S.chunk, 1u);
+    __syncthreads();
+    for (int it = 0;; ++it) {
+        const unsigned ck = ticket[it & 1];
+        if (ck >= nchunks) break;   // the same value for the whole block
+        if (threadIdx.x == 0) ticket[(it + 1) & 1] = atomicAdd(&S.chunk, 1u);
+        T acc[kNSum];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            V::ld(e + c * N + lin0, ec[c]);
-            V::ld(v + c * N + lin0, vc[c]);
+        for (int q = 0; q < kNSum; ++q) acc[q] = T(0);
+#pragma unroll 1
+        for (int gi = 0; gi < kVecChunkGroups; ++gi) {
+            const long long q = ((long long)ck * kVecChunkGroups + gi) * kThreads + threadIdx.x;
+            if (q < ngroups) {
+                const long long lin0 = q * W;
+                const unsigned row = fdiv((unsigned)lin0, g.div_n3);
+                const int k0 = (int)(lin0 - (long long)row * g.n3);
+                const RowNb rn = row_neighbours(g, row);
+                const int kp = (k0 + W == g.n3) ? 0 : k0 + W;
+                const int km = (k0 == 0) ? g.n3 - 1 : k0 - 1;
+                T ec[6][W], vc[6][W];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+                    V::ld(e + c * N + lin0, ec[c]);
+                    V::ld(v + c * N + lin0, vc[c]);
+                }
+                T gm[W], ph[W];
+                V::ld(gam + lin0, gm);
+                V::ld(phi + lin0, ph);
+                // x and y neighbours (whole groups), z neighbours inside the group or one scalar each side
+                T e2x[W], v2x[W], e1x[W], v1x[W], e2y[W], v2y[W], e1y[W], v1y[W];
+                T phxp[W], phxm[W], phyp[W], phym[W];
+                V::ld(e + 3 * N + rn.ip + k0, e2x);
+                V::ld(v + 3 * N + rn.ip + k0, v2x);
+                V::ld(e + 0 * N + rn.im + k0, e1x);
+                V::ld(v + 0 * N + rn.im + k0, v1x);
+                V::ld(e + 4 * N + rn.jp + k0, e2y);
+                V::ld(v + 4 * N + rn.jp + k0, v2y);
+                V::ld(e + 1 * N + rn.jm + k0, e1y);
+                V::ld(v + 1 * N + rn.jm + k0, v1y);
+                V::ld(phi + rn.ip + k0, phxp);
+                V::ld(phi + rn.im + k0, phxm);
+                V::ld(phi + rn.jp + k0, phyp);
+                V::ld(phi + rn.jm + k0, phym);
+                const T e2z_after = __ldg(e + 5 * N + rn.row + kp), v2z_after = __ldg(v + 5 * N + rn.row + kp);
+                const T e1z_before = __ldg(e + 2 * N + rn.row + km), v1z_before = __ldg(v + 2 * N + rn.row + km);
+                const T ph_after = __ldg(phi + rn.row + kp), ph_before = __ldg(phi + rn.row + km);
+                T eo[6][W], vo[6][W], fo[3][W];
+#pragma unroll
+                for (int u = 0; u < W; ++u) {
+                    T ecu[6], vcu[6];
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) {
+                        ecu[c] = ec[c][u];
+                        vcu[c] = vc[c][u];
+                    }
+                    const bool last = (u + 1 == W), first = (u == 0);
+                    const T php[3] = {phxp[u], phyp[u], last ? ph_after : ph[(u + 1) % W]};
+                    const T phm[3] = {phxm[u], phym[u], first ? ph_before : ph[(u + W - 1) % W]};
+                    const T e2p[3] = {e2x[u], e2y[u], last ? e2z_after : ec[5][(u + 1) % W]};
+                    const T v2p[3] = {v2x[u], v2y[u], last ? v2z_after : vc[5][(u + 1) % W]};
+                    const T e1m[3] = {e1x[u], e1y[u], first ? e1z_before : ec[2][(u + W - 1) % W]};
+                    const T v1m[3] = {v1x[u], v1y[u], first ? v1z_before : vc[2][(u + W - 1) % W]};
+                    T eou[6], vou[6], fl[3];
+                    voxel_step<T, OUT>(K, ecu, vcu, gm[u], ph[u], php, phm, e2p, v2p, e1m, v1m, acc, eou, vou, fl);
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) {
+                        eo[c][u] = eou[c];
+                        vo[c][u] = vou[c];
+                    }
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) fo[a][u] = fl[a];
+                }
+                if (OUT) {
+                    // final evaluation: the cut xi^{K+1/2} and the flow A* v^K
+                    if (p.cut) {
+                        T* cut = p.cut + (size_t)s * 6 * N;
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) V::st(cut + c * N + lin0, eo[c]);
+                    }
+                    if (p.flow) {
+                        T* flow = p.flow + (size_t)s * 3 * N;
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) V::st(flow + a * N + lin0, fo[a]);
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) {
+                        V::st(e_out + c * N + lin0, eo[c]);
+                        V::st(v_out + c * N + lin0, vo[c]);
+                    }
+                }
+            }
         }
-        T gm[W], ph[W];
-        V::ld(gam + lin0, gm);
-        V::ld(phi + lin0, ph);
-        // x and y neighbours (whole groups), z neighbours inside the group or one scalar each side
-        T e2x[W], v2x[W], e1x[W], v1x[W], e2y[W], v2y[W], e1y[W], v1y[W];
-        T phxp[W], phxm[W], phyp[W], phym[W];
-        V::ld(e + 3 * N + rn.ip + k0, e2x);
-        V::ld(v + 3 * N + rn.ip + k0, v2x);
-        V::ld(e + 0 * N + rn.im + k0, e1x);
-        V::ld(v + 0 * N + rn.im + k0, v1x);
-        V::ld(e + 4 * N + rn.jp + k0, e2y);
-        V::ld(v + 4 * N + rn.jp + k0, v2y);
-        V::ld(e + 1 * N + rn.jm + k0, e1y);
-        V::ld(v + 1 * N + rn.jm + k0, v1y);
-        V::ld(phi + rn.ip + k0, phxp);
-        V::ld(phi + rn.im + k0, phxm);
-        V::ld(phi + rn.jp + k0, phyp);
-        V::ld(phi + rn.jm + k0, phym);
-        const T e2z_after = __ldg(e + 5 * N + rn.row + kp), v2z_after = __ldg(v + 5 * N + rn.row + kp);
-        const T e1z_before = __ldg(e + 2 * N + rn.row + km), v1z_before = __ldg(v + 2 * N + rn.row + km);
-        const T ph_after = __ldg(phi + rn.row + kp), ph_before = __ldg(phi + rn.row + km);
-        T eo[6][W], vo[6][W], fo[3][W];
-#pragma unroll
-        for (int u = 0; u < W; ++u) {
-            T ecu[6], vcu[6];
-#pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                ecu[c] = ec[c][u];
-                vcu[c] = vc[c][u];
-            }
-            const bool last = (u + 1 == W), first = (u == 0);
-            const T php[3] = {phxp[u], phyp[u], last ? ph_after : ph[(u + 1) % W]};
-            const T phm[3] = {phxm[u], phym[u], first ? ph_before : ph[(u + W - 1) % W]};
-            const T e2p[3] = {e2x[u], e2y[u], last ? e2z_after : ec[5][(u + 1) % W]};
-            const T v2p[3] = {v2x[u], v2y[u], last ? v2z_after : vc[5][(u + 1) % W]};
-            const T e1m[3] = {e1x[u], e1y[u], first ? e1z_before : ec[2][(u + W - 1) % W]};
-            const T v1m[3] = {v1x[u], v1y[u], first ? v1z_before : vc[2][(u + W - 1) % W]};
-            T eou[6], vou[6], fl[3];
-            voxel_step<T, OUT>(K, ecu, vcu, gm[u], ph[u], php, phm, e2p, v2p, e1m, v1m, acc, eou, vou, fl);
-#pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                eo[c][u] = eou[c];
-                vo[c][u] = vou[c];
-            }
-#pragma unroll
-            for (int a = 0; a < 3; ++a) fo[a][u] = fl[a];
-        }
-        if (OUT) {
-            // final evaluation: the cut xi^{K+1/2} and the flow A* v^K
-            if (p.cut) {
-                T* cut = p.cut + (size_t)s * 6 * N;
-#pragma unroll
-                for (int c = 0; c < 6; ++c) V::st(cut + c * N + lin0, eo[c]);
-            }
-            if (p.flow) {
-                T* flow = p.flow + (size_t)s * 3 * N;
-#pragma unroll
-                for (int a = 0; a < 3; ++a) V::st(flow + a * N + lin0, fo[a]);
-            }
-        } else {
-#pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                V::st(e_out + c * N + lin0, eo[c]);
-                V::st(v_out + c * N + lin0, vo[c]);
-            }
-        }
+        block_store_partial<T, kNSum>(acc, part, ck);
+        __syncthreads();   // the next ticket is visible, this one is read by everyone, red[] is free
     }
-    update_epilogue<T, OUT>(g, p, cfg, S, s, rho_d, acc);
+    if (block_ticket(&S.counter, gridDim.x)) update_finish<T, OUT>(g, p, cfg, S, s, rho_d, part, (int)nchunks);
 }
+
 
 // ---------------------------------------------------------------------------
 // TMA-staged update pass. A tile is J consecutive z rows (i, j0 .. j0+J-1) of one

@@ -66,6 +66,7 @@ __global__ void k_setup(SolveScalars* sc, const double* __restrict__ xi, int bat
     sc[s].xi[1] = xi[3 * s + 1];
     sc[s].xi[2] = xi[3 * s + 2];
     sc[s].counter = 0;
+    sc[s].chunk = 0;
     sc[s].active = 0;
 }
 
@@ -445,6 +446,7 @@ __global__ void k_adj_restore(SolveScalars* sc, int batch, int k0, const double*
     sc[s].rho = sched[(size_t)s * sched_len + k0];
     sc[s].active = 1;
     sc[s].counter = 0;
+    sc[s].chunk = 0;
 }
 
 template <typename T>

@@ -175,7 +175,9 @@ int static_solve(int n1, int n2, int n3, const T* gamma, const double* xi_bar, c
         return o;
     };
     const size_t o_sc = take(256), o_nact = take(256), o_xi = take(3 * sizeof(double));
-    const size_t o_part = take(sizeof(double) * kNSum * (size_t)sh.grid_update);
+    // partial sums: one slot per update block, or per chunk of the vector update pass
+    const long long nparts = std::max<long long>(sh.grid_update, vec_update_chunks(g.N, 16 / (int)sizeof(T)));
+    const size_t o_part = take(sizeof(double) * kNSum * (size_t)nparts);
     const size_t o_hist = take(sizeof(double) * kHistFields * (size_t)kHistCap);
     const size_t o_e = take(sizeof(T) * 6 * N * 2), o_v = take(sizeof(T) * 6 * N * 2);
     const size_t o_spec = take(cs * (size_t)g.Nh), o_phi = take(sizeof(T) * N);

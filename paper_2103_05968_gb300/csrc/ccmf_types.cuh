@@ -25,6 +25,15 @@ constexpr int kHistFields = 6;
 constexpr int kHistCap = 4096;   // history entries reserved per solve
 constexpr int kThreads = 256;
 
+// The vector update pass works in chunks of kVecChunkGroups groups of 16 bytes per
+// thread (16 K voxels in FP32), taken in order from a ticket counter, with one
+// partial-sum slot per chunk.
+constexpr int kVecChunkGroups = 16;
+__host__ __device__ inline long long vec_update_chunks(long long n_voxels, int voxels_per_group) {
+    const long long per = (long long)kThreads * kVecChunkGroups;
+    return (n_voxels / voxels_per_group + per - 1) / per;
+}
+
 // One per solve, in the workspace (256-byte slot).
 struct SolveScalars {
     double rho;          // current penalty rho^k
@@ -39,7 +48,7 @@ struct SolveScalars {
     int call_start;      // iters at the start of the current solve call
     unsigned int counter;  // last-block ticket of the reductions
     int bad;             // number of invalid gamma values seen at init
-    int pad;
+    unsigned int chunk;  // next work ticket of the vector update pass (dynamic schedule)
 };
 static_assert(sizeof(SolveScalars) <= 256, "scalar slot");
 

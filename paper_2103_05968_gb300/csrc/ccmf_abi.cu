@@ -45,10 +45,11 @@ constexpr int kMaxN = 1024;
 constexpr size_t kSmemBudget = 96 * 1024;
 constexpr size_t kSmemMax = 200 * 1024;   // dynamic shared memory of one block, at most
 constexpr int kMaxTimedIters = 2048;
-// update-pass variant per precision, from measurements on GB300 (128^3 x 3 solves):
-// FP32 is bandwidth-bound and best with the 3-stage TMA pipeline of 128 threads,
-// FP64 is ALU-bound and best with register vectors
-constexpr int kDefaultUpdateVariantF32 = 3;
+// update-pass variant per precision, from measurements on GB300: register vectors in
+// ticket-ordered chunks (variant 0) in both. FP32 is bandwidth-bound: 0.248 ms per
+// 128^3 x 3 step against 0.253-0.256 ms with the pipelined variants, 2.41 ms per 512^3
+// pass against 4.1 TB/s for the pipelines. FP64 is ALU-bound.
+constexpr int kDefaultUpdateVariantF32 = 0;
 constexpr int kDefaultUpdateVariantF64 = 0;
 // the captured loop runs the solves of a batch as up to this many independent graph
 // branches, so that one branch's FFT pass (on-chip work) overlaps another branch's

@@ -598,7 +598,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch-shape rules")
-    ap.add_argument("--tune-iters", type=int, default=10, help="iterations timed per autotuner candidate")
+    ap.add_argument("--tune-iters", type=int, default=40, help="iterations timed per autotuner candidate")
     ap.add_argument("--tuning-in", default=None, help="tuning table text to import instead of autotuning")
     ap.add_argument("--tuning-out", default=None, help="write the tuning table text here after autotuning")
     ap.add_argument("--tuning-json", default=None, help="knob values (JSON object) set on the plan, no autotuning")

@@ -27,6 +27,7 @@ template <typename T> int pipe_blocks_per_sm(int, size_t);
 template <typename T> int plane_cluster_capacity(int, size_t);
 template <typename T> int lines_blocks_per_sm(int, int, size_t);
 template <typename T> int wlines_blocks_per_sm(int, int, size_t);
+template <typename T> int update_vec_blocks_per_sm();
 template <typename T> void launch_init(const Ctx<T>&, cudaStream_t);
 template <typename T> void launch_iteration(const Ctx<T>&, cudaStream_t);
 template <typename T> void launch_iteration_range(const Ctx<T>&, int, int, cudaStream_t);
@@ -249,6 +250,7 @@ int shape_for(const ccmf_plan* pl, const ccmf_tuning& t, LaunchShape* out, ccmf_
     long long gu = (pl->g.N + kThreads - 1) / kThreads;
     if (gu > 608) gu = 608;
     sh.grid_update = (int)gu;
+    sh.vec_resident = (f64 ? update_vec_blocks_per_sm<double>() : update_vec_blocks_per_sm<float>()) * sms;
     // TMA-staged update: tiles of J z rows with J * N3 <= 512 (FP32) / 256 (FP64) voxels,
     // J a power of two dividing N2; two stages must fit the shared memory of a block
     const int tv_max = f64 ? 256 : 512;

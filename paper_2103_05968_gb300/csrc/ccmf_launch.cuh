@@ -165,6 +165,20 @@ int lines_blocks_per_sm(int mode, int lines, size_t smem) {
     return nb;
 }
 
+// Resident blocks per SM of the vector update pass (the smaller of the advancing and
+// the final-evaluation kernels), at least 1.
+template <typename T>
+int update_vec_blocks_per_sm() {
+    int a = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_update_vec<T, false>, kThreads, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_update_vec<T, true>, kThreads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    const int m = a < b ? a : b;
+    return m < 1 ? 1 : m;
+}
+
 // Blocks per SM of a warp-per-line pass of length n (power of two 128 ... 1024), 0 on error.
 template <typename T>
 int wlines_blocks_per_sm(int mode, int n, size_t smem) {
@@ -302,6 +316,10 @@ void launch_passes(const Ctx<T>& c, const Ptrs<T>& p, cudaStream_t st, F&& betwe
     dim3 gwy((unsigned)twy, (unsigned)g.batch);
     dim3 gwx((unsigned)twx, (unsigned)g.batch);
     dim3 gu((unsigned)sh.grid_update, (unsigned)g.batch);
+    // the vector update pass takes its chunks from a ticket counter: the resident blocks, shared
+    // by the solves of this launch, so that every solve's chunks run at once on all SMs
+    const int vpb = sh.vec_resident > 0 ? sh.vec_resident / g.batch : sh.grid_update;
+    const dim3 gv((unsigned)(vpb < 1 ? 1 : vpb), (unsigned)g.batch);
     const T inv_n = (T)(1.0 / (double)g.N);
     const dim3 gwz((unsigned)ceil_div((long long)g.n1 * g.n2, 2 * (kThreads / 32)), (unsigned)g.batch);
     if (sh.wzd && c.vec_div) {
@@ -372,7 +390,7 @@ void launch_passes(const Ctx<T>& c, const Ptrs<T>& p, cudaStream_t st, F&& betwe
     }
     between(kKIrfftZ);
     if (OUT && c.vec_update && vec_out_ok(p))
-        k_update_vec<T, true><<<gu, kThreads, 0, st>>>(g, p, c.cfg);
+        k_update_vec<T, true><<<gv, kThreads, 0, st>>>(g, p, c.cfg);
     else if (OUT)
         k_update<T, true><<<gu, kThreads, 0, st>>>(g, p, c.cfg);
     else if (c.vec_update && sh.upd_variant >= 2) {
@@ -395,7 +413,7 @@ void launch_passes(const Ctx<T>& c, const Ptrs<T>& p, cudaStream_t st, F&& betwe
             k_update_tma<T, 1><<<gt, kThreads, sh.smem_tma, st>>>(g, p, c.cfg, sh.tma_rows);
     }
     else if (c.vec_update)
-        k_update_vec<T, false><<<gu, kThreads, 0, st>>>(g, p, c.cfg);
+        k_update_vec<T, false><<<gv, kThreads, 0, st>>>(g, p, c.cfg);
     else
         k_update<T, false><<<gu, kThreads, 0, st>>>(g, p, c.cfg);
     between(kKUpdate);

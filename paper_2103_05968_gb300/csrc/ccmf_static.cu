@@ -164,6 +164,7 @@ int static_solve(int n1, int n2, int n3, const T* gamma, const double* xi_bar, c
     sh.smem_x = ((size_t)n1 + 2 * (size_t)n1 * (sh.lpb_x + 1)) * cs;
     long long gu = (g.N + kThreads - 1) / kThreads;
     sh.grid_update = (int)(gu < kStaticGridUpdate ? gu : kStaticGridUpdate);
+    sh.vec_resident = 0;   // the vector update pass runs grid_update blocks per solve
 
     // scratch layout: scalars, counter, normal, partials, history, state (two copies),
     // spectrum, phi, tables

@@ -96,6 +96,7 @@ struct LaunchShape {
     size_t smem_zi;           // its dynamic shared memory
     int lpb_y, lpb_x;         // strided passes: lines per block
     int grid_update;          // blocks per solve of the voxel passes
+    int vec_resident;         // resident blocks of the vector update pass on the whole GPU
     size_t smem_z, smem_y, smem_x;
     int tma_rows;             // TMA-staged update: z rows per tile (0 = path not available)
     int grid_tma;             // blocks per solve of the TMA-staged update

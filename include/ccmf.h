@@ -196,12 +196,13 @@ int ccmf_plan_launch_info(const ccmf_plan* plan, int* out, int capacity, int* co
  * In ccmf_plan_set_tuning a negative entry selects the built-in rule.
  */
 typedef struct {
-    int update_variant;     /* update pass: 0 register vectors, 1 TMA rows, 2..7 pipelined TMA */
+    int update_variant;     /* update pass: 0 register vectors in ticket-ordered chunks, 1 TMA rows,
+                               2..7 pipelined TMA */
     int plane_blocks;       /* y / x passes: 0 three strided passes, 1 one block per (x, y) plane,
                                2, 4, 8, 16 a thread-block cluster per plane */
     int z_pairs_per_block;  /* divergence + forward z pass: line pairs per block, power of two 1..16 */
-    int y_lines_per_block;  /* strided y passes: lines per block, power of two 1..16 */
-    int x_lines_per_block;  /* strided x pass: lines per block, power of two 1..16 */
+    int y_lines_per_block;  /* strided y passes, line engine 0: lines per block, power of two 1..16 */
+    int x_lines_per_block;  /* strided x pass, line engine 0: lines per block, power of two 1..16 */
     int branches;           /* independent graph branches of a batch, 1..4 */
     int radix_mode;         /* radix schedule of every axis: 0 radix 8 first, then 4, 2, 3, 5;
                                1 as 0 but radix 4s in place of a radix 8 + 2 tail; 2 radix 4 at most */

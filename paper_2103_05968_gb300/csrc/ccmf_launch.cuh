@@ -309,7 +309,7 @@ void launch_passes(const Ctx<T>& c, const Ptrs<T>& p, cudaStream_t st, F&& betwe
     if (sh.grid_x > 0 && sh.grid_x < tx) tx = sh.grid_x;
     dim3 gy((unsigned)ty, (unsigned)g.batch);
     dim3 gx((unsigned)tx, (unsigned)g.batch);
-    constexpr int kWarpLines = kThreads / 32;   // lines per tile of the warp-per-line passes
+    constexpr int kWarpLines = kThreads / 32;   // lines per block round of the warp-per-line passes
     long long twy = ceil_div((long long)g.n1 * g.n3h, kWarpLines), twx = ceil_div((long long)g.n2 * g.n3h, kWarpLines);
     if (sh.grid_y > 0 && sh.grid_y < twy) twy = sh.grid_y;
     if (sh.grid_x > 0 && sh.grid_x < twx) twx = sh.grid_x;

@@ -136,6 +136,9 @@ int ccmf_plan_workspace_bytes(const ccmf_plan* plan, size_t* bytes);
  * The loop runs on the device; the host only relaunches a captured CUDA graph
  * of params->check_every updates and reads one counter between chunks (no
  * host round trip in fixed_iters mode).
+ * Every reduction sums in a fixed order (per block or per work chunk, then by the
+ * last block in index order), so repeated solves with the same plan, tuning and
+ * inputs give bit-identical results, whatever the order the blocks ran in.
  */
 int ccmf_solve(ccmf_plan* plan, const void* gamma, long long gamma_stride, const double* xi_bar,
                const ccmf_params* params, void* workspace, size_t workspace_bytes,

@@ -5,7 +5,10 @@ j = lane + 32 b of the pass at sub-transform length Ns reads elements j + r N/R 
 od + r Ns, od = (j - j mod Ns) R + j mod Ns, at padded positions wpad(i) = i + i / 16. These
 tests re-derive the kernels' offset formulas and check them against wpad of the plain index for
 every lane, butterfly and radix of the lengths the warp engine takes (128 ... 1024), plus the
-per-pass twiddle table and the register hand-off between two transforms."""
+per-pass twiddle table and the register hand-off between two transforms, and run the passes in
+numpy with those index formulas to check that they compute the DFT."""
+
+import numpy as np
 
 
 def wpad(i):
@@ -146,3 +149,50 @@ def test_half_warp_bank_groups():
                     assert wavefronts(loads) == 2
                     expect = {8: 4, 4: 8}.get(ns, 2)
                     assert wavefronts(stores) == expect, (n, ns, q)
+
+
+def _twiddle_table(n):
+    """The per-pass table as the kernels fill it: entry OFF + q of the pass at Ns holds
+    W_N^{(q mod Ns)(1 + q div Ns) N / (Ns R)}, W_N = exp(-2 pi i / N)."""
+    table = {}
+    off = 0
+    for ns, r in passes(n):
+        if ns == 1:
+            continue
+        tws = n // (ns * r)
+        for q in range((r - 1) * ns):
+            table[off + q] = (q % ns) * (1 + q // ns) * tws
+        off += (r - 1) * ns
+    return {k: np.exp(-2j * np.pi * e / n) for k, e in table.items()}
+
+
+def test_stockham_passes_compute_the_dft():
+    """Run the warp Stockham passes in numpy with the kernels' index formulas (lane, butterfly,
+    radix, per-pass twiddle lookups); the result is the DFT of the input line."""
+    rng = np.random.default_rng(5)
+    for n in LENGTHS:
+        tw = _twiddle_table(n)
+        x0 = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+        x = x0.copy()
+        off = 0
+        for ns, r in passes(n):
+            nb = n // r
+            out = np.empty_like(x)
+            for lane in range(32):
+                for b in range(nb // 32):
+                    j = lane + 32 * b
+                    vals = np.array([x[j + q * nb] for q in range(r)])
+                    if ns > 1:
+                        base = off + ((lane & (ns - 1)) if ns <= 32 else lane)
+                        jb = 0 if ns <= 32 else ((32 * b) & (ns - 1))
+                        for q in range(1, r):
+                            vals[q] *= tw[base + jb + (q - 1) * ns]
+                    vals = np.fft.fft(vals)   # the radix-R butterfly, forward kernel
+                    jm = j & (ns - 1)
+                    od = (j - jm) * r + jm
+                    for q in range(r):
+                        out[od + q * ns] = vals[q]
+            x = out
+            if ns > 1:
+                off += (r - 1) * ns
+        np.testing.assert_allclose(x, np.fft.fft(x0), rtol=0, atol=1e-9 * np.sqrt(n))

@@ -50,6 +50,39 @@ Readings where the paper is silent (each one is listed in the design notes):
      reference to He et al.): primal residual r = |e^k - xi^{k+1/2}| (Eq. 31),
      dual residual s = rho^k |e^{k+1} - e^k|; rho * s_max if r > 10 s, rho / s_max
      if s > 10 r, else rho (s_max = rho_step_max).
+
+Pins: what fixes each function independently of itself (tests/), and the planted
+mistake (tests/test_oracle_mutations.py) that the pin catches.
+  shift_back, shift_forward  S*S = Id, <Su, w> = <u, S*w>; face form of Eq. 6/7 equals
+                             Eq. 10 (test_oracle_operators) -- wrong shift direction
+  op_A, op_A_adj             A*A = Id, AA* a projector (test_oracle_operators); homogeneous
+                             gamma_eff = gamma for oblique normals -- missing 1/sqrt2; dense
+                             barrier max-flow (test_oracle_solver) -- unshifted A*
+  div_minus, grad_plus       <grad^+ phi, u> = -<phi, div^- u>; face-form divergence B f
+                             (test_oracle_operators) -- backward gradient
+  laplacian_symbol, _pinv    real-space Laplacian by rolls on odd and radix-3/5 grids
+                             (test_oracle_operators) -- symbol without its factor 4
+  op_Gamma, op_M, project_K  Gamma a self-adjoint projector fixing gradients; P_K(w) in K,
+                             idempotent, the nearest point (test_oracle_operators); the
+                             column closed form of P_K (test_oracle_trajectory)
+  project_C                  feasible, idempotent, nearest point (test_oracle_operators);
+                             dense barrier agreement -- no clip
+  admm_step                  one step of Eq. 30 on a 1 x 1 x 2 column against literal
+                             values, random columns against the column closed form, and
+                             delta = 1/2 against the undamped scheme (test_oracle_trajectory)
+                             -- delta swapped with 1 - delta, relaxation dropped
+  next_rho                   BB and LTD ratios, the R3 safeguard and clamp on hand-made
+                             fields with literal values; residual-balancing direction
+                             (test_oracle_trajectory, test_oracle_solver) -- the other BB
+                             step |dv|^2/<dv,de>, LTD inverted
+  solve, evaluate            homogeneous, laminate, axis-normal bounds, config-1 exact value
+                             0.8171875, the paper's Sec. 4.2 result, dense barrier
+                             max-flow on 2x3x5 ... 8^3 grids, strong duality, equivariances
+                             (test_oracle_solver)
+  mincut_objective,          both estimates bracket and converge to the dense barrier value
+  flow_objective             and the closed forms (test_oracle_solver)
+  initial_rho                R2 is a reading; gamma -> 2 gamma equivariance with rho^0
+                             proportional to gamma (test_oracle_solver)
 """
 
 from __future__ import annotations

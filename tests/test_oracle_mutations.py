@@ -38,13 +38,76 @@ def _homogeneous_pin_holds():
     return abs(r.gamma_eff - 1.3) < 1e-7 and abs(r.gamma_primal - 1.3) < 1e-7
 
 
+def _column_step_pin_holds():
+    """The literal single step of Eq. 30 on the two-voxel column (test_oracle_trajectory)."""
+    r2 = 0.5 ** 0.5
+    e = np.array([[1.0, 0.0], [0.0, 0.0], [0.5, -0.5], [0.0, 1.0], [0.0, 0.0], [0.5, 1.5]]).reshape(6, 1, 1, 2)
+    c = 1.5 * r2
+    v_lit0 = np.array([0.25, 0.0, c - 0.25, -0.75, 0.0, c - 0.25])   # voxel 0: z unclipped
+    half, _, v_new = O.admm_step(e, np.zeros_like(e), 1.0, np.array([100.0, 0.5]).reshape(1, 1, 2),
+                                 np.array([0.0, 0.0, 1.0]), 0.25)
+    ok_half = np.allclose(half.reshape(6, 2)[:, 0], [0.5, 0.0, r2, -0.5, 0.0, r2], atol=1e-14)
+    return ok_half and np.allclose(v_new.reshape(6, 2)[:, 0], v_lit0, atol=1e-14)
+
+
+def _bb_ratio_pin_holds():
+    """de = (1, 0, ..), dv = (1, 1, ..) per voxel: <dv, de> / |de|^2 = 1 (test_oracle_trajectory)."""
+    one = np.zeros((6, 2, 1, 2))
+    one[0] = 1.0
+    dv = one.copy()
+    dv[1] = 1.0
+    z = np.zeros_like(one)
+    return abs(O.next_rho(0.8, O.RHO_BB, z, one, z, dv, O.Params()) - 1.0) < 1e-15
+
+
+def _ltd_ratio_pin_holds():
+    """|v| = 1, |e| = 2 per voxel: |v| / |e| = 0.5 (test_oracle_trajectory)."""
+    e = np.zeros((6, 2, 1, 2))
+    e[1] = 2.0
+    v = np.zeros_like(e)
+    v[0], v[5] = 0.6, 0.8
+    z = np.zeros_like(e)
+    return abs(O.next_rho(0.7, O.RHO_LTD, z, e, z, v, O.Params()) - 0.5) < 1e-15
+
+
 def _laplacian_pin_holds():
     d = np.random.default_rng(2).standard_normal((5, 6, 7))
     d -= d.mean()
     return np.allclose(O.div_minus(O.grad_plus(O.laplacian_pinv(d))), d, atol=1e-10)
 
 
+_admm_step = O.admm_step
+_next_rho = O.next_rho
+
+
+def _next_rho_other_bb(rho, rule, e_old, e_new, v_old, v_new, params, primal_res=None):
+    """The other Barzilai-Borwein step |dv|^2 / <dv, de> in place of <dv, de> / |de|^2."""
+    if rule != O.RHO_BB:
+        return _next_rho(rho, rule, e_old, e_new, v_old, v_new, params, primal_res)
+    de, dv = e_new - e_old, v_new - v_old
+    s_ve, s_ee, s_vv = O.inner(dv, de), O.inner(de, de), O.inner(dv, dv)
+    if s_ve > 0.0 and s_ee > 0.0 and s_vv > 0.0 and s_ve / np.sqrt(s_vv * s_ee) > params.bb_corr_min:
+        return min(max(s_vv / s_ve, rho / params.rho_step_max), rho * params.rho_step_max)
+    return rho
+
+
+def _next_rho_ltd_inverted(rho, rule, e_old, e_new, v_old, v_new, params, primal_res=None):
+    """Lorenz-Tran-Dinh as |e| / |v| instead of |v| / |e|."""
+    if rule != O.RHO_LTD:
+        return _next_rho(rho, rule, e_old, e_new, v_old, v_new, params, primal_res)
+    nv, ne = O.l2_norm(v_new), O.l2_norm(e_new)
+    if nv > 0.0 and ne > 0.0:
+        return min(max(ne / nv, rho / params.rho_step_max), rho * params.rho_step_max)
+    return rho
+
+
 MUTATIONS = {
+    "relaxation_delta_swapped": ("admm_step", lambda e, v, rho, g, xi, delta: _admm_step(e, v, rho, g, xi, 1.0 - delta),
+                                 _column_step_pin_holds),
+    "relaxation_dropped": ("admm_step", lambda e, v, rho, g, xi, delta: _admm_step(e, v, rho, g, xi, 0.5),
+                           _column_step_pin_holds),
+    "bb_other_step": ("next_rho", _next_rho_other_bb, _bb_ratio_pin_holds),
+    "ltd_inverted": ("next_rho", _next_rho_ltd_inverted, _ltd_ratio_pin_holds),
     "shift_back_wrong_direction": ("shift_back", lambda u: np.stack([np.roll(u[a], -1, axis=a) for a in range(3)]),
                                    _face_pin_holds),
     "A_missing_sqrt_half": ("op_A", lambda u: np.concatenate([u, O.shift_back(u)]), _homogeneous_pin_holds),

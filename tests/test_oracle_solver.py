@@ -57,6 +57,18 @@ def test_dense_barrier_agreement(seed, xi):
     assert abs(r.gamma_primal - val) <= 1e-8 * val + gap
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("n,seed,xi", [(6, 41, [0.3, -0.5, 0.8]), (8, 42, [0.0, 0.0, 1.0])])
+def test_dense_barrier_agreement_6_and_8(n, seed, xi):
+    """The same agreement on 6^3 and 8^3 grids (648 and 1536 face unknowns)."""
+    g = M.uniform_random((n, n, n), 0.5, 2.0, seed)
+    val, _, gap = D.max_flow(g, xi, gap_tol=1e-9)
+    r = O.solve(g, xi, O.Params(tol=1e-10, max_iter=200000), record_history=False)
+    assert r.converged
+    assert abs(r.gamma_eff - val) <= 1e-8 * val + gap
+    assert abs(r.gamma_primal - val) <= 1e-8 * val + gap
+
+
 def test_dense_barrier_anisotropic_grid():
     g = M.random_two_phase((2, 3, 5), 0.4, 0.2, 1.0, 6)
     xi = [0.2, 0.4, -0.9]

@@ -348,11 +348,10 @@ int ccmf_batch_solve(ccmf_batch* batch, const void* const* gammas, const double*
  * ccmf_solve_static - one solve (batch 1) that allocates no memory.
  *
  * The paper has no counterpart: this entry point exists for callers that cannot
- * allocate device memory where they need a solve, for example code running while
- * one of its own streams is being captured into a CUDA graph (cudaMalloc is not
- * allowed there), plug-ins whose host application owns all device memory through
- * its own pool, or latency-critical paths that must avoid the implicit device
- * synchronisation of cudaMalloc and cudaFree. It needs no plan and no workspace:
+ * allocate device memory where they need a solve, for example plug-ins whose host
+ * application owns all device memory through its own pool (an allocation of theirs
+ * would fail or fragment that pool), or latency-critical paths that must avoid the
+ * implicit device synchronisation of cudaMalloc and cudaFree. It needs no plan and no workspace:
  * its state, spectra, reduction partials, history and FFT tables live in the
  * library's fixed scratch area of CCMF_STATIC_SCRATCH_BYTES bytes, and it calls no
  * cudaMalloc, cudaFree or other allocating routine.
@@ -369,10 +368,13 @@ int ccmf_batch_solve(ccmf_batch* batch, const void* const* gammas, const double*
  * Returns CCMF_OK or an error code; per-solve failures are in result->status.
  *
  * The first call on a device looks up the device address of the scratch area
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture. Kernels are launched directly on `stream` (no graph); with a
- * tolerance (fixed_iters = 0) the host reads a counter from the device every
- * check_every updates. Every call on a device shares the one scratch area and
+ * (cudaGetSymbolAddress) with that device current, once per device (thread-safe);
+ * the address belongs to the device's primary context, so the entry point must not
+ * be used on a device after a cudaDeviceReset of it. Kernels are launched directly
+ * on `stream` (no graph). The call copies the unit normal from host memory with
+ * cudaMemcpyAsync; with a tolerance (fixed_iters = 0) the host reads a counter from
+ * the device every check_every updates, and with a non-NULL result it synchronises
+ * the stream before returning. Every call on a device shares the one scratch area and
  * overwrites what the previous call left there: calls whose GPU work overlaps in
  * time (other streams, other host threads) race with each other and must be
  * serialised by the caller.

@@ -2,13 +2,17 @@
 //
 // Every other entry point of this library takes a workspace that the caller
 // allocated, and ccmf_plan_create allocates small tables. Some callers cannot
-// allocate device memory at the point where they need a solve: code that runs
-// while one of their streams is being captured into a CUDA graph (cudaMalloc is
-// not allowed there), plug-ins whose host application owns the whole device
-// memory through its own pool, and latency-critical paths that must not take the
-// implicit device synchronisation of cudaMalloc / cudaFree. For them this file
-// keeps a fixed scratch area in a file-scope __device__ array and runs one
-// single-normal solve on it; the caller still passes gamma and the outputs.
+// allocate device memory at the point where they need a solve: plug-ins whose
+// host application owns the whole device memory through its own pool (a
+// cudaMalloc of theirs would fail or fragment that pool), and latency-critical
+// paths that must not take the implicit device synchronisation of cudaMalloc /
+// cudaFree. For them this file keeps a fixed scratch area in a file-scope
+// __device__ array and runs one single-normal solve on it; the caller still
+// passes gamma and the outputs.
+//
+// The call copies the unit normal from host memory with cudaMemcpyAsync, and it
+// synchronises the stream when it stops on a tolerance (it reads an active
+// counter every check_every updates) or returns a result.
 //
 // The scratch array is part of the library image: every GPU that loads the
 // library holds kStaticScratchBytes of device memory for it until the process
@@ -18,6 +22,8 @@
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
+
+#include <mutex>
 
 #include "../../include/ccmf.h"
 #include "ccmf_launch.cuh"
@@ -46,6 +52,7 @@ static __device__ __align__(256) unsigned char g_ccmf_scratch[CCMF_STATIC_SCRATC
 namespace {
 
 unsigned char* g_scratch_ptr[kMaxDevices];   // device address of g_ccmf_scratch per device
+std::mutex g_scratch_mutex;                   // first calls from several host threads look it up once
 
 // Frequency held by slot p after the in-place decimation-in-frequency stages of
 // the radix schedule ap: k(p) = sum_s q_s prod_{t<s} R_t, q_s = (p / m_s) mod R_s.
@@ -121,9 +128,12 @@ int lines_for(int n, size_t cs) {
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
 // One-time set-up per device, with that device current: the device address of
-// the scratch array (host code cannot use the array's name as an address).
+// the scratch array (host code cannot use the array's name as an address). The
+// address belongs to the device's primary context; a cudaDeviceReset ends that
+// context, and ccmf_solve_static must not be called on the device afterwards.
 int static_setup(int dev, unsigned char** base) {
     if (dev < 0 || dev >= kMaxDevices) return CCMF_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
     if (!g_scratch_ptr[dev]) {
         void* ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_ccmf_scratch) != cudaSuccess || !ptr) return CCMF_ERR_CUDA;

@@ -1,8 +1,9 @@
 """The allocation-free entry point ccmf_solve_static against ccmf_solve.
 
 ccmf_solve_static serves callers that cannot allocate device memory where they
-need a solve (for example inside their own stream capture, or under a host
-application that owns all device memory): it keeps its whole working set in the
+need a solve (for example a plug-in under a host application that owns all device
+memory through its own pool, or a latency-critical path that must not take the
+implicit synchronisation of cudaMalloc): it keeps its whole working set in the
 library's fixed device scratch area instead of a caller-provided workspace.
 This test calls it through the C ABI twice in a row on different inputs (the
 second call reuses the scratch the first one left behind) and checks each call
@@ -44,11 +45,15 @@ def reference(gamma, xi, params, precision):
     return res[0], flow[0].cpu().numpy(), cut[0].cpu().numpy()
 
 
-def static_solve(gamma, xi, params, precision):
+def static_solve(gamma, xi, params, precision, gamma_offset=0):
+    """gamma_offset > 0 passes gamma as a view that starts that many elements into a
+    larger buffer (not 16-byte aligned: the scalar update pass)."""
     dt = torch.float64 if precision == ccmf.CCMF_FP64 else torch.float32
     n1, n2, n3 = gamma.shape
     with torch.cuda.device(DEV):
-        g = torch.from_numpy(gamma).to(DEV, dt)
+        buf = torch.empty(gamma.size + gamma_offset, dtype=dt, device=DEV)
+        g = buf[gamma_offset:].view(gamma.shape)
+        g.copy_(torch.from_numpy(gamma).to(DEV, dt))
         flow = torch.empty((3, n1, n2, n3), dtype=dt, device=DEV)
         cut = torch.empty((6, n1, n2, n3), dtype=dt, device=DEV)
         res = ccmf.ccmf_result()
@@ -85,6 +90,41 @@ def test_static_matches_workspace_entry_point(precision):
         assert abs(r1["gamma_primal"] - r0["gamma_primal"]) <= geff_tol * abs(r0["gamma_primal"])
         np.testing.assert_allclose(f1, f0, rtol=0, atol=field_tol)
         np.testing.assert_allclose(c1, c0, rtol=0, atol=field_tol)
+
+
+EDGE_CASES = [
+    # the documented size limits (80^3 FP32, 64^3 FP64), an odd N3 (scalar divergence and
+    # update passes) and an offset gamma view (scalar update pass); the tolerance cases stop
+    # after more updates than check_every
+    ("limit_fp32", lambda: M.boolean_spheres((80, 80, 80), 4.0, 0.2, 0.3, 1.0, seed=4)[0], [0.0, 0.6, 0.8],
+     ccmf.Params(fixed_iters=60), ccmf.CCMF_FP32_MIXED, 0),
+    ("limit_fp64", lambda: M.boolean_spheres((64, 64, 64), 4.0, 0.2, 0.3, 1.0, seed=5)[0], [0.0, 0.0, 1.0],
+     ccmf.Params(tol=1e-4, check_every=16, max_iter=3000), ccmf.CCMF_FP64, 0),
+    ("odd_n3_fp64", lambda: M.boolean_spheres((18, 20, 15), 2.5, 0.2, 0.3, 1.0, seed=6)[0], [0.36, 0.48, 0.8],
+     ccmf.Params(tol=1e-6, check_every=5, max_iter=5000), ccmf.CCMF_FP64, 0),
+    ("offset_gamma_fp64", lambda: M.boolean_spheres((16, 24, 20), 2.5, 0.2, 0.3, 1.0, seed=7)[0], [1.0, 0.0, 0.0],
+     ccmf.Params(tol=1e-6, check_every=9, max_iter=5000), ccmf.CCMF_FP64, 1),
+    ("offset_gamma_fp32", lambda: M.boolean_spheres((16, 24, 20), 2.5, 0.2, 0.3, 1.0, seed=7)[0], [1.0, 0.0, 0.0],
+     ccmf.Params(fixed_iters=45), ccmf.CCMF_FP32_MIXED, 3),
+]
+
+
+@pytest.mark.parametrize("case", EDGE_CASES, ids=[c[0] for c in EDGE_CASES])
+def test_static_edge_cases_match_workspace_entry_point(case):
+    _, build, xi, params, precision, offset = case
+    gamma = build()
+    r0, f0, c0 = reference(gamma, xi, params, precision)
+    r1, f1, c1 = static_solve(gamma, xi, params, precision, gamma_offset=offset)
+    assert r1["status"] == 0 and r1["iters"] == r0["iters"] and r1["converged"] == r0["converged"]
+    if params.fixed_iters == 0:
+        assert r0["iters"] > params.check_every
+    if precision == ccmf.CCMF_FP64:
+        geff_tol, field_tol = 1e-10, 1e-9
+    else:
+        geff_tol, field_tol = 1e-5, 1e-4 * max(1.0, float(np.abs(c0).max()))
+    assert abs(r1["gamma_eff"] - r0["gamma_eff"]) <= geff_tol * abs(r0["gamma_eff"])
+    np.testing.assert_allclose(f1, f0, rtol=0, atol=field_tol)
+    np.testing.assert_allclose(c1, c0, rtol=0, atol=field_tol)
 
 
 def test_static_rejects_grids_beyond_the_scratch_area():

@@ -7,7 +7,13 @@ overlapping balls (radius 6 voxels, volume fraction 0.20, gamma 0.3 in balls /
 1.0 matrix) with the three crack normals e1, e2, e3 solved together (3 solves),
 FP32 fields with FP64 reductions.
 
-Output: one JSON line (rank 0). See the design doc for the definitions of every key.
+Output: one JSON line (rank 0). Besides the keys of the contract it carries
+`roofline` (dominant kernel against the measured HBM copy bandwidth, plus the
+whole step on the 132 B/voxel basis: read e, v, gamma, the spectrum and two
+stored divergences, write e, v, the spectrum and the divergences), `fibres512`
+(the same figures for one 512^3 short-fibre solve, when run on one GPU),
+`kernels`, `fp32_vs_fp64`, `cufft_yardstick` and `cpu_baseline` (the oracle on
+all host cores and on one).
 Multi-GPU runs (torchrun) are replicas: every rank solves the same workload on
 its own GPU; value = all ranks' voxel-iterations / slowest rank's time.
 """
@@ -114,7 +120,7 @@ def run_batch(args, world, rank, local):
     clk = clocks.stop()
     value = world * vox * K / (t_ms * 1e-3)
     peak, peak_kind = load_peaks()
-    step_bytes = vox * (12 * esize + 2 * esize + 12 * esize + 12 * esize + 6 * esize)
+    step_bytes = vox * basis_bytes_per_voxel(esize)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
                 "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -124,11 +130,21 @@ def run_batch(args, world, rank, local):
                            "l2": "inputs larger than L2"},
                 "roofline": {"bound": "hbm", "achieved": step_bytes / (t_ms / K * 1e-3) / 1e9, "peak": peak,
                              "unit": "GB/s", "frac": step_bytes / (t_ms / K * 1e-3) / 1e9 / peak,
-                             "traffic": None, "kernel": "whole step (196 B/voxel FP32 basis)",
+                             "traffic": None,
+                             "kernel": f"whole step ({basis_bytes_per_voxel(esize)} B/voxel basis)",
                              "peak_kind": peak_kind},
                 "autotune": tune, "clocks": clk}
         print(json.dumps(line), flush=True)
     batch.close()
+
+
+def basis_bytes_per_voxel(esize):
+    """Algorithmic HBM bytes of one ADMM iteration per voxel in the three-pass schedule:
+    pass 1 reads two stored divergences a = div^- A* e, b = div^- A* v (2 esize) and writes
+    the half spectrum (esize), pass 2 reads and writes it (2 esize), pass 3 reads it (esize)
+    and e, v, gamma (13 esize) and writes e, v and the divergences (14 esize): 33 esize,
+    i.e. 132 B in FP32 and 264 B in FP64."""
+    return 33 * esize
 
 
 def bytes_per_voxel(kernel, esize, n3):
@@ -145,19 +161,19 @@ def bytes_per_voxel(kernel, esize, n3):
     }[kernel]
 
 
-def load_traffic(kernel, workload, precision):
+def load_traffic(kernel, workload, precision, with_source=False):
     """DRAM bytes per launch of a kernel from the committed ncu summaries (profiles/*.md),
     or None when no capture of this kernel, workload and precision is recorded. The
     update pass is keyed with its variant (k_update@v<variant>), so a figure measured on
-    one variant is never reported for another."""
+    one variant is never reported for another. with_source: also return the file name."""
     import glob
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         for line in open(path):
             parts = line.split()
             if len(parts) == 5 and parts[0] == "dram_bytes_per_launch" and parts[1:4] == [kernel, workload,
                                                                                            precision]:
-                return float(parts[4])
-    return None
+                return (float(parts[4]), os.path.basename(path)) if with_source else float(parts[4])
+    return (None, None) if with_source else None
 
 
 def load_peaks():
@@ -330,6 +346,72 @@ def time_to_accuracy(gamma_np, normals, dev, rel=1e-5, ref_tol=1e-7, max_iter=40
     return out
 
 
+def call_ms(plan, gamma_dev, normals, iters):
+    """Device time of one ccmf_solve call of `iters` iterations from the current state
+    (init statistics, the captured loop, the final evaluation), CUDA events on the
+    launching stream, after an untimed call that captures the graph."""
+    import torch
+    from paper_2103_05968_gb300 import ccmf
+    p = ccmf.Params(fixed_iters=iters, check_every=iters, resume=1)
+    plan.solve(gamma_dev, normals, p, want_results=False)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(gamma_dev.device)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    plan.solve(gamma_dev, normals, p, want_results=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1)
+
+
+def fibres512_record(args, dev):
+    """The 512^3 short-fibre workload (one solve, normal e3, FP32-mixed) measured beside
+    the default line: ms per step of a K-step call (init, K iterations, final
+    evaluation), ms per iteration from the difference of a 2K- and a K-step call
+    (the per-call work cancels), both on the 132 B/voxel basis, and the dominant kernel
+    of a sequential event-timed pass against the measured HBM bandwidth."""
+    import torch
+    from paper_2103_05968_gb300 import ccmf
+    t_set = time.perf_counter()
+    gamma_np = make_gamma("fibres512", np.float32)
+    normals = np.asarray(WORKLOADS["fibres512"]["normals"], dtype=np.float64)
+    N = gamma_np.size
+    plan = ccmf.Plan(gamma_np.shape, batch=1, precision=ccmf.CCMF_FP32_MIXED, device=dev)
+    gamma_dev = torch.from_numpy(gamma_np).to(dev)
+    del gamma_np
+    K = max(args.steps, 20)
+    plan.solve(gamma_dev, normals, ccmf.Params(fixed_iters=args.warmup, check_every=args.warmup))
+    tune = None
+    if not args.no_autotune:
+        best, tune_ms = plan.autotune(gamma_dev, normals, iters=max(10, args.tune_iters // 2))
+        tune = {"tuning": best, "ms_per_iter": tune_ms}
+    setup_s = time.perf_counter() - t_set
+    t_k = call_ms(plan, gamma_dev, normals, K)
+    t_2k = call_ms(plan, gamma_dev, normals, 2 * K)
+    plan.set_kernel_timing(True)
+    call_ms(plan, gamma_dev, normals, K)
+    kt = {k: v for k, v in plan.kernel_times().items() if v[1] > 0}
+    plan.set_kernel_timing(False)
+    peak, peak_kind = load_peaks()
+    dom = max(kt, key=lambda k: kt[k][0])
+    dom_ms = kt[dom][0] / kt[dom][1]
+    dom_bytes = bytes_per_voxel(dom, 4, 512) * N
+    basis = basis_bytes_per_voxel(4) * N
+    ms_step, ms_iter = t_k / K, (t_2k - t_k) / K
+    plan.close()
+    return {"workload": WORKLOADS["fibres512"]["desc"] + " FP32-mixed (FP64 reductions)", "steps": K,
+            "ms_per_step": ms_step, "value": N * K / (t_k * 1e-3), "unit": UNIT,
+            "step_frac_132": basis / (ms_step * 1e-3) / 1e9 / peak,
+            "ms_per_iter": ms_iter, "iter_frac_132": basis / (ms_iter * 1e-3) / 1e9 / peak,
+            "target_ms_per_iter_at_0.60": basis / (0.60 * peak * 1e9) * 1e3,
+            "dominant_kernel": {"kernel": dom, "ms_per_launch": dom_ms,
+                                "achieved_gbs": dom_bytes / (dom_ms * 1e-3) / 1e9,
+                                "frac": dom_bytes / (dom_ms * 1e-3) / 1e9 / peak},
+            "kernels_ms_per_launch": {k: v[0] / v[1] for k, v in kt.items()},
+            "peak": peak, "peak_kind": peak_kind, "autotune": tune, "setup_seconds": setup_s,
+            "l2": "inputs larger than L2: state 6.4 GB per step"}
+
+
 def cufft_yardstick(shape, B, dev, reps=20):
     """cuFFT (torch.fft) R2C + C2R of the same B scalar grids: a yardstick beside the
     solver's own FFT passes, not used by the solver."""
@@ -349,9 +431,10 @@ def cufft_yardstick(shape, B, dev, reps=20):
     return ev0.elapsed_time(ev1) / reps
 
 
-def cpu_baseline(name, max_seconds=20.0):
-    """The oracle as it stands on the host cores: a bounded sample of the workload
-    (one solve of the same grid, as many iterations as fit in about max_seconds)."""
+def _oracle_sample(name, max_seconds, max_iters=50):
+    """A bounded sample of the oracle as it stands: FP64 iterations of one solve of the
+    workload's grid (128^3 corner block of larger grids) until max_seconds or max_iters.
+    Returns (voxel-iterations, wall seconds, CPU seconds, iterations, grid shape)."""
     from oracle import ccmf_oracle as O
     wl = WORKLOADS[name]
     gamma = make_gamma(name, np.float64) if name == "boolean128" else None
@@ -368,14 +451,71 @@ def cpu_baseline(name, max_seconds=20.0):
         rho = O.next_rho(rho, O.RHO_BB, e, e2, v, v2, O.Params())
         e, v = e2, v2
         iters += 1
-        if time.perf_counter() - t0 > max_seconds or iters >= 50:
+        if time.perf_counter() - t0 > max_seconds or iters >= max_iters:
             break
     wall = time.perf_counter() - t0
-    cpu = time.process_time() - c0
-    value = gamma.size * iters / wall
-    return {"value": value, "unit": UNIT, "cores": max(1, round(cpu / wall)), "kind": "oracle",
-            "sample": f"{iters} FP64 oracle iterations of one solve ({gamma.shape[0]}^3, normal "
-                      f"{wl['normals'][0]}) in {wall:.1f} s wall / {cpu:.1f} s CPU"}
+    return gamma.size * iters, wall, time.process_time() - c0, iters, gamma.shape
+
+
+def _oracle_worker(args):
+    import os as _os
+    _os.environ.setdefault("OMP_NUM_THREADS", "1")
+    name, max_seconds, max_iters = args
+    return _oracle_sample(name, max_seconds, max_iters)
+
+
+def host_cpu():
+    """(usable cores, CPU model string) of this host."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        cores = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+    return cores, f"{model or 'unknown'} ({platform.machine()})"
+
+
+def cpu_baseline(name, max_seconds=20.0):
+    """The oracle as it stands on the host cores, on a bounded sample of the workload:
+    one process per usable core, each running FP64 iterations of one solve of the same
+    grid for about max_seconds (throughput = all processes' voxel-iterations / wall
+    time), then the same on one core. The processes are spawned, not forked, so a CUDA
+    context of this process is never copied."""
+    import multiprocessing as mp
+    cores, model = host_cpu()
+    one_vox, one_wall, one_cpu, one_it, shape = _oracle_sample(name, max_seconds)
+    one = {"value": one_vox / one_wall, "unit": UNIT, "cores": 1, "iters": one_it,
+           "sample": f"{one_it} FP64 oracle iterations of one solve ({shape[0]}^3) in {one_wall:.1f} s wall / "
+                     f"{one_cpu:.1f} s CPU"}
+    workers = max(1, min(cores, 64))
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(workers) as pool:
+        outs = pool.map(_oracle_worker, [(name, max_seconds, 50)] * workers)
+    wall = time.perf_counter() - t0
+    iters = sum(o[3] for o in outs)
+    rate = sum(o[0] / o[1] for o in outs)   # the processes iterate concurrently
+    return {"value": rate, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": f"{workers} concurrent processes, each running FP64 oracle iterations of one solve "
+                      f"({shape[0]}^3, normal {WORKLOADS[name]['normals'][0]}) for about {max_seconds:.0f} s: "
+                      f"{iters} iterations; value = sum of the per-process rates ({wall:.1f} s wall with "
+                      f"process start-up and field generation)",
+            "nproc": cores, "cpu_model": model, "one_core": one}
 
 
 def run_reference(args, world, rank):
@@ -520,17 +660,24 @@ def run_gpu(args, world, rank, local):
     kern = {k: {"ms_per_launch": ms / n, "launches": n, "share": ms / sum(x[0] for x in kt.values()),
                 "gbs": bytes_per_voxel(k, esize, n3) * N * B / (ms / n * 1e-3) / 1e9}
             for k, (ms, n) in kt.items()}
-    step_bytes = sum(bytes_per_voxel(k, esize, n3) for k in kt) * N * B
+    own_bpv = sum(bytes_per_voxel(k, esize, n3) for k in kt)
     tuned = plan.tuning()
     traffic_key = f"{dom}@v{tuned['update_variant']}" if dom == "k_update" else dom
+    traffic, traffic_src = (None, None) if args.grid else load_traffic(traffic_key, name, args.precision,
+                                                                       with_source=True)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": load_traffic(traffic_key, name, args.precision) if not args.grid else None,
+                "traffic": traffic,
+                "traffic_source": (f"ncu capture summarised in profiles/{traffic_src} (not this run)"
+                                   if traffic_src else None),
                 "kernel": traffic_key, "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": per_launch_bytes,
                 "kernel_times_from": f"sequential event-timed pass of the same {K} steps "
                                      f"({t_seq_ms / K:.4f} ms/step)",
-                "step_frac": step_bytes / (t_ms / K * 1e-3) / 1e9 / peak,
-                "floor_100B_frac": (100 if esize == 4 else 200) * N * B / (t_ms / K * 1e-3) / 1e9 / peak}
+                "step_frac_132": basis_bytes_per_voxel(esize) * N * B / (t_ms_max / K * 1e-3) / 1e9 / peak,
+                "step_basis_bytes_per_voxel": basis_bytes_per_voxel(esize),
+                "step_frac_own_schedule": own_bpv * N * B / (t_ms_max / K * 1e-3) / 1e9 / peak,
+                "own_schedule_bytes_per_voxel": own_bpv,
+                "floor_100B_frac": (100 if esize == 4 else 200) * N * B / (t_ms_max / K * 1e-3) / 1e9 / peak}
 
     # end to end through the public API with host buffers: pinned gamma in, results out
     gamma_host = torch.from_numpy(gamma_np).pin_memory()
@@ -562,6 +709,11 @@ def run_gpu(args, world, rank, local):
     if rank == 0 and world == 1 and name == "boolean128" and esize == 4 and not args.no_speedup:
         tta = time_to_accuracy(gamma_np, normals, dev)
 
+    # the 512^3 workload beside the default line (one GPU)
+    fib = None
+    if rank == 0 and world == 1 and name == "boolean128" and not args.grid and not args.no_fibres512:
+        fib = fibres512_record(args, dev)
+
     # kernels launched in the timed region: per iteration one launch of each pass per graph
     # branch, plus setup and gamma statistics, plus the passes of the final evaluation
     nk = len(kt)
@@ -581,7 +733,7 @@ def run_gpu(args, world, rank, local):
                     "note": f"one ccmf_solve from pinned host gamma: H2D {esize * N} B, init, {K} iterations, "
                             "final evaluation, results D2H"},
                 "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
-                "fp32_vs_fp64": tta, "cufft_yardstick": yard, "autotune": tune,
+                "fp32_vs_fp64": tta, "cufft_yardstick": yard, "autotune": tune, "fibres512": fib,
                 "gamma_eff": [r["gamma_eff"] for r in res]}
         print(json.dumps(line), flush=True)
     plan.close()
@@ -603,6 +755,8 @@ def main():
     ap.add_argument("--tuning-out", default=None, help="write the tuning table text here after autotuning")
     ap.add_argument("--tuning-json", default=None, help="knob values (JSON object) set on the plan, no autotuning")
     ap.add_argument("--grid", default=None, help="N1xN2xN3 corner block of the workload's field (profiling cases)")
+    ap.add_argument("--no-fibres512", action="store_true",
+                    help="skip the 512^3 short-fibre record beside the default workload")
     ap.add_argument("--no-speedup", action="store_true",
                     help="skip the FP32-mixed vs FP64 time-to-accuracy measurement")
     args = ap.parse_args()

@@ -636,22 +636,32 @@ class Batch:
 def crack_energy(gamma, normal, plan, K, ckpt_every=20, params=None):
     """gamma_eff(normal) after K updates as a differentiable torch function of gamma.
 
-    The forward pass records the adaptive penalty schedule of K updates and returns
-    the max-flow value; the backward pass runs the library's reverse mode
-    (ccmf_adjoint) with that schedule held fixed.
+    The forward pass runs K updates with the adaptive penalty rule (ccmf_solve) and
+    records the penalty schedule from the history ring; it returns the max-flow value.
+    The reverse sweep runs only in the backward pass: the library's reverse mode
+    (ccmf_adjoint) replays the recorded schedule, so it differentiates the same map.
     """
     import torch
+
+    if K > 4096:
+        raise ValueError("crack_energy records the penalty schedule in the history ring: K <= 4096")
+    base = params or Params()
 
     class _CrackEnergy(torch.autograd.Function):
         @staticmethod
         def forward(ctx, g):
-            grad, res, rho = plan.gradient(g.detach().contiguous(), [normal], K, ckpt_every, params)
-            ctx.save_for_backward(grad)
+            gd = g.detach().contiguous()
+            rec = dataclasses.replace(base, fixed_iters=K, check_every=K, resume=0, history_len=K)
+            res, _, _ = plan.solve(gd, [normal], rec)
+            rho = plan.history(K)[0][:, 1].copy()
+            ctx.save_for_backward(gd)
+            ctx.rho = rho
             return torch.tensor(res[0]["gamma_eff"], dtype=g.dtype, device=g.device)
 
         @staticmethod
         def backward(ctx, gout):
-            (grad,) = ctx.saved_tensors
+            (gd,) = ctx.saved_tensors
+            grad, _, _ = plan.gradient(gd, [normal], K, ckpt_every, base, rho_schedule=ctx.rho[None, :])
             return gout * grad[0]
 
     return _CrackEnergy.apply(gamma)

@@ -103,16 +103,16 @@ def boolean_spheres(n, radius, volume_fraction, gamma_sphere, gamma_matrix, seed
     return g, count
 
 
-def _segment_distance_sq(p0, d0, P1, D1):
-    """Squared distances between the segment p0 + s d0 and the segments P1[i] + t D1[i]
-    (s, t in [0, 1]); P1, D1 have shape (m, 3). Closest points by the clamped
-    parameter formulas of two line segments."""
-    r = p0[None, :] - P1
-    a = float(d0 @ d0)
-    e = np.einsum("ij,ij->i", D1, D1)
-    f = np.einsum("ij,ij->i", D1, r)
-    c = r @ d0
-    b = D1 @ d0
+def _segment_distance_sq_pairs(P0, D0, P1, D1):
+    """Squared distances between the segments P0 + s D0 and P1 + t D1 (s, t in [0, 1]),
+    elementwise over broadcast leading axes (last axis: the 3 coordinates). Closest
+    points by the clamped parameter formulas of two line segments."""
+    r = P0 - P1
+    a = np.sum(D0 * D0, axis=-1)
+    e = np.sum(D1 * D1, axis=-1)
+    f = np.sum(D1 * r, axis=-1)
+    c = np.sum(r * D0, axis=-1)
+    b = np.sum(D1 * D0, axis=-1)
     denom = a * e - b * b
     safe = denom > 1e-14
     s = np.where(safe, np.clip((b * f - c * e) / np.where(safe, denom, 1.0), 0.0, 1.0), 0.0)
@@ -120,20 +120,22 @@ def _segment_distance_sq(p0, d0, P1, D1):
     low, high = t < 0.0, t > 1.0
     s = np.where(low, np.clip(-c / a, 0.0, 1.0), np.where(high, np.clip((b - c) / a, 0.0, 1.0), s))
     t = np.clip(t, 0.0, 1.0)
-    q = r + s[:, None] * d0[None, :] - t[:, None] * D1
-    return np.einsum("ij,ij->i", q, q)
+    q = r + s[..., None] * D0 - t[..., None] * D1
+    return np.sum(q * q, axis=-1)
 
 
 def short_fibres(n, diameter, aspect_ratio, volume_fraction, gamma_fibre, gamma_matrix,
-                 seed, max_attempts=2_000_000, dtype=np.float32):
+                 seed, max_attempts=2_000_000, dtype=np.float32, batch=512):
     """Straight cylinders (spherocylinder distance rule) by random sequential addition.
 
     Axis directions are isotropic on the sphere. A candidate is rejected if the
-    periodic segment-segment distance to any accepted fibre is below the
-    diameter (neighbours found through a cell list of side >= length + diameter).
-    Fibres are added until the voxel volume fraction first reaches
-    ``volume_fraction``; a voxel belongs to a fibre iff its centre lies within
-    radius of the axis segment (projected parameter clipped to the segment).
+    periodic segment-segment distance (nearest periodic image of the midpoints) to
+    any accepted fibre is below the diameter. Fibres are added until the voxel volume
+    fraction first reaches ``volume_fraction``; a voxel belongs to a fibre iff its
+    centre lies within radius of the axis segment (projected parameter clipped to
+    the segment). Candidates are drawn in batches (5 uniform numbers each: midpoint,
+    cos of the polar angle, azimuth) and tested against every accepted fibre at once,
+    then in turn against the fibres accepted earlier in the same batch.
     Returns (gamma, number_of_fibres).
     """
     n = np.asarray([int(m) for m in n], dtype=np.int64)
@@ -142,52 +144,47 @@ def short_fibres(n, diameter, aspect_ratio, volume_fraction, gamma_fibre, gamma_
     length = diameter * aspect_ratio
     mask = np.zeros(tuple(n), dtype=bool)
     total = float(np.prod(n))
-    cell = max(length + diameter, 1.0)
-    ncell = np.maximum((n / cell).astype(np.int64), 1)
-    cells = {}
-    cap = 1024
-    mids = np.zeros((cap, 3))
-    dirs = np.zeros((cap, 3))
+    nf = n.astype(np.float64)
+    mids = np.zeros((0, 3))
+    dirs = np.zeros((0, 3))
     count = 0
     filled = 0
     attempts = 0
-    nf = n.astype(np.float64)
-    # the distinct neighbour cells of each cell (3 x 3 x 3 with periodic wrap)
-    nbr = {}
-    for cx in range(ncell[0]):
-        for cy in range(ncell[1]):
-            for cz in range(ncell[2]):
-                nbr[(cx, cy, cz)] = sorted({((cx + dx) % ncell[0], (cy + dy) % ncell[1], (cz + dz) % ncell[2])
-                                            for dx in (-1, 0, 1) for dy in (-1, 0, 1) for dz in (-1, 0, 1)})
+    d2min = diameter * diameter
     while filled / total < volume_fraction:
-        attempts += 1
-        if attempts > max_attempts:
+        if attempts >= max_attempts:
             raise RuntimeError("fibre volume fraction not reachable")
-        mid = rng.random(3) * nf
-        z = rng.uniform(-1.0, 1.0)
-        phi = rng.uniform(0.0, 2.0 * math.pi)
-        s = math.sqrt(max(0.0, 1.0 - z * z))
-        d = np.array([s * math.cos(phi), s * math.sin(phi), z]) * length
-        key = tuple(int(x) for x in (mid / nf * ncell).astype(np.int64) % ncell)
-        lists = [cells[c] for c in nbr[key] if c in cells]
-        if lists:
-            ids = np.concatenate(lists) if len(lists) > 1 else lists[0]
-            Q = mids[ids]
-            D = dirs[ids]
-            # nearest periodic image of each neighbour's midpoint relative to the candidate
-            delta = _periodic_delta(mid[None, :], Q, nf[None, :])
-            if np.any(_segment_distance_sq(mid - 0.5 * d, d, (mid[None, :] - delta) - 0.5 * D, D)
-                      < diameter * diameter):
+        u = rng.random((batch, 5))
+        attempts += batch
+        mid = u[:, :3] * nf
+        z = -1.0 + 2.0 * u[:, 3]
+        phi = 2.0 * math.pi * u[:, 4]
+        sz = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+        d = np.stack([sz * np.cos(phi), sz * np.sin(phi), z], axis=1) * length
+        if count:
+            delta = _periodic_delta(mid[:, None, :], mids[None, :, :], nf)
+            dist = _segment_distance_sq_pairs((mid - 0.5 * d)[:, None, :], d[:, None, :],
+                                              (mid[:, None, :] - delta) - 0.5 * dirs[None, :, :],
+                                              dirs[None, :, :])
+            ok = ~np.any(dist < d2min, axis=1)
+        else:
+            ok = np.ones(batch, dtype=bool)
+        for i in range(batch):
+            if not ok[i]:
                 continue
-        if count == cap:
-            cap *= 2
-            mids = np.concatenate([mids, np.zeros_like(mids)])
-            dirs = np.concatenate([dirs, np.zeros_like(dirs)])
-        mids[count] = mid
-        dirs[count] = d
-        cells[key] = np.append(cells.get(key, np.zeros(0, dtype=np.int64)), count)
-        count += 1
-        filled += _stamp_cylinder(mask, mid - 0.5 * d, d, radius)
+            mids = np.concatenate([mids, mid[i:i + 1]])
+            dirs = np.concatenate([dirs, d[i:i + 1]])
+            count += 1
+            filled += _stamp_cylinder(mask, mid[i] - 0.5 * d[i], d[i], radius)
+            if filled / total >= volume_fraction:
+                break
+            rest = np.arange(i + 1, batch)
+            rest = rest[ok[rest]]
+            if rest.size:
+                delta = _periodic_delta(mid[rest], mid[i][None, :], nf)
+                dist = _segment_distance_sq_pairs(mid[rest] - 0.5 * d[rest], d[rest],
+                                                  (mid[rest] - delta) - 0.5 * d[i][None, :], d[i][None, :])
+                ok[rest[dist < d2min]] = False
     g = np.where(mask, gamma_fibre, gamma_matrix).astype(dtype)
     return g, count
 

@@ -282,6 +282,24 @@ int ccmf_set_kernel_timing(ccmf_plan* plan, int enable);
  *   results             : optional host [batch]: gamma_eff of the replayed run; synchronises the stream
  */
 int ccmf_adjoint_workspace_bytes(const ccmf_plan* plan, int K, int ckpt_every, size_t* bytes);
+
+/*
+ * Precision of the forward and recompute passes of ccmf_adjoint (the benchmark spec's precision
+ * pattern applied to reverse mode; the update differentiated is still Eq. 30 with the
+ * penalties replayed). For a CCMF_FP32_MIXED plan, CCMF_FP64 runs the recorded schedule,
+ * the forward replay with its checkpoints and every segment recomputation in double,
+ * rounds each update's pre-projection point z^k to float and records the branch of the
+ * radial projection (Eq. 19, [|z^k| > gamma] in double) as one bit per voxel and update;
+ * the reverse sweep then runs in float and takes the branches from those bits. The FP32
+ * forward takes the other branch at near-tied voxels and so differentiates another piece
+ * of the piecewise-smooth map; with the FP64 forward the FP32 gradient agrees with central
+ * differences of the FP64 replayed map. gamma_eff in the results is the FP64 forward's.
+ * The first call with CCMF_FP64 creates an FP64 plan of the same grid (its small tables);
+ * ccmf_adjoint_workspace_bytes then also counts the FP64 workspace, the FP64 checkpoints
+ * and the bits. CCMF_FP32_MIXED (the default of an FP32 plan) keeps everything in float.
+ * An FP64 plan accepts only CCMF_FP64.
+ */
+int ccmf_set_adjoint_forward(ccmf_plan* plan, int precision);
 int ccmf_adjoint(ccmf_plan* plan, const void* gamma, long long gamma_stride, const double* xi_bar,
                  const ccmf_params* params, int K, int ckpt_every, const double* rho_schedule,
                  void* workspace, size_t workspace_bytes, void* adj_workspace, size_t adj_workspace_bytes,

@@ -124,6 +124,7 @@ _SIGNATURES = {
     "ccmf_tuning_import": (ctypes.c_int, [ctypes.c_char_p]),
     "ccmf_adjoint_workspace_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                                      ctypes.POINTER(ctypes.c_size_t)]),
+    "ccmf_set_adjoint_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "ccmf_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong,
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ccmf_params), ctypes.c_int,
                                      ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_size_t,
@@ -303,6 +304,10 @@ def ccmf_adjoint_workspace_bytes(plan, K, ckpt_every):
     b = ctypes.c_size_t()
     code = load_library().ccmf_adjoint_workspace_bytes(plan, int(K), int(ckpt_every), ctypes.byref(b))
     return code, b.value
+
+
+def ccmf_set_adjoint_forward(plan, precision):
+    return load_library().ccmf_set_adjoint_forward(plan, int(precision))
 
 
 def ccmf_adjoint(plan, gamma_ptr, gamma_stride, xi_bar, params, K, ckpt_every, rho_schedule, workspace_ptr,
@@ -530,6 +535,12 @@ class Plan:
         _check(code, "ccmf_adjoint")
         results = [{f[0]: getattr(r, f[0]) for f in ccmf_result._fields_} for r in res]
         return grad, results, rho_out
+
+    def set_adjoint_forward(self, precision):
+        """Precision of the forward / recompute passes of gradient() (ccmf_set_adjoint_forward):
+        CCMF_FP64 on an FP32 plan gives the FP64 forward with the FP32 reverse sweep."""
+        with self.torch.cuda.device(self.device):
+            _check(ccmf_set_adjoint_forward(self.handle, precision), "ccmf_set_adjoint_forward")
 
     def set_kernel_timing(self, enable):
         _check(ccmf_set_kernel_timing(self.handle, 1 if enable else 0), "ccmf_set_kernel_timing")

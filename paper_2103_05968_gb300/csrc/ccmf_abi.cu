@@ -37,7 +37,7 @@ template <typename T> void launch_adj_restore(const Ctx<T>&, int, const double*,
 template <typename T> void launch_adj_seed(const Ctx<T>&, T*, T*, SolveScalars*, cudaStream_t);
 template <typename T>
 void launch_adj_step(const Ctx<T>&, const T*, T*, T*, T*, T*, T*, const T*, SolveScalars*, T*, const double*, int, int,
-                     cudaStream_t);
+                     cudaStream_t, const unsigned*);
 }  // namespace ccmf
 
 namespace {
@@ -166,6 +166,9 @@ struct ccmf_plan {
     double kms[kNumKernelClasses];
     long long klaunch[kNumKernelClasses];
     long long launches_last;
+    // reverse mode of an FP32 plan with an FP64 forward (ccmf_set_adjoint_forward)
+    int adj_forward;         // precision of the adjoint's forward and recompute passes
+    ccmf_plan* shadow64;     // FP64 plan of the same grid and batch for those passes
 };
 
 namespace {
@@ -877,6 +880,7 @@ int ccmf_plan_create(int n1, int n2, int n3, int batch, int precision, ccmf_plan
     pl->n3h = n3 / 2 + 1;
     pl->batch = batch;
     pl->prec = precision;
+    pl->adj_forward = precision;
     pl->esize = precision == CCMF_FP64 ? 8 : 4;
     for (int a = 0; a < 3; ++a) pl->ax[a] = ax[a];
     Geom& g = pl->g;
@@ -997,6 +1001,7 @@ int ccmf_plan_create(int n1, int n2, int n3, int batch, int precision, ccmf_plan
 
 int ccmf_plan_destroy(ccmf_plan* pl) {
     if (!pl) return CCMF_OK;
+    if (pl->shadow64) ccmf_plan_destroy(pl->shadow64);
     destroy_graph(pl);
     for (cudaEvent_t ev : pl->events) cudaEventDestroy(ev);
     for (int a = 0; a < 3; ++a) {
@@ -1854,7 +1859,252 @@ int adjoint_impl(ccmf_plan* pl, const T* gamma, long long gstride, const double*
         }
         for (int k = k1 - 1; k >= k0; --k)
             launch_adj_step<T>(c, zbuf + (size_t)(k - k0) * f6, ebar, vbar, zbar, y, my, zero, dummy, grad, dsched, K,
-                               k, st);
+                               k, st, nullptr);
+        if (cudaGetLastError() != cudaSuccess) return CCMF_ERR_CUDA;
+    }
+    return CCMF_OK;
+}
+
+// Reverse mode of an FP32 plan with the forward and the segment recomputation in FP64
+// (the FP64 shadow plan) and the reverse sweep in FP32: the FP32 trajectory takes the
+// other branch of P_C at near-tied voxels (|z| close to gamma), so an FP32 forward
+// differentiates another piece of the piecewise-smooth map. Here the FP64 forward keeps
+// its checkpoints in double; each segment is recomputed in double and every update's
+// pre-projection point z^k is rounded to float together with one bit per voxel, the
+// branch the FP64 projection took; the FP32 reverse steps take the branches from the bits.
+// FP64 forward, FP32 reverse: the pre-projection point z^k of an FP64 update, rounded to
+// float, and the branch the FP64 projection took, [|z^k| > gamma] (Eq. 19), one bit per
+// voxel. Threads of a warp take 32 consecutive voxels and the warp writes one word.
+__global__ void __launch_bounds__(kThreads) k_adj_pack(Geom g, const double* __restrict__ z,
+                                                       const double* __restrict__ gamma, long long gstride,
+                                                       float* __restrict__ z32, unsigned* __restrict__ bits) {
+    const int s = blockIdx.y;
+    const long long N = g.N;
+    const long long words = (N + 31) / 32;
+    const double* zs = z + (size_t)s * 6 * N;
+    const double* gs = gamma + (size_t)s * gstride;
+    float* zo = z32 + (size_t)s * 6 * N;
+    unsigned* bo = bits + (size_t)s * words;
+    const long long stride = (long long)gridDim.x * kThreads;   // a multiple of 32
+    for (long long lin = (long long)blockIdx.x * kThreads + threadIdx.x; lin < words * 32; lin += stride) {
+        bool clip = false;
+        if (lin < N) {
+            double nz2 = 0.0;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                const double zc = zs[c * N + lin];
+                nz2 += zc * zc;
+                zo[c * N + lin] = (float)zc;
+            }
+            clip = sqrt(nz2) > gs[lin];
+        }
+        const unsigned word = __ballot_sync(0xffffffffu, clip);
+        if ((threadIdx.x & 31) == 0) bo[lin >> 5] = word;
+    }
+}
+
+// A float field widened to double (gamma for the FP64 forward of an FP32 plan).
+__global__ void __launch_bounds__(kThreads) k_widen(const float* __restrict__ src, double* __restrict__ dst,
+                                                    long long n) {
+    const long long stride = (long long)gridDim.x * kThreads;
+    for (long long q = (long long)blockIdx.x * kThreads + threadIdx.x; q < n; q += stride) dst[q] = (double)src[q];
+}
+
+// Pack the FP64 pre-projection points of one update into float plus clip bits.
+void launch_adj_pack(const Ctx<double>& c, const double* zk, const double* gamma64, long long gstride,
+                            float* z32, unsigned* bits, cudaStream_t st) {
+    dim3 grid((unsigned)c.sh.grid_update, (unsigned)c.g.batch);
+    k_adj_pack<<<grid, kThreads, 0, st>>>(c.g, zk, gamma64, gstride, z32, bits);
+}
+
+void launch_widen(const float* src, double* dst, long long n, cudaStream_t st) {
+    long long blocks = ceil_div(n, kThreads);
+    if (blocks > 4096) blocks = 4096;
+    k_widen<<<(unsigned)(blocks < 1 ? 1 : blocks), kThreads, 0, st>>>(src, dst, n);
+}
+
+struct AdjLayoutMixed {
+    size_t sched, dummy, ws64, gamma64, ckpt, ztmp, z, bits, ebar, vbar, zbar, y, my, zero, total;
+};
+
+AdjLayoutMixed adj_layout_mixed(const ccmf_plan* pl, int K, int m) {
+    AdjLayoutMixed L;
+    const ccmf_plan* p64 = pl->shadow64;
+    const size_t N = (size_t)pl->g.N, B = (size_t)pl->batch;
+    const size_t f6_32 = 4 * 6 * N * B, f6_64 = 8 * 6 * N * B;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes);
+        return o;
+    };
+    L.sched = take(sizeof(double) * (size_t)K * B);
+    L.dummy = take(256 * B);
+    L.ws64 = take(p64 ? p64->total : 0);
+    L.gamma64 = take(8 * N * B);
+    L.ckpt = take(2 * f6_64 * (size_t)((K + m - 1) / m));
+    L.ztmp = take(f6_64);
+    L.z = take(f6_32 * (size_t)m);
+    L.bits = take(sizeof(unsigned) * ((N + 31) / 32) * B * (size_t)m);
+    L.ebar = take(f6_32);
+    L.vbar = take(f6_32);
+    L.zbar = take(f6_32);
+    L.y = take(f6_32);
+    L.my = take(f6_32);
+    L.zero = take(f6_32);
+    L.total = off;
+    return L;
+}
+
+int adjoint_mixed_impl(ccmf_plan* pl, const float* gamma, long long gstride, const double* xi_host,
+                       const ccmf_params* prm, int K, int m, const double* sched_host, unsigned char* ws,
+                       unsigned char* aws, float* grad, double* rho_out, ccmf_result* results, cudaStream_t st) {
+    ccmf_plan* p64 = pl->shadow64;
+    const Geom& g = pl->g;
+    const int B = pl->batch;
+    const size_t N = (size_t)g.N;
+    const AdjLayoutMixed L = adj_layout_mixed(pl, K, m);
+    unsigned char* ws64 = aws + L.ws64;
+    double* gam64 = reinterpret_cast<double*>(aws + L.gamma64);
+    const size_t gfields = gstride == 0 ? 1 : (size_t)B;
+    for (size_t s = 0; s < gfields; ++s) launch_widen(gamma + s * (size_t)gstride, gam64 + s * N, (long long)N, st);
+    const long long gstride64 = gstride == 0 ? 0 : (long long)N;
+
+    std::vector<double> sched((size_t)K * B);
+    if (sched_host) {
+        memcpy(sched.data(), sched_host, sched.size() * sizeof(double));
+    } else {
+        // the penalties of an adaptive FP64 run of K updates
+        ccmf_params rec = *prm;
+        rec.fixed_iters = K;
+        rec.check_every = K;
+        rec.resume = 0;
+        rec.history_len = K;
+        int rc = solve_impl<double>(p64, gam64, gstride64, xi_host, &rec, ws64, nullptr, nullptr, nullptr, st);
+        if (rc != CCMF_OK) return rc;
+        std::vector<double> hist((size_t)B * K * kHistFields);
+        int cnt = 0;
+        rc = ccmf_history_export(p64, ws64, hist.data(), K, &cnt, st);
+        if (rc != CCMF_OK) return rc;
+        if (cnt != K) return CCMF_ERR_NUMERICAL;
+        for (int s = 0; s < B; ++s)
+            for (int k = 0; k < K; ++k) sched[(size_t)s * K + k] = hist[((size_t)s * K + k) * kHistFields + 1];
+    }
+    if (rho_out) memcpy(rho_out, sched.data(), sched.size() * sizeof(double));
+    double* dsched = reinterpret_cast<double*>(aws + L.sched);
+    if (cudaMemcpyAsync(dsched, sched.data(), sched.size() * sizeof(double), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+        return CCMF_ERR_CUDA;
+
+    std::vector<double> xi(3 * (size_t)B);
+    for (int s = 0; s < B; ++s) {
+        const double* x = xi_host + 3 * s;
+        const double nn = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        for (int a = 0; a < 3; ++a) xi[3 * s + a] = x[a] / nn;
+    }
+    if (cudaMemcpyAsync(ws64 + p64->off_xi, xi.data(), xi.size() * sizeof(double), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(ws + pl->off_xi, xi.data(), xi.size() * sizeof(double), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemsetAsync(ws64 + p64->off_nact, 0, sizeof(int), st) != cudaSuccess ||
+        cudaMemsetAsync(ws + pl->off_nact, 0, sizeof(int), st) != cudaSuccess)
+        return CCMF_ERR_CUDA;
+    LoopConfig cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.tol = 1.0;
+    cfg.delta = prm->delta;
+    cfg.rho0 = prm->rho0;
+    cfg.bb_corr_min = prm->bb_corr_min;
+    cfg.rho_step_max = prm->rho_step_max;
+    cfg.max_iter = K;
+    cfg.fixed_iters = K;
+    cfg.rho_rule = CCMF_RHO_CONST;
+    cfg.hist_len = 0;
+    cfg.resume = 0;
+    cfg.rho_sched = dsched;
+    cfg.sched_len = K;
+
+    // FP64 forward replay with FP64 checkpoints of (e, v)
+    Ctx<double> c64 = make_ctx<double>(p64, ws64, gam64, gstride64, cfg);
+    c64.vec_update = false;   // the scalar update pass can also emit z
+    const size_t f6 = (size_t)6 * N * B;
+    double* ckpt = reinterpret_cast<double*>(aws + L.ckpt);
+    double* e_state = reinterpret_cast<double*>(ws64 + p64->off_e);
+    double* v_state = reinterpret_cast<double*>(ws64 + p64->off_v);
+    launch_init<double>(c64, st);
+    for (int k = 0; k < K; ++k) {
+        if (k % m == 0) {
+            const size_t cur = (size_t)(k & 1) * f6;
+            double* slot = ckpt + (size_t)(k / m) * 2 * f6;
+            if (cudaMemcpyAsync(slot, e_state + cur, f6 * sizeof(double), cudaMemcpyDeviceToDevice, st) !=
+                    cudaSuccess ||
+                cudaMemcpyAsync(slot + f6, v_state + cur, f6 * sizeof(double), cudaMemcpyDeviceToDevice, st) !=
+                    cudaSuccess)
+                return CCMF_ERR_CUDA;
+        }
+        launch_iteration<double>(c64, st);
+    }
+    launch_final<double>(c64, st, nullptr, nullptr);
+    if (cudaGetLastError() != cudaSuccess) return CCMF_ERR_CUDA;
+    if (results) {
+        std::vector<SolveScalars> sc(B);
+        if (cudaMemcpyAsync(sc.data(), ws64 + p64->off_sc, sizeof(SolveScalars) * B, cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return CCMF_ERR_CUDA;
+        for (int s = 0; s < B; ++s) {
+            ccmf_result& r = results[s];
+            r.gamma_eff = sc[s].dual;
+            r.gamma_primal = sc[s].primal;
+            r.gamma_dual = sc[s].dual;
+            r.residual = sc[s].residual;
+            r.mean_v_norm = sc[s].mean_v;
+            r.rho = sc[s].rho;
+            r.iters = sc[s].iters;
+            r.converged = 0;
+            r.status = sc[s].status;
+            r.reserved = 0;
+        }
+    }
+
+    // FP32 reverse sweep; the FP32 context supplies the M applications and the seed
+    Ctx<float> c32 = make_ctx<float>(pl, ws, gamma, gstride, cfg);
+    launch_init<float>(c32, st);   // unit normals and gamma statistics of the FP32 workspace
+    float* zbuf = reinterpret_cast<float*>(aws + L.z);
+    unsigned* bits = reinterpret_cast<unsigned*>(aws + L.bits);
+    const size_t words = ((N + 31) / 32) * (size_t)B;
+    double* ztmp = reinterpret_cast<double*>(aws + L.ztmp);
+    float* ebar = reinterpret_cast<float*>(aws + L.ebar);
+    float* vbar = reinterpret_cast<float*>(aws + L.vbar);
+    float* zbar = reinterpret_cast<float*>(aws + L.zbar);
+    float* y = reinterpret_cast<float*>(aws + L.y);
+    float* my = reinterpret_cast<float*>(aws + L.my);
+    float* zero = reinterpret_cast<float*>(aws + L.zero);
+    SolveScalars* dummy = reinterpret_cast<SolveScalars*>(aws + L.dummy);
+    if (cudaMemsetAsync(zero, 0, f6 * sizeof(float), st) != cudaSuccess ||
+        cudaMemsetAsync(grad, 0, sizeof(float) * N * B, st) != cudaSuccess)
+        return CCMF_ERR_CUDA;
+    launch_adj_seed<float>(c32, ebar, vbar, dummy, st);
+    const int nseg = (K + m - 1) / m;
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+        const int k0 = sg * m, k1 = (k0 + m < K) ? k0 + m : K;
+        const size_t cur = (size_t)(k0 & 1) * f6;
+        double* slot = ckpt + (size_t)sg * 2 * f6;
+        if (cudaMemcpyAsync(e_state + cur, slot, f6 * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(v_state + cur, slot + f6, f6 * sizeof(double), cudaMemcpyDeviceToDevice, st) !=
+                cudaSuccess)
+            return CCMF_ERR_CUDA;
+        launch_adj_restore<double>(c64, k0, dsched, K, st);
+        for (int k = k0; k < k1; ++k) {
+            Ctx<double> ck = c64;
+            ck.p.zout = ztmp;
+            launch_iteration<double>(ck, st);
+            launch_adj_pack(c64, ztmp, gam64, gstride64, zbuf + (size_t)(k - k0) * f6, bits + (size_t)(k - k0) * words,
+                            st);
+        }
+        for (int k = k1 - 1; k >= k0; --k)
+            launch_adj_step<float>(c32, zbuf + (size_t)(k - k0) * f6, ebar, vbar, zbar, y, my, zero, dummy, grad,
+                                   dsched, K, k, st, bits + (size_t)(k - k0) * words);
         if (cudaGetLastError() != cudaSuccess) return CCMF_ERR_CUDA;
     }
     return CCMF_OK;
@@ -1864,9 +2114,24 @@ int adjoint_impl(ccmf_plan* pl, const T* gamma, long long gstride, const double*
 
 extern "C" {
 
+int ccmf_set_adjoint_forward(ccmf_plan* plan, int precision) {
+    if (!plan || (precision != CCMF_FP64 && precision != CCMF_FP32_MIXED)) return CCMF_ERR_INVALID_ARG;
+    if (plan->prec == CCMF_FP64 && precision != CCMF_FP64) return CCMF_ERR_INVALID_ARG;
+    if (plan->prec == CCMF_FP32_MIXED && precision == CCMF_FP64 && !plan->shadow64) {
+        if (cudaSetDevice(plan->device) != cudaSuccess) return CCMF_ERR_CUDA;
+        ccmf_plan* p64 = nullptr;
+        const int rc = ccmf_plan_create(plan->n1, plan->n2, plan->n3, plan->batch, CCMF_FP64, &p64);
+        if (rc != CCMF_OK) return rc;
+        plan->shadow64 = p64;
+    }
+    plan->adj_forward = precision;
+    return CCMF_OK;
+}
+
 int ccmf_adjoint_workspace_bytes(const ccmf_plan* plan, int K, int ckpt_every, size_t* bytes) {
     if (!plan || !bytes || K < 1 || ckpt_every < 1) return CCMF_ERR_INVALID_ARG;
-    *bytes = adj_layout(plan, K, ckpt_every).total;
+    const bool mixed = plan->prec == CCMF_FP32_MIXED && plan->adj_forward == CCMF_FP64 && plan->shadow64;
+    *bytes = mixed ? adj_layout_mixed(plan, K, ckpt_every).total : adj_layout(plan, K, ckpt_every).total;
     return CCMF_OK;
 }
 
@@ -1897,13 +2162,18 @@ int ccmf_adjoint(ccmf_plan* plan, const void* gamma, long long gamma_stride, con
             if (!(rho_schedule[q] > 0.0) || !isfinite(rho_schedule[q])) return CCMF_ERR_INVALID_ARG;
     if (!is_device_ptr(gamma) || !is_device_ptr(grad_gamma)) return CCMF_ERR_INVALID_ARG;
     if (!workspace || workspace_bytes < plan->total || ((uintptr_t)workspace & 255u) != 0) return CCMF_ERR_WORKSPACE;
-    const size_t need = adj_layout(plan, K, ckpt_every).total;
+    const bool mixed = plan->prec == CCMF_FP32_MIXED && plan->adj_forward == CCMF_FP64 && plan->shadow64;
+    const size_t need = mixed ? adj_layout_mixed(plan, K, ckpt_every).total : adj_layout(plan, K, ckpt_every).total;
     if (!adj_workspace || adj_workspace_bytes < need || ((uintptr_t)adj_workspace & 255u) != 0)
         return CCMF_ERR_WORKSPACE;
     if (cudaSetDevice(plan->device) != cudaSuccess) return CCMF_ERR_CUDA;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     unsigned char* ws = reinterpret_cast<unsigned char*>(workspace);
     unsigned char* aws = reinterpret_cast<unsigned char*>(adj_workspace);
+    if (mixed)
+        return adjoint_mixed_impl(plan, reinterpret_cast<const float*>(gamma), gamma_stride, xi_bar, &prm, K,
+                                  ckpt_every, rho_schedule, ws, aws, reinterpret_cast<float*>(grad_gamma), rho_out,
+                                  results, st);
     if (plan->prec == CCMF_FP64)
         return adjoint_impl<double>(plan, reinterpret_cast<const double*>(gamma), gamma_stride, xi_bar, &prm, K,
                                     ckpt_every, rho_schedule, ws, aws, reinterpret_cast<double*>(grad_gamma), rho_out,

@@ -16,5 +16,5 @@ template void launch_final<float>(const Ctx<float>&, cudaStream_t, float*, float
 template void launch_adj_restore<float>(const Ctx<float>&, int, const double*, int, cudaStream_t);
 template void launch_adj_seed<float>(const Ctx<float>&, float*, float*, SolveScalars*, cudaStream_t);
 template void launch_adj_step<float>(const Ctx<float>&, const float*, float*, float*, float*, float*, float*, const float*, SolveScalars*, float*,
-                                   const double*, int, int, cudaStream_t);
+                                   const double*, int, int, cudaStream_t, const unsigned*);
 }  // namespace ccmf

@@ -16,5 +16,5 @@ template void launch_final<double>(const Ctx<double>&, cudaStream_t, double*, do
 template void launch_adj_restore<double>(const Ctx<double>&, int, const double*, int, cudaStream_t);
 template void launch_adj_seed<double>(const Ctx<double>&, double*, double*, SolveScalars*, cudaStream_t);
 template void launch_adj_step<double>(const Ctx<double>&, const double*, double*, double*, double*, double*, double*, const double*, SolveScalars*, double*,
-                                   const double*, int, int, cudaStream_t);
+                                   const double*, int, int, cudaStream_t, const unsigned*);
 }  // namespace ccmf

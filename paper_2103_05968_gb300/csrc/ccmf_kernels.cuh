@@ -2087,7 +2087,8 @@ __global__ void __launch_bounds__(kThreads) k_adj_pre(Geom g, const T* __restric
                                                       long long gstride, const T* __restrict__ ebar,
                                                       const T* __restrict__ vbar, const double* __restrict__ rho_k,
                                                       int sched_len, int k, double a, T* __restrict__ zbar,
-                                                      T* __restrict__ y, T* __restrict__ gbar) {
+                                                      T* __restrict__ y, T* __restrict__ gbar,
+                                                      const unsigned* __restrict__ clip_bits) {
     const int s = blockIdx.y;
     const long long N = g.N;
     const T rho = (T)rho_k[(size_t)s * sched_len + k];
@@ -2112,7 +2113,10 @@ __global__ void __launch_bounds__(kThreads) k_adj_pre(Geom g, const T* __restric
         }
         const T gm = gs[lin];
         const T nz = Real<T>::sqrt_(nz2);
-        const bool clip = nz > gm;
+        // the branch of P_C: taken here, or recorded by a forward pass in higher precision
+        // (one bit per voxel, [solve][ceil(N / 32)] words)
+        const bool clip = clip_bits ? ((clip_bits[(size_t)s * ((N + 31) / 32) + (lin >> 5)] >> (lin & 31)) & 1u) != 0
+                                    : nz > gm;
         if (clip) {
 #pragma unroll
             for (int c = 0; c < 6; ++c) zu += zc[c] * u[c];

@@ -490,14 +490,16 @@ void launch_adj_seed(const Ctx<T>& c, T* ebar, T* vbar, SolveScalars* dummy, cud
 
 // One reverse step k: zbar, y from (ebar, vbar, z^k); M y by the forward passes
 // (final-evaluation mode, xi_bar = 0, e = y, v = 0); then ebar, vbar.
+// clip_bits: optional [solve][ceil(N / 32)] branches of P_C recorded by an FP64 forward pass.
 template <typename T>
 void launch_adj_step(const Ctx<T>& c, const T* zk, T* ebar, T* vbar, T* zbar, T* y, T* my, const T* zero,
-                     SolveScalars* dummy, T* grad, const double* sched, int sched_len, int k, cudaStream_t st) {
+                     SolveScalars* dummy, T* grad, const double* sched, int sched_len, int k, cudaStream_t st,
+                     const unsigned* clip_bits) {
     const double a = 2.0 * (1.0 - c.cfg.delta), b = 1.0 - 2.0 * c.cfg.delta;
     dim3 grid((unsigned)c.sh.grid_update, (unsigned)c.g.batch);
     const T* gam = c.p.gptrs ? nullptr : c.p.gamma;
     k_adj_pre<T><<<grid, kThreads, 0, st>>>(c.g, zk, gam, c.p.gstride, ebar, vbar, sched, sched_len, k, a, zbar, y,
-                                             grad);
+                                             grad, clip_bits);
     Ctx<T> cm = c;
     cm.p.e = y;
     cm.p.v = const_cast<T*>(zero);

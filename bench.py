@@ -147,18 +147,26 @@ def basis_bytes_per_voxel(esize):
     return 33 * esize
 
 
-def bytes_per_voxel(kernel, esize, n3):
-    """Algorithmic DRAM bytes per voxel of one launch of each loop kernel."""
+def bytes_per_voxel(kernel, esize, n3, stored_div=False):
+    """Algorithmic DRAM bytes per voxel of one launch of each loop kernel. stored_div: the
+    stored-divergence schedule (update variants 8, 9), whose first pass reads the two
+    divergences a, b and whose update pass also writes them."""
     half = (n3 // 2 + 1) / n3 * 2 * esize  # half-spectrum bytes per voxel
     return {
-        "k_div_rfft_z": 12 * esize + half,          # read e, v; write spectrum
+        "k_div_rfft_z": (2 if stored_div else 12) * esize + half,   # read a, b (or e, v); write spectrum
         "k_fft_y_fwd": 2 * half,                    # read + write spectrum
         "k_fft_x_solve": 2 * half,
         "k_fft_y_inv": 2 * half,
         "k_fft_plane": 2 * half,                    # read + write spectrum once (y, x, solve, x, y fused)
         "k_irfft_z": half + esize,                  # read spectrum; write phi
-        "k_update": 12 * esize + 2 * esize + 12 * esize,  # read e, v, gamma, phi; write e, v
+        # read e, v, gamma, phi; write e, v (and a, b)
+        "k_update": 12 * esize + 2 * esize + 12 * esize + (2 * esize if stored_div else 0),
     }[kernel]
+
+
+def plan_stored_div(plan):
+    """True when the plan's update variant is the stored-divergence schedule (8 or 9)."""
+    return int(plan.tuning()["update_variant"]) >= 8
 
 
 def load_traffic(kernel, workload, precision, with_source=False):
@@ -404,9 +412,11 @@ def fibres512_record(args, dev):
     peak, peak_kind = load_peaks()
     dom = max(kt, key=lambda k: kt[k][0])
     dom_ms = kt[dom][0] / kt[dom][1]
-    dom_bytes = bytes_per_voxel(dom, 4, 512) * N
+    sd = plan_stored_div(plan)
+    dom_bytes = bytes_per_voxel(dom, 4, 512, sd) * N
     basis = basis_bytes_per_voxel(4) * N
     ms_step, ms_iter = t_k / K, (t_2k - t_k) / K
+    tuning = plan.tuning()
     plan.close()
     return {"workload": WORKLOADS["fibres512"]["desc"] + " FP32-mixed (FP64 reductions)", "steps": K,
             "ms_per_step": ms_step, "value": N * K / (t_k * 1e-3), "unit": UNIT,
@@ -417,6 +427,8 @@ def fibres512_record(args, dev):
                                 "achieved_gbs": dom_bytes / (dom_ms * 1e-3) / 1e9,
                                 "frac": dom_bytes / (dom_ms * 1e-3) / 1e9 / peak},
             "kernels_ms_per_launch": {k: v[0] / v[1] for k, v in kt.items()},
+            "own_schedule_bytes_per_voxel": sum(bytes_per_voxel(k, 4, 512, sd) for k in kt),
+            "tuning": tuning,
             "peak": peak, "peak_kind": peak_kind, "autotune": tune, "setup_seconds": setup_s,
             "l2": "inputs larger than L2: state 6.4 GB per step"}
 
@@ -663,13 +675,14 @@ def run_gpu(args, world, rank, local):
     # roofline of the dominant kernel
     dom = max(kt, key=lambda k: kt[k][0])
     dom_ms, dom_n = kt[dom]
-    per_launch_bytes = bytes_per_voxel(dom, esize, n3) * N * B
+    sd = plan_stored_div(plan)
+    per_launch_bytes = bytes_per_voxel(dom, esize, n3, sd) * N * B
     achieved = per_launch_bytes / (dom_ms / dom_n * 1e-3) / 1e9
     peak, peak_kind = load_peaks()
     kern = {k: {"ms_per_launch": ms / n, "launches": n, "share": ms / sum(x[0] for x in kt.values()),
-                "gbs": bytes_per_voxel(k, esize, n3) * N * B / (ms / n * 1e-3) / 1e9}
+                "gbs": bytes_per_voxel(k, esize, n3, sd) * N * B / (ms / n * 1e-3) / 1e9}
             for k, (ms, n) in kt.items()}
-    own_bpv = sum(bytes_per_voxel(k, esize, n3) for k in kt)
+    own_bpv = sum(bytes_per_voxel(k, esize, n3, sd) for k in kt)
     tuned = plan.tuning()
     traffic_key = f"{dom}@v{tuned['update_variant']}" if dom == "k_update" else dom
     traffic, traffic_src = (None, None) if args.grid else load_traffic(traffic_key, name, args.precision,

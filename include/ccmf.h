@@ -184,7 +184,7 @@ int ccmf_kernel_times(const ccmf_plan* plan, double* ms, long long* launches, co
 
 /*
  * Launch shape the plan chose, for tests and reports: out[0..7] = {update-pass
- * variant (0 registers, 1 TMA rows, 2..7 pipelined TMA), plane pass fused (0 / 1),
+ * variant (0 registers, 1 TMA rows, 2..7 pipelined TMA, 8..10 stored divergences), plane pass fused (0 / 1),
  * blocks sharing one (x, y) plane (1 = one block, 2..16 = a thread-block cluster),
  * z-pass line pairs per block, y-pass lines per block, x-pass lines per block,
  * update-pass blocks per solve, graph branches}. Writes min(capacity, 8) entries and
@@ -200,7 +200,14 @@ int ccmf_plan_launch_info(const ccmf_plan* plan, int* out, int capacity, int* co
  */
 typedef struct {
     int update_variant;     /* update pass: 0 register vectors in ticket-ordered chunks, 1 TMA rows,
-                               2..7 pipelined TMA */
+                               2..7 pipelined TMA; 8, 9 the stored-divergence schedule: the update
+                               pass also writes a = div^- A* e and b = div^- A* v of the new state
+                               (Eq. 28, Eq. 30: the divergence of e - v / rho is a - b / rho), so the
+                               first pass of the next iteration reads 2 scalars per voxel instead of
+                               the 12 state components; 8: 8 warps per block, 9: 16 warps with half
+                               the voxels per lane, 10: 8 warps with half the voxels per lane and two
+                               blocks per SM; needs N3 a multiple of 128 / 64 / 64 (variant 8 / 9 / 10,
+                               FP32) or 64 / 32 / 32 (FP64) */
     int plane_blocks;       /* y / x passes: 0 three strided passes, 1 one block per (x, y) plane,
                                2, 4, 8, 16 a thread-block cluster per plane */
     int z_pairs_per_block;  /* divergence + forward z pass: line pairs per block, power of two 1..16 */

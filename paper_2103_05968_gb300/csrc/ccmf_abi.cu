@@ -28,6 +28,7 @@ template <typename T> int plane_cluster_capacity(int, size_t);
 template <typename T> int lines_blocks_per_sm(int, int, size_t);
 template <typename T> int wlines_blocks_per_sm(int, int, size_t);
 template <typename T> int update_vec_blocks_per_sm();
+template <typename T> int ab_blocks_per_sm(int, size_t);
 template <typename T> void launch_init(const Ctx<T>&, cudaStream_t);
 template <typename T> void launch_iteration(const Ctx<T>&, cudaStream_t);
 template <typename T> void launch_iteration_range(const Ctx<T>&, int, int, cudaStream_t);
@@ -146,7 +147,7 @@ struct ccmf_plan {
     void* rsym[2];   // x, y symbol tables in digit-reversed order
     // workspace layout
     size_t off_sc, off_nact, off_xi, off_part, off_hist, off_e, off_v, off_spec, off_phi, off_gam, off_cut,
-        off_flow, total;
+        off_flow, off_ab, total;
     cudaStream_t cap_stream;
     cudaStream_t branch_stream[kMaxBranches];
     cudaEvent_t fork_event, join_event[kMaxBranches];
@@ -278,9 +279,54 @@ int shape_for(const ccmf_plan* pl, const ccmf_tuning& t, LaunchShape* out, ccmf_
         variant = env ? atoi(env) : vdef;
         if (variant < 0 || variant > 7) variant = vdef;
     }
-    if (variant > 7) return CCMF_ERR_UNSUPPORTED_SIZE;
+    if (variant >= kNumUpdateVariants) return CCMF_ERR_UNSUPPORTED_SIZE;
     sh.upd_variant = 0;
-    if (variant >= 2) {
+    if (variant >= 8) {
+        // stored-divergence update: whole z rows in passes of 32 VW voxels, a block of NW warps
+        // (NW - 2 interior rows); x segments sized so that the blocks of a launch fill the
+        // resident slots of the GPU in whole waves as far as possible
+        int nw = 0, vw = 0;
+        if (f64) {
+            CCMF_DISPATCH_AB(variant, {
+                nw = AbVariant<double, AV>::NW;
+                vw = AbVariant<double, AV>::VW;
+            });
+        } else {
+            CCMF_DISPATCH_AB(variant, {
+                nw = AbVariant<float, AV>::NW;
+                vw = AbVariant<float, AV>::VW;
+            });
+        }
+        const int kz = 32 * vw, tj = nw - 2;
+        const size_t smem = ab_smem_elems(tj, n3, nw, vw) * pl->esize;
+        if (n3 % kz == 0 && smem <= kSmemMax) {
+            const int nb = f64 ? ab_blocks_per_sm<double>(variant, smem) : ab_blocks_per_sm<float>(variant, smem);
+            if (nb > 0) {
+                AbShape& a = sh.ab;
+                a.tj = tj;
+                a.nq = (n2 + tj - 1) / tj;
+                a.npass = n3 / kz;
+                const long long slots = (long long)nb * sms;
+                double best = -1.0;
+                for (int nr = 1; nr <= n1; ++nr) {
+                    const int xs = (n1 + nr - 1) / nr;
+                    if ((long long)(nr - 1) * xs >= n1) continue;   // the same xs with fewer segments
+                    const long long items = (long long)a.nq * nr * batch;
+                    const long long waves = (items + slots - 1) / slots;
+                    // useful slab updates over slab updates done, times the share of busy slots
+                    const double eff = (double)n1 / ((double)nr * (xs + 2)) * (double)items / (double)(waves * slots);
+                    if (eff > best + 1e-9) {
+                        best = eff;
+                        a.nr = nr;
+                        a.xs = xs;
+                    }
+                }
+                sh.upd_variant = variant;
+                sh.smem_ab = smem;
+            }
+        }
+    }
+    if (variant >= 2 && variant <= 7) {
         const int vw = f64 ? 1 : 2;
         const int tv = kUpdatePipe[variant][0] * vw;
         const int stages = kUpdatePipe[variant][1];
@@ -306,7 +352,8 @@ int shape_for(const ccmf_plan* pl, const ccmf_tuning& t, LaunchShape* out, ccmf_
     if (explicit_variant && sh.upd_variant != variant) return CCMF_ERR_UNSUPPORTED_SIZE;
     r.update_variant = sh.upd_variant;
     sh.grid_partials = std::max(sh.grid_update, sh.grid_tma);
-    if (sh.upd_variant >= 2) sh.grid_partials = std::max(sh.grid_partials, sh.grid_pipe);
+    if (sh.upd_variant >= 2 && sh.upd_variant <= 7) sh.grid_partials = std::max(sh.grid_partials, sh.grid_pipe);
+    if (sh.upd_variant >= 8) sh.grid_partials = std::max(sh.grid_partials, sh.ab.nq * sh.ab.nr);
     // the vector update pass (variant 0 and every final evaluation) keeps one slot per chunk
     sh.grid_partials = (int)std::max<long long>(sh.grid_partials, vec_update_chunks(pl->g.N, f64 ? 2 : 4));
     // y / x passes: one block per k_z plane when the plane fits its shared memory, a
@@ -440,7 +487,7 @@ int shape_for(const ccmf_plan* pl, const ccmf_tuning& t, LaunchShape* out, ccmf_
 // variant, so that every tuning fits the same workspace.
 int partials_capacity(const ccmf_plan* pl) {
     int cap = std::max(608, pl->sh.grid_partials);
-    for (int v = 0; v <= 7; ++v) {
+    for (int v = 0; v < kNumUpdateVariants; ++v) {
         ccmf_tuning t;
         tuning_auto(&t);
         t.update_variant = v;
@@ -520,6 +567,10 @@ Ctx<T> make_ctx(const ccmf_plan* pl, unsigned char* ws, const T* gamma, long lon
     const int W = 16 / (int)sizeof(T);
     c.vec_div = (pl->n3 % W) == 0;
     c.vec_update = c.vec_div && ((uintptr_t)gamma % 16) == 0;
+    c.p.ab = reinterpret_cast<T*>(ws + pl->off_ab);
+    // the stored-divergence schedule needs the vector loads of gamma (a per-solve pointer
+    // table is aligned by the batch API's allocations of whole fields)
+    c.use_ab = pl->sh.upd_variant >= 8 && c.vec_update;
     return c;
 }
 
@@ -795,7 +846,7 @@ int tune_descent(ccmf_plan* plan, const std::function<int(double*)>& measure, do
     std::vector<int> brs;
     for (int b = 1; b <= std::min(kMaxBranches, plan->batch); ++b) brs.push_back(b);
     const Knob knobs[] = {
-        {&ccmf_tuning::update_variant, {0, 1, 2, 3, 4, 5, 6, 7}},
+        {&ccmf_tuning::update_variant, {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10}},
         {&ccmf_tuning::plane_blocks, {0, 1, 2, 4, 8, 16}},
         {&ccmf_tuning::z_pairs_per_block, {1, 2, 4, 8, 16}},
         {&ccmf_tuning::y_lines_per_block, {1, 2, 4, 8, 16}},
@@ -931,6 +982,7 @@ int ccmf_plan_create(int n1, int n2, int n3, int batch, int precision, ccmf_plan
     pl->off_v = take(pl->esize * 6 * N * batch * 2);
     pl->off_spec = take(cs * (size_t)g.Nh * batch);
     pl->off_phi = take(pl->esize * N * batch);
+    pl->off_ab = take(pl->esize * 2 * N * batch);
     pl->off_gam = take(pl->esize * N * batch);
     pl->off_cut = take(pl->esize * 6 * N * batch);
     pl->off_flow = take(pl->esize * 3 * N * batch);
@@ -1110,6 +1162,7 @@ int ccmf_state_import(const ccmf_plan* plan, void* workspace, const void* e, con
             return CCMF_ERR_CUDA;
         sc[s].rho = rho[s];
         sc[s].iters = iters[s];
+        sc[s].ab_iter = -1;   // stored divergences are recomputed from the imported state
     }
     if (cudaMemcpyAsync(ws + plan->off_sc, sc.data(), sizeof(SolveScalars) * plan->batch, cudaMemcpyHostToDevice,
                         st) != cudaSuccess)
@@ -1274,7 +1327,10 @@ int ccmf_tuning_import(const char* text) {
 int ccmf_plan_launch_info(const ccmf_plan* plan, int* out, int capacity, int* count) {
     if (!plan || !count || (capacity > 0 && !out)) return CCMF_ERR_INVALID_ARG;
     const LaunchShape& sh = plan->sh;
-    const int grid_upd = sh.upd_variant >= 2 ? sh.grid_pipe : sh.upd_variant == 1 ? sh.grid_tma : sh.grid_update;
+    const int grid_upd = sh.upd_variant >= 8   ? sh.ab.nq * sh.ab.nr
+                         : sh.upd_variant >= 2 ? sh.grid_pipe
+                         : sh.upd_variant == 1 ? sh.grid_tma
+                                               : sh.grid_update;
     const int v[8] = {sh.upd_variant, sh.plane_fused, sh.plane_fused ? sh.plane_cluster : 0, sh.pairs_per_block,
                       sh.lpb_y, sh.lpb_x, grid_upd, plan->branches};
     for (int i = 0; i < 8 && i < capacity; ++i) out[i] = v[i];
@@ -1791,6 +1847,7 @@ int adjoint_impl(ccmf_plan* pl, const T* gamma, long long gstride, const double*
     cfg.sched_len = K;
     Ctx<T> c = make_ctx<T>(pl, ws, gamma, gstride, cfg);
     c.vec_update = false;   // the scalar update pass can also emit z
+    c.use_ab = false;
     const size_t f6 = (size_t)6 * g.N * B;
     T* ckpt = reinterpret_cast<T*>(aws + L.ckpt);
     T* e_state = reinterpret_cast<T*>(ws + pl->off_e);
@@ -2027,6 +2084,7 @@ int adjoint_mixed_impl(ccmf_plan* pl, const float* gamma, long long gstride, con
     // FP64 forward replay with FP64 checkpoints of (e, v)
     Ctx<double> c64 = make_ctx<double>(p64, ws64, gam64, gstride64, cfg);
     c64.vec_update = false;   // the scalar update pass can also emit z
+    c64.use_ab = false;
     const size_t f6 = (size_t)6 * N * B;
     double* ckpt = reinterpret_cast<double*>(aws + L.ckpt);
     double* e_state = reinterpret_cast<double*>(ws64 + p64->off_e);
@@ -2069,6 +2127,7 @@ int adjoint_mixed_impl(ccmf_plan* pl, const float* gamma, long long gstride, con
 
     // FP32 reverse sweep; the FP32 context supplies the M applications and the seed
     Ctx<float> c32 = make_ctx<float>(pl, ws, gamma, gstride, cfg);
+    c32.use_ab = false;
     launch_init<float>(c32, st);   // unit normals and gamma statistics of the FP32 workspace
     float* zbuf = reinterpret_cast<float*>(aws + L.z);
     unsigned* bits = reinterpret_cast<unsigned*>(aws + L.bits);

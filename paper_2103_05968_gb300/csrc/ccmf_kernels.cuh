@@ -247,6 +247,7 @@ __global__ void __launch_bounds__(kThreads) k_init_stats(Geom g, Ptrs<T> p, Loop
         if (!cfg.resume) {
             S.rho = cfg.rho_sched ? cfg.rho_sched[(size_t)s * cfg.sched_len] : rho0;
             S.iters = 0;
+            S.ab_iter = -1;
         }
         S.status = status;
         S.converged = 0;
@@ -332,7 +333,7 @@ __device__ __forceinline__ RowNb row_neighbours(const Geom& g, unsigned row) {
 // d(p) = (1/sqrt2) sum_a [w1_a(p) - w1_a(p - e_a) + w2_a(p + e_a) - w2_a(p)].
 // VEC: each thread reads W consecutive voxels of a line with 16-byte loads.
 // ---------------------------------------------------------------------------
-template <typename T, int P, bool VEC>
+template <typename T, int P, bool VEC, bool AB = false>
 __global__ void __launch_bounds__(kThreads) k_div_rfft_z(Geom g, Ptrs<T> p, AxisPlan az,
                                                          const cx<T>* __restrict__ tw) {
     using C = cx<T>;
@@ -363,7 +364,19 @@ __global__ void __launch_bounds__(kThreads) k_div_rfft_z(Geom g, Ptrs<T> p, Axis
         T d[W];
 #pragma unroll
         for (int u = 0; u < W; ++u) d[u] = T(0);
-        if (l < L) {
+        if (AB && l < L) {
+            // stored divergences of the state: d = a - b / rho
+            const T* a = p.ab + (size_t)s * 2 * N + l * g.n3 + k0;
+            if constexpr (VEC) {
+                T ta[W], tb[W];
+                Vec16<T>::ld(a, ta);
+                Vec16<T>::ld(a + N, tb);
+#pragma unroll
+                for (int u = 0; u < W; ++u) d[u] = ta[u] - tb[u] * irho;
+            } else {
+                d[0] = a[0] - a[N] * irho;
+            }
+        } else if (l < L) {
             const RowNb rn = row_neighbours(g, (unsigned)l);
             const int kp = (k0 + W == g.n3) ? 0 : k0 + W;      // first voxel after the group
             const int km = (k0 == 0) ? g.n3 - 1 : k0 - 1;        // last voxel before the group
@@ -885,7 +898,7 @@ __global__ void __launch_bounds__(kPlaneClusterThreads, 1)
 // per k_z row, instead of a few lines per block. The divergence pass needs
 // N3 % 4 == 0 (FP32) / N3 % 2 == 0 (FP64) 16-byte groups, which power-of-two N3 >= 128 has.
 // ---------------------------------------------------------------------------
-template <typename T, int N>
+template <typename T, int N, bool AB = false>
 __global__ void __launch_bounds__(kThreads) k_div_rfft_wz(Geom g, Ptrs<T> p, const cx<T>* __restrict__ tw) {
     using C = cx<T>;
     constexpr int NW = kThreads / 32;     // packed lines per block
@@ -934,7 +947,15 @@ __global__ void __launch_bounds__(kThreads) k_div_rfft_wz(Geom g, Ptrs<T> p, con
             T d[W];
 #pragma unroll
             for (int u = 0; u < W; ++u) d[u] = T(0);
-            if (valid) {
+            if (AB && valid) {
+                // stored divergences of the state: d = a - b / rho
+                const T* a = p.ab + (size_t)s * 2 * Nv + rn.row + k0;
+                T ta[W], tb[W];
+                Vec16<T>::ld(a, ta);
+                Vec16<T>::ld(a + Nv, tb);
+#pragma unroll
+                for (int u = 0; u < W; ++u) d[u] = ta[u] - tb[u] * irho;
+            } else if (valid) {
                 const int kp = (k0 + W == N) ? 0 : k0 + W;   // first voxel after the group
                 const int km = (k0 == 0) ? N - 1 : k0 - 1;   // last voxel before the group
                 T wv[6][W], te[W], tv[W];
@@ -1172,7 +1193,7 @@ __device__ __forceinline__ void voxel_step(const StepConsts<T>& K, const T (&ec)
                                            const T (&php)[3], const T (&phm)[3], const T (&e2p)[3],
                                            const T (&v2p)[3], const T (&e1m)[3], const T (&v1m)[3],
                                            T (&acc)[kNSum], T (&eo)[6], T (&vo)[6], T (&flow)[3],
-                                           T* zo = nullptr) {
+                                           T* zo = nullptr, bool count = true) {
     T w[6], xh[6];
 #pragma unroll
     for (int c = 0; c < 6; ++c) w[c] = ec[c] - vc[c] * K.irho;
@@ -1193,10 +1214,12 @@ __device__ __forceinline__ void voxel_step(const StepConsts<T>& K, const T (&ec)
         const T dd = ec[c] - xh[c];
         r2 += dd * dd;
         nx2 += xh[c] * xh[c];
-        acc[kSumV + c] += vc[c];
+        if (count) acc[kSumV + c] += vc[c];
     }
-    acc[kSumRes] += r2;
-    acc[kSumPrimal] += gm * Proj<T>::norm(nx2);
+    if (count) {
+        acc[kSumRes] += r2;
+        acc[kSumPrimal] += gm * Proj<T>::norm(nx2);
+    }
     if (OUT) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) eo[c] = xh[c];                   // the cut xi^{K+1/2}
@@ -1233,17 +1256,19 @@ __device__ __forceinline__ void voxel_step(const StepConsts<T>& K, const T (&ec)
             eo[c] = en;
             vo[c] = vn;
         }
-        acc[kSumDvDe] += dvde;
-        acc[kSumDeDe] += dede;
-        acc[kSumDvDv] += dvdv;
-        acc[kSumVV] += vv;
-        acc[kSumEE] += ee;
+        if (count) {
+            acc[kSumDvDe] += dvde;
+            acc[kSumDeDe] += dede;
+            acc[kSumDvDv] += dvdv;
+            acc[kSumVV] += vv;
+            acc[kSumEE] += ee;
+        }
     }
 }
 
 // Reduction epilogue of the update pass: block partials, then the last block of
 // the solve reduces them in double and runs the penalty / history / stop logic.
-template <typename T, bool OUT, int NT = kThreads>
+template <typename T, bool OUT, int NT = kThreads, bool AB = false>
 __device__ void update_finish(const Geom& g, const Ptrs<T>& p, const LoopConfig& cfg, SolveScalars& S, int s,
                               double rho_d, const double* part, int nparts);
 
@@ -1259,7 +1284,7 @@ __device__ void update_epilogue(const Geom& g, const Ptrs<T>& p, const LoopConfi
 
 // The last block of a solve's update pass: reduce the nparts partials in a fixed
 // order, then the penalty rule, the history row and the stop decision.
-template <typename T, bool OUT, int NT>
+template <typename T, bool OUT, int NT, bool AB>
 __device__ void update_finish(const Geom& g, const Ptrs<T>& p, const LoopConfig& cfg, SolveScalars& S, int s,
                               double rho_d, const double* part, int nparts) {
     double sums[kNSum];
@@ -1323,6 +1348,7 @@ __device__ void update_finish(const Geom& g, const Ptrs<T>& p, const LoopConfig&
     }
     const int done = kk + 1 - S.call_start;
     S.iters = kk + 1;
+    S.ab_iter = AB ? kk + 1 : -1;   // whether the pass also wrote the divergences of the new state
     bool stop = false;
     if (S.status != 0) {
         stop = true;   // a failure recorded during the pass (e.g. a bounded wait that gave up)
@@ -1565,6 +1591,324 @@ __global__ void __launch_bounds__(kThreads) k_update_vec(Geom g, Ptrs<T> p, Loop
     if (block_ticket(&S.counter, gridDim.x)) update_finish<T, OUT>(g, p, cfg, S, s, rho_d, part, (int)nchunks);
 }
 
+
+// ---------------------------------------------------------------------------
+// Stored-divergence schedule (update variants 8 and 9). By Eq. 28 and Eq. 30 the
+// divergence the first pass needs is linear in the state: d = div^- A* (e - v / rho)
+// = a - b / rho with a = div^- A* e and b = div^- A* v. This update pass writes a and
+// b of the state it produces, so the first pass of the next iteration reads two
+// scalars per voxel instead of the twelve state components.
+//
+// div^- A* of the new state at voxel p takes, besides p itself, component 1a of the
+// voxel p - e_a and component 2a of p + e_a (the backward divergence of Sec. 2.2 applied
+// to A* of Eq. 17), i.e. updates of the six neighbours. A block owns tj consecutive y
+// rows of whole z rows (warps 1 .. tj; warps 0 and tj + 1 recompute the updates of the
+// rows just outside) and sweeps x over a segment of slabs, recomputing the slab before
+// and after the segment. The x terms wait one slab in shared memory (pending sums and
+// the component 1x of the previous slab), the y terms go through shared memory between
+// warps, the z terms between lanes (across the passes of a row, the first and last
+// voxels of a pass are completed by a fix-up in the next pass / at the end of the row).
+// ---------------------------------------------------------------------------
+template <typename T, int VW> struct VecN;
+template <> struct VecN<float, 4> {
+    __device__ __forceinline__ static void ld(const float* __restrict__ p, float (&o)[4]) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+        o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+    }
+    __device__ __forceinline__ static void st(float* p, const float (&o)[4]) {
+        *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+};
+template <> struct VecN<float, 2> {
+    __device__ __forceinline__ static void ld(const float* __restrict__ p, float (&o)[2]) {
+        const float2 t = __ldg(reinterpret_cast<const float2*>(p));
+        o[0] = t.x; o[1] = t.y;
+    }
+    __device__ __forceinline__ static void st(float* p, const float (&o)[2]) {
+        *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
+    }
+};
+template <> struct VecN<double, 2> {
+    __device__ __forceinline__ static void ld(const double* __restrict__ p, double (&o)[2]) {
+        const double2 t = __ldg(reinterpret_cast<const double2*>(p));
+        o[0] = t.x; o[1] = t.y;
+    }
+    __device__ __forceinline__ static void st(double* p, const double (&o)[2]) {
+        *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+    }
+};
+template <> struct VecN<double, 1> {
+    __device__ __forceinline__ static void ld(const double* __restrict__ p, double (&o)[1]) { o[0] = __ldg(p); }
+    __device__ __forceinline__ static void st(double* p, const double (&o)[1]) { p[0] = o[0]; }
+};
+
+__host__ __device__ constexpr size_t ab_smem_elems(int tj, int n3, int nw, int vw) {
+    return 4 * (size_t)tj * n3 + 2 * (size_t)nw * 4 * 32 * vw;
+}
+
+template <typename T, int VAR>
+__global__ void __launch_bounds__(AbVariant<T, VAR>::NW * 32, AbVariant<T, VAR>::MINB)
+    k_update_ab(Geom g, Ptrs<T> p, LoopConfig cfg, AbShape ab) {
+    constexpr int NW = AbVariant<T, VAR>::NW, VW = AbVariant<T, VAR>::VW;
+    constexpr int NT = NW * 32, KZ = 32 * VW;
+    using V = VecN<T, VW>;
+    const int s = blockIdx.y + p.s0;
+    SolveScalars& S = p.sc[s];
+    if (!S.active) return;
+    const long long N = g.N;
+    const int n1 = g.n1, n2 = g.n2, n3 = g.n3;
+    const double rho_d = S.rho;
+    const StepConsts<T> K = step_consts<T>(S, cfg);
+    const T h = K.h;
+    const int par = S.iters & 1;
+    const T* __restrict__ e = p.e + (long long)par * p.sstride + (long long)s * 6 * N;
+    const T* __restrict__ v = p.v + (long long)par * p.sstride + (long long)s * 6 * N;
+    T* __restrict__ e_out = p.e + (long long)(1 - par) * p.sstride + (long long)s * 6 * N;
+    T* __restrict__ v_out = p.v + (long long)(1 - par) * p.sstride + (long long)s * 6 * N;
+    const T* __restrict__ phi = p.phi + (size_t)s * N;
+    const T* __restrict__ gam = gamma_of(p, s);
+    T* __restrict__ a_out = p.ab + (size_t)s * 2 * N;
+    T* __restrict__ b_out = a_out + N;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int tj = ab.tj;
+    const int q = (int)(blockIdx.x % (unsigned)ab.nq), r = (int)(blockIdx.x / (unsigned)ab.nq);
+    const int j0 = q * tj;
+    const int nint = min(tj, n2 - j0);
+    const bool active_w = w <= nint + 1;              // warp-uniform
+    const bool interior_row = w >= 1 && w <= nint;    // warp-uniform (the recomputed rows 0, nint + 1
+                                                      // are needed for interior slabs only)
+    int j = j0 - 1 + w;
+    if (j < 0) j += n2;
+    if (j >= n2) j -= n2;
+    if (j >= n2) j -= n2;
+    const int jp = (j + 1 == n2) ? 0 : j + 1, jm = (j == 0) ? n2 - 1 : j - 1;
+    const int i0 = r * ab.xs, i1 = min(i0 + ab.xs, n1);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* pe = reinterpret_cast<T*>(smem_raw);     // pending a of the current slab, [tj][n3] (slot order)
+    T* pv = pe + (size_t)tj * n3;               // pending b
+    T* ex = pv + (size_t)tj * n3;               // component 1x of e' of the previous slab
+    T* vx = ex + (size_t)tj * n3;               // component 1x of v'
+    // [2][NW][4][KZ]: e'1y, e'2y, v'1y, v'2y of a pass, two buffers alternating by pass, so
+    // that one barrier per pass separates a buffer's writes from its reads and its reads
+    // (pass q) from its next writes (pass q + 2)
+    T* yb2 = vx + (size_t)tj * n3;
+    const size_t rbase = (size_t)(w - 1) * n3;  // this warp's row of the pending arrays
+    T acc[kNSum];
+#pragma unroll
+    for (int qq = 0; qq < kNSum; ++qq) acc[qq] = T(0);
+    T carry_e = T(0), carry_v = T(0);   // e'1z, v'1z of the last voxel of the previous pass
+    T z0_e = T(0), z0_v = T(0);         // e'2z, v'2z of voxel k = 0 (lane 0), for the row's wrap
+    const int npass = ab.npass;
+    for (int i = i0 - 1; i <= i1; ++i) {
+        const bool ring_lo = (i == i0 - 1), ring_hi = (i == i1), inner = !ring_lo && !ring_hi;
+        const int ii = (i < 0) ? i + n1 : (i >= n1 ? i - n1 : i);
+        const int ip = (ii + 1 == n1) ? 0 : ii + 1, im = (ii == 0) ? n1 - 1 : ii - 1;
+        const long long row = ((long long)ii * n2 + j) * n3;
+        const long long rxp = ((long long)ip * n2 + j) * n3, rxm = ((long long)im * n2 + j) * n3;
+        const long long ryp = ((long long)ii * n2 + jp) * n3, rym = ((long long)ii * n2 + jm) * n3;
+        const long long rprev = ((long long)im * n2 + j) * n3;   // slab i - 1, finalised in this step
+        const bool count = inner && interior_row;
+        for (int pz = 0; pz < npass; ++pz) {
+            const int k0 = pz * KZ + lane * VW;
+            T* yb = yb2 + (size_t)(((i - i0 + 1) * npass + pz) & 1) * NW * 4 * KZ;
+            T eo[6][VW], vo[6][VW];
+#pragma unroll
+            for (int c = 0; c < 6; ++c)
+#pragma unroll
+                for (int u = 0; u < VW; ++u) eo[c][u] = vo[c][u] = T(0);
+            if (interior_row || (active_w && inner)) {
+                const int kp = (k0 + VW == n3) ? 0 : k0 + VW;
+                const int km = (k0 == 0) ? n3 - 1 : k0 - 1;
+                T ec[6][VW], vc[6][VW];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+                    V::ld(e + c * N + row + k0, ec[c]);
+                    V::ld(v + c * N + row + k0, vc[c]);
+                }
+                T gm[VW], ph[VW];
+                V::ld(gam + row + k0, gm);
+                V::ld(phi + row + k0, ph);
+                T e2x[VW], v2x[VW], e1x[VW], v1x[VW], e2y[VW], v2y[VW], e1y[VW], v1y[VW];
+                T phxp[VW], phxm[VW], phyp[VW], phym[VW];
+                V::ld(e + 3 * N + rxp + k0, e2x);
+                V::ld(v + 3 * N + rxp + k0, v2x);
+                V::ld(e + 0 * N + rxm + k0, e1x);
+                V::ld(v + 0 * N + rxm + k0, v1x);
+                V::ld(e + 4 * N + ryp + k0, e2y);
+                V::ld(v + 4 * N + ryp + k0, v2y);
+                V::ld(e + 1 * N + rym + k0, e1y);
+                V::ld(v + 1 * N + rym + k0, v1y);
+                V::ld(phi + rxp + k0, phxp);
+                V::ld(phi + rxm + k0, phxm);
+                V::ld(phi + ryp + k0, phyp);
+                V::ld(phi + rym + k0, phym);
+                const T e2z_after = __ldg(e + 5 * N + row + kp), v2z_after = __ldg(v + 5 * N + row + kp);
+                const T e1z_before = __ldg(e + 2 * N + row + km), v1z_before = __ldg(v + 2 * N + row + km);
+                const T ph_after = __ldg(phi + row + kp), ph_before = __ldg(phi + row + km);
+#pragma unroll
+                for (int u = 0; u < VW; ++u) {
+                    T ecu[6], vcu[6];
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) {
+                        ecu[c] = ec[c][u];
+                        vcu[c] = vc[c][u];
+                    }
+                    const bool last = (u + 1 == VW), first = (u == 0);
+                    const T php[3] = {phxp[u], phyp[u], last ? ph_after : ph[(u + 1) % VW]};
+                    const T phm[3] = {phxm[u], phym[u], first ? ph_before : ph[(u + VW - 1) % VW]};
+                    const T e2p[3] = {e2x[u], e2y[u], last ? e2z_after : ec[5][(u + 1) % VW]};
+                    const T v2p[3] = {v2x[u], v2y[u], last ? v2z_after : vc[5][(u + 1) % VW]};
+                    const T e1m[3] = {e1x[u], e1y[u], first ? e1z_before : ec[2][(u + VW - 1) % VW]};
+                    const T v1m[3] = {v1x[u], v1y[u], first ? v1z_before : vc[2][(u + VW - 1) % VW]};
+                    T eou[6], vou[6], fl[3];
+                    voxel_step<T, false>(K, ecu, vcu, gm[u], ph[u], php, phm, e2p, v2p, e1m, v1m, acc, eou, vou, fl,
+                                         nullptr, count);
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) {
+                        eo[c][u] = eou[c];
+                        vo[c][u] = vou[c];
+                    }
+                }
+                if (count) {
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) {
+                        V::st(e_out + c * N + row + k0, eo[c]);
+                        V::st(v_out + c * N + row + k0, vo[c]);
+                    }
+                }
+                if (inner) {   // the y terms of the pending sums of interior slabs
+                    T* yw = yb + (size_t)w * 4 * KZ;
+#pragma unroll
+                    for (int u = 0; u < VW; ++u) {
+                        yw[0 * KZ + u * 32 + lane] = eo[1][u];
+                        yw[1 * KZ + u * 32 + lane] = eo[4][u];
+                        yw[2 * KZ + u * 32 + lane] = vo[1][u];
+                        yw[3 * KZ + u * 32 + lane] = vo[4][u];
+                    }
+                }
+            }
+            __syncthreads();
+            if (interior_row) {
+                // z neighbours from the neighbouring lanes (a row of one pass wraps within the warp)
+                const T e1z_l = __shfl_sync(0xffffffffu, eo[2][VW - 1], (lane + 31) & 31);
+                const T v1z_l = __shfl_sync(0xffffffffu, vo[2][VW - 1], (lane + 31) & 31);
+                const T e2z_r = __shfl_sync(0xffffffffu, eo[5][0], (lane + 1) & 31);
+                const T v2z_r = __shfl_sync(0xffffffffu, vo[5][0], (lane + 1) & 31);
+                T fa[VW], fb[VW];
+#pragma unroll
+                for (int u = 0; u < VW; ++u) {
+                    const size_t slot = rbase + (size_t)pz * KZ + u * 32 + lane;
+                    if (!ring_lo && i > i0) {   // a', b' of slab i - 1: its x+ terms are this slab's 2x
+                        fa[u] = pe[slot] + h * eo[3][u];
+                        fb[u] = pv[slot] + h * vo[3][u];
+                    }
+                    if (inner) {
+                        T tm_e, tm_v, tp_e, tp_v;
+                        if (u > 0) {
+                            tm_e = eo[2][u - 1];
+                            tm_v = vo[2][u - 1];
+                        } else if (lane > 0 || npass == 1) {
+                            tm_e = e1z_l;
+                            tm_v = v1z_l;
+                        } else {   // lane 0: the previous pass's last voxel (pass 0: fixed up at the row's end)
+                            tm_e = pz > 0 ? carry_e : T(0);
+                            tm_v = pz > 0 ? carry_v : T(0);
+                        }
+                        if (u + 1 < VW) {
+                            tp_e = eo[5][u + 1];
+                            tp_v = vo[5][u + 1];
+                        } else if (lane < 31 || npass == 1) {
+                            tp_e = e2z_r;
+                            tp_v = v2z_r;
+                        } else {   // lane 31: the next pass's first voxel (fixed up in the next pass)
+                            tp_e = T(0);
+                            tp_v = T(0);
+                        }
+                        const T* ym = yb + (size_t)(w - 1) * 4 * KZ;
+                        const T* yp = yb + (size_t)(w + 1) * 4 * KZ;
+                        const int ys = u * 32 + lane;
+                        const T la = h * ((eo[0][u] + eo[1][u] + eo[2][u]) - (eo[3][u] + eo[4][u] + eo[5][u]));
+                        const T lb = h * ((vo[0][u] + vo[1][u] + vo[2][u]) - (vo[3][u] + vo[4][u] + vo[5][u]));
+                        pe[slot] = la + h * ((tp_e - tm_e) + (yp[1 * KZ + ys] - ym[0 * KZ + ys]) - ex[slot]);
+                        pv[slot] = lb + h * ((tp_v - tm_v) + (yp[3 * KZ + ys] - ym[2 * KZ + ys]) - vx[slot]);
+                    }
+                    if (!ring_hi) {
+                        ex[slot] = eo[0][u];
+                        vx[slot] = vo[0][u];
+                    }
+                }
+                if (!ring_lo && i > i0) {
+                    V::st(a_out + rprev + k0, fa);
+                    V::st(b_out + rprev + k0, fb);
+                }
+                if (inner && npass > 1) {
+                    // z terms across passes of the row
+                    if (lane == 0 && pz > 0) {   // the previous pass's last voxel gets this voxel's 2z
+                        const size_t sl = rbase + (size_t)(pz - 1) * KZ + (VW - 1) * 32 + 31;
+                        pe[sl] += h * eo[5][0];
+                        pv[sl] += h * vo[5][0];
+                    }
+                    if (lane == 0 && pz == 0) {
+                        z0_e = eo[5][0];
+                        z0_v = vo[5][0];
+                    }
+                    if (pz == npass - 1) {
+                        __syncwarp();
+                        if (lane == 31) {   // voxel 0 gets the 1z of voxel n3 - 1
+                            pe[rbase] -= h * eo[2][VW - 1];
+                            pv[rbase] -= h * vo[2][VW - 1];
+                        }
+                        if (lane == 0) {   // voxel n3 - 1 gets the 2z of voxel 0
+                            const size_t sl = rbase + (size_t)(npass - 1) * KZ + (VW - 1) * 32 + 31;
+                            pe[sl] += h * z0_e;
+                            pv[sl] += h * z0_v;
+                        }
+                    }
+                }
+                carry_e = __shfl_sync(0xffffffffu, eo[2][VW - 1], 31);
+                carry_v = __shfl_sync(0xffffffffu, vo[2][VW - 1], 31);
+                __syncwarp();   // the fix-ups above before this warp's next writes of its slots
+            }
+        }
+    }
+    const int nblocks = gridDim.x;
+    double* part = p.partial + (size_t)s * nblocks * kNSum;
+    if (block_partials<T, kNSum, NT>(acc, part, &S.counter, nblocks, blockIdx.x))
+        update_finish<T, false, NT, true>(g, p, cfg, S, s, rho_d, part, nblocks);
+}
+
+// The stored divergences a = div^- A* e, b = div^- A* v of the current state, for a
+// state that the stored-divergence update did not write (a new solve, an imported
+// state, a state advanced by another update pass). Skipped for solves whose stored
+// divergences are current.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_ab_init(Geom g, Ptrs<T> p) {
+    const int s = blockIdx.y + p.s0;
+    const SolveScalars& S = p.sc[s];
+    if (S.ab_iter == S.iters) return;
+    const long long N = g.N;
+    const T h = T(0.70710678118654752440084436210485);
+    const long long cur = (long long)(S.iters & 1) * p.sstride + (long long)s * 6 * N;
+    const T* __restrict__ e = p.e + cur;
+    const T* __restrict__ v = p.v + cur;
+    T* a_out = p.ab + (size_t)s * 2 * N;
+    T* b_out = a_out + N;
+    const long long stride = (long long)gridDim.x * kThreads;
+    for (long long lin = (long long)blockIdx.x * kThreads + threadIdx.x; lin < N; lin += stride) {
+        const unsigned row = fdiv((unsigned)lin, g.div_n3);
+        const int k = (int)(lin - (long long)row * g.n3);
+        const RowNb rn = row_neighbours(g, row);
+        const int kp = (k + 1 == g.n3) ? 0 : k + 1, km = (k == 0) ? g.n3 - 1 : k - 1;
+        auto dv = [&](const T* f) {
+            const T sx = f[0 * N + lin] - f[0 * N + rn.im + k] + f[3 * N + rn.ip + k] - f[3 * N + lin];
+            const T sy = f[1 * N + lin] - f[1 * N + rn.jm + k] + f[4 * N + rn.jp + k] - f[4 * N + lin];
+            const T sz = f[2 * N + lin] - f[2 * N + rn.row + km] + f[5 * N + rn.row + kp] - f[5 * N + lin];
+            return h * (sx + sy + sz);
+        };
+        a_out[lin] = dv(e);
+        b_out[lin] = dv(v);
+    }
+}
 
 // ---------------------------------------------------------------------------
 // TMA-staged update pass. A tile is J consecutive z rows (i, j0 .. j0+J-1) of one

@@ -29,6 +29,7 @@ struct Ctx {
     LaunchShape sh;
     bool vec_div;         // 16-byte path of the divergence pass (N3 % W == 0)
     bool vec_update;      // 16-byte path of the update pass (also needs gamma 16-byte aligned)
+    bool use_ab;          // stored-divergence schedule: update variants 8 .. 10 write a, b; the first pass reads them
 };
 
 // Kernel classes of one loop iteration.
@@ -91,6 +92,14 @@ inline long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
         case 256: { constexpr int NN = 256; __VA_ARGS__; } break;  \
         case 512: { constexpr int NN = 512; __VA_ARGS__; } break;  \
         default: { constexpr int NN = 1024; __VA_ARGS__; } break;  \
+    }
+
+// Runs the statement list with the compile-time stored-divergence variant AV (8, 9, 10).
+#define CCMF_DISPATCH_AB(VAR, ...)                                 \
+    switch (VAR) {                                                 \
+        case 8: { constexpr int AV = 8; __VA_ARGS__; } break;      \
+        case 9: { constexpr int AV = 9; __VA_ARGS__; } break;      \
+        default: { constexpr int AV = 10; __VA_ARGS__; } break;    \
     }
 
 // Runs the statement list with compile-time ST (stages) and NTH (threads) of a
@@ -245,12 +254,18 @@ cudaError_t configure_kernels(const LaunchShape& sh) {
             err = raise_smem_limit(f, bytes);
     };
     CCMF_DISPATCH_LINES(sh.pairs_per_block, {
-        set((const void*)k_div_rfft_z<T, LN, true>, sh.smem_z);
-        set((const void*)k_div_rfft_z<T, LN, false>, sh.smem_z);
+        set((const void*)k_div_rfft_z<T, LN, true, false>, sh.smem_z);
+        set((const void*)k_div_rfft_z<T, LN, false, false>, sh.smem_z);
+        set((const void*)k_div_rfft_z<T, LN, true, true>, sh.smem_z);
     });
     CCMF_DISPATCH_LINES(sh.pairs_inv, { set((const void*)k_irfft_z<T, LN>, sh.smem_zi); });
     if (sh.wz) { CCMF_DISPATCH_N(sh.wz, { set((const void*)k_irfft_wz<T, NN>, sh.smem_wzi); }); }
-    if (sh.wzd) { CCMF_DISPATCH_N(sh.wzd, { set((const void*)k_div_rfft_wz<T, NN>, sh.smem_wzd); }); }
+    if (sh.wzd) {
+        CCMF_DISPATCH_N(sh.wzd, {
+            set((const void*)k_div_rfft_wz<T, NN, false>, sh.smem_wzd);
+            set((const void*)k_div_rfft_wz<T, NN, true>, sh.smem_wzd);
+        });
+    }
     CCMF_DISPATCH_LINES(sh.lpb_y, {
         set((const void*)k_fft_lines<T, 0, LN>, sh.smem_y);
         set((const void*)k_fft_lines<T, 2, LN>, sh.smem_y);
@@ -272,7 +287,8 @@ cudaError_t configure_kernels(const LaunchShape& sh) {
         set((const void*)k_update_tma<T, 1>, sh.smem_tma);
         set((const void*)k_update_tma<T, 2>, sh.smem_tma);
     }
-    if (sh.upd_variant >= 2) {
+    if (sh.upd_variant >= 8) { CCMF_DISPATCH_AB(sh.upd_variant, { set((const void*)k_update_ab<T, AV>, sh.smem_ab); }); }
+    if (sh.upd_variant >= 2 && sh.upd_variant <= 7) {
         CCMF_DISPATCH_PIPE(sh.upd_variant, {
             set((const void*)k_update_pipe<T, 0, ST, NTH>, sh.smem_pipe);
             set((const void*)k_update_pipe<T, 1, ST, NTH>, sh.smem_pipe);
@@ -288,6 +304,25 @@ void launch_init(const Ctx<T>& c, cudaStream_t st) {
     dim3 grid((unsigned)c.sh.grid_update, (unsigned)c.g.batch);
     k_init_stats<T><<<grid, kThreads, 0, st>>>(c.g, c.p, c.cfg);
     if (!c.cfg.resume) k_init_state<T><<<grid, kThreads, 0, st>>>(c.g, c.p);
+    if (c.use_ab) k_ab_init<T><<<grid, kThreads, 0, st>>>(c.g, c.p);
+}
+
+// Blocks per SM of the stored-divergence update variant 8, 9 or 10 (occupancy API), 0 on error.
+template <typename T>
+int ab_blocks_per_sm(int variant, size_t smem) {
+    const void* f = nullptr;
+    int nt = 0;
+    CCMF_DISPATCH_AB(variant, {
+        f = (const void*)k_update_ab<T, AV>;
+        nt = 32 * AbVariant<T, AV>::NW;
+    });
+    int nb = 0;
+    if (raise_smem_limit(f, smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, nt, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
 }
 
 // The 16-byte final evaluation pass needs 16-byte aligned cut and flow outputs.
@@ -322,14 +357,22 @@ void launch_passes(const Ctx<T>& c, const Ptrs<T>& p, cudaStream_t st, F&& betwe
     const dim3 gv((unsigned)(vpb < 1 ? 1 : vpb), (unsigned)g.batch);
     const T inv_n = (T)(1.0 / (double)g.N);
     const dim3 gwz((unsigned)ceil_div((long long)g.n1 * g.n2, 2 * (kThreads / 32)), (unsigned)g.batch);
+    const bool ab = !OUT && c.use_ab;   // the first pass reads the stored divergences a, b
     if (sh.wzd && c.vec_div) {
-        CCMF_DISPATCH_N(sh.wzd, { k_div_rfft_wz<T, NN><<<gwz, kThreads, sh.smem_wzd, st>>>(g, p, c.tw[2]); });
+        CCMF_DISPATCH_N(sh.wzd, {
+            if (ab)
+                k_div_rfft_wz<T, NN, true><<<gwz, kThreads, sh.smem_wzd, st>>>(g, p, c.tw[2]);
+            else
+                k_div_rfft_wz<T, NN, false><<<gwz, kThreads, sh.smem_wzd, st>>>(g, p, c.tw[2]);
+        });
     } else {
         CCMF_DISPATCH_LINES(sh.pairs_per_block, {
-            if (c.vec_div)
-                k_div_rfft_z<T, LN, true><<<gz, kThreads, sh.smem_z, st>>>(g, p, c.ax[2], c.tw[2]);
+            if (c.vec_div && ab)
+                k_div_rfft_z<T, LN, true, true><<<gz, kThreads, sh.smem_z, st>>>(g, p, c.ax[2], c.tw[2]);
+            else if (c.vec_div)
+                k_div_rfft_z<T, LN, true, false><<<gz, kThreads, sh.smem_z, st>>>(g, p, c.ax[2], c.tw[2]);
             else
-                k_div_rfft_z<T, LN, false><<<gz, kThreads, sh.smem_z, st>>>(g, p, c.ax[2], c.tw[2]);
+                k_div_rfft_z<T, LN, false, false><<<gz, kThreads, sh.smem_z, st>>>(g, p, c.ax[2], c.tw[2]);
         });
     }
     between(kKDivRfftZ);
@@ -393,7 +436,12 @@ void launch_passes(const Ctx<T>& c, const Ptrs<T>& p, cudaStream_t st, F&& betwe
         k_update_vec<T, true><<<gv, kThreads, 0, st>>>(g, p, c.cfg);
     else if (OUT)
         k_update<T, true><<<gu, kThreads, 0, st>>>(g, p, c.cfg);
-    else if (c.vec_update && sh.upd_variant >= 2) {
+    else if (ab) {
+        const dim3 ga((unsigned)(sh.ab.nq * sh.ab.nr), (unsigned)g.batch);
+        CCMF_DISPATCH_AB(sh.upd_variant, {
+            k_update_ab<T, AV><<<ga, AbVariant<T, AV>::NW * 32, sh.smem_ab, st>>>(g, p, c.cfg, sh.ab);
+        });
+    } else if (c.vec_update && sh.upd_variant >= 2 && sh.upd_variant <= 7) {
         const dim3 gp((unsigned)sh.grid_pipe, (unsigned)g.batch);
         CCMF_DISPATCH_PIPE(sh.upd_variant, {
             if (c.cfg.rho_rule == 0 || c.cfg.rho_rule == 3)   // BB and residual balancing need |de|^2

@@ -49,6 +49,7 @@ struct SolveScalars {
     unsigned int counter;  // last-block ticket of the reductions
     int bad;             // number of invalid gamma values seen at init
     unsigned int chunk;  // next work ticket of the vector update pass (dynamic schedule)
+    int ab_iter;         // update count the stored divergences a, b belong to (-1: not current)
 };
 static_assert(sizeof(SolveScalars) <= 256, "scalar slot");
 
@@ -88,6 +89,18 @@ struct Ptrs {
     int run_all;          // 1: passes run for every solve (final evaluation), 0: active solves only
     int s0;               // first solve of this launch (blockIdx.y counts from it)
     T* zout;              // when not null the (scalar) update pass also writes z = v + rho xi, [batch][6][N]
+    T* ab;                // stored divergences a = div^- A* e, b = div^- A* v of the state, [batch][2][N]
+};
+
+// Shape of the stored-divergence update (update variants 8, 9, 10): a block owns tj
+// consecutive y rows (plus one recomputed row on each side) of whole z rows and sweeps
+// x over a segment of xs slabs (plus one recomputed slab on each side).
+struct AbShape {
+    int tj;      // interior y rows per block (warps per block - 2)
+    int nq;      // y tiles: ceil(n2 / tj)
+    int xs;      // interior x slabs per block
+    int nr;      // x segments: ceil(n1 / xs)
+    int npass;   // z passes of 32 VW voxels per row (n3 / (32 VW))
 };
 
 struct LaunchShape {
@@ -115,9 +128,22 @@ struct LaunchShape {
     int wz, wzd;              // > 0: the inverse / divergence z pass runs one warp per line pair; N3
     size_t smem_wzd, smem_wzi;
     FastDiv div_r1, div_r2;   // rows (n1 / C) and columns (n2 / C) of one cluster block
+    AbShape ab;               // update variants 8, 9, 10: the stored-divergence update
+    size_t smem_ab;           // its dynamic shared memory
 };
 
 // Pipelined update variants: {threads per block, stages}.
 constexpr int kUpdatePipe[8][2] = {{0, 0}, {0, 0}, {256, 2}, {128, 3}, {128, 4}, {256, 3}, {128, 2}, {64, 3}};
+
+// Stored-divergence update variants 8, 9, 10: warps per block, voxels per lane and z pass,
+// blocks per SM the register budget is sized for.
+template <typename T, int VAR> struct AbVariant;
+template <> struct AbVariant<float, 8> { static constexpr int NW = 8, VW = 4, MINB = 1; };
+template <> struct AbVariant<float, 9> { static constexpr int NW = 16, VW = 2, MINB = 1; };
+template <> struct AbVariant<float, 10> { static constexpr int NW = 8, VW = 2, MINB = 2; };
+template <> struct AbVariant<double, 8> { static constexpr int NW = 8, VW = 2, MINB = 1; };
+template <> struct AbVariant<double, 9> { static constexpr int NW = 16, VW = 1, MINB = 1; };
+template <> struct AbVariant<double, 10> { static constexpr int NW = 8, VW = 1, MINB = 2; };
+constexpr int kNumUpdateVariants = 11;
 
 }  // namespace ccmf

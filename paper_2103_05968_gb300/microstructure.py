@@ -29,6 +29,9 @@ __all__ = [
     "random_two_phase",
     "uniform_random",
     "disks_2d",
+    "relaxed_spheres",
+    "porous_spheres",
+    "sand_binder",
     "config_single_sphere_32",
     "config_boolean_spheres_128",
     "config_short_fibres_512",
@@ -294,6 +297,108 @@ def disks_2d(n, count, area_fraction, gamma_disk, gamma_matrix, seed, max_attemp
         inside |= dx * dx + dy * dy < radius * radius
     gamma = np.where(inside, gamma_disk, gamma_matrix).astype(dtype)[:, :, None]
     return gamma, centres
+
+def relaxed_spheres(n, radii, seed, iterations=4000, tol=1e-3):
+    """Non-overlapping balls (periodic cell of shape n): centres i.i.d. uniform, then
+    overlaps removed by repeated pairwise pushes (every overlapping pair moves apart
+    along its centre line by its overlap, shared in proportion to the other ball's
+    radius) until the largest overlap is below tol voxels or `iterations` sweeps
+    have run. A stand-in for packings made by mechanical contraction (denser than
+    random sequential addition allows). Returns the centres, shape (len(radii), 3)."""
+    L = np.asarray([float(m) for m in n])
+    r = np.asarray(radii, dtype=np.float64)
+    rng = np.random.default_rng(seed)
+    x = rng.random((len(r), 3)) * L
+    rsum = r[:, None] + r[None, :]
+    share = r[None, :] / rsum            # ball i moves by this share of the pair's overlap
+    for _ in range(iterations):
+        d = x[:, None, :] - x[None, :, :]
+        d -= L * np.round(d / L)
+        dist = np.sqrt(np.sum(d * d, axis=-1))
+        np.fill_diagonal(dist, np.inf)
+        over = rsum - dist
+        over[over < 0.0] = 0.0
+        if over.max() < tol:
+            break
+        unit = d / np.maximum(dist, 1e-12)[:, :, None]
+        x += np.sum((over * share)[:, :, None] * unit, axis=1) * 1.0001
+        x %= L
+    return x
+
+
+def _stamp_balls(mask, centres, radii):
+    added = 0
+    for c, r in zip(centres, radii):
+        added += _stamp_ball(mask, c, r)
+    return added
+
+
+def porous_spheres(n, count, porosity, seed, gamma_solid=1.0, dtype=np.float64):
+    """Solid with `count` monodisperse, non-overlapping spherical pores of vanishing crack
+    resistance (Sec. 4.5: 200 pores, porosity 5 ... 50 %, gamma = 0 in the pores).
+    The radius gives the target porosity for balls in the continuum, the centres come
+    from relaxed_spheres. Returns (gamma, voxel porosity)."""
+    n = tuple(int(m) for m in n)
+    vol = float(np.prod(n))
+    radius = (porosity * vol * 3.0 / (4.0 * math.pi * count)) ** (1.0 / 3.0)
+    centres = relaxed_spheres(n, np.full(count, radius), seed)
+    mask = np.zeros(n, dtype=bool)
+    _stamp_balls(mask, centres, np.full(count, radius))
+    g = np.where(mask, 0.0, gamma_solid).astype(dtype)
+    return g, float(mask.mean())
+
+
+def sand_binder(n, grain_radius, grain_fraction, binder_fraction, seed, radius_spread=0.25):
+    """Three-phase sand-core stand-in (Sec. 4.6: grains 58.6 %, binder 1.3 %, the rest the
+    third phase): polydisperse, non-overlapping spherical grains (radius uniform in
+    grain_radius (1 +- radius_spread), added until the continuum volume reaches
+    grain_fraction, relaxed apart), a binder phase in the necks between neighbouring
+    grains (the voxels outside the grains closest to a second grain surface, i.e. with the
+    smallest distance to the second-nearest grain, up to binder_fraction of the cell),
+    and the remaining space as the third phase ("matrix").
+    Returns (labels, fractions): labels 0 matrix, 1 grain, 2 binder, uint8."""
+    n = tuple(int(m) for m in n)
+    vol = float(np.prod(n))
+    rng = np.random.default_rng(seed)
+    radii = []
+    total = 0.0
+    while total < grain_fraction * vol:
+        r = grain_radius * rng.uniform(1.0 - radius_spread, 1.0 + radius_spread)
+        radii.append(r)
+        total += 4.0 / 3.0 * math.pi * r ** 3
+    radii = np.asarray(radii)
+    centres = relaxed_spheres(n, radii, seed + 1)
+    # distance to the nearest and second-nearest grain surface, per voxel (grains stamped
+    # one at a time on their bounding boxes)
+    d1 = np.full(n, np.inf)
+    d2 = np.full(n, np.inf)
+    for c, r in zip(centres, radii):
+        reach = 1.5 * r + 2.0
+        idx = [np.arange(int(math.floor(c[a] - reach)), int(math.ceil(c[a] + reach)) + 1) for a in range(3)]
+        dd = None
+        for a in range(3):
+            da = (idx[a] + 0.5) - c[a]
+            sh = [1, 1, 1]
+            sh[a] = -1
+            t = (da * da).reshape(sh)
+            dd = t if dd is None else dd + t
+        dist = np.sqrt(dd) - r
+        sel = np.ix_(idx[0] % n[0], idx[1] % n[1], idx[2] % n[2])
+        cur1, cur2 = d1[sel], d2[sel]
+        new1 = np.minimum(cur1, dist)
+        new2 = np.minimum(cur2, np.maximum(cur1, dist))
+        d1[sel], d2[sel] = new1, new2
+    labels = np.zeros(n, dtype=np.uint8)
+    outside = d1 >= 0.0
+    k = int(round(binder_fraction * np.prod(n)))
+    if k > 0:
+        d2o = np.where(outside, d2, np.inf).reshape(-1)
+        order = np.argsort(d2o, kind="stable")[:k]
+        labels.reshape(-1)[order] = 2
+    labels[~outside] = 1
+    fr = [float(np.mean(labels == k)) for k in range(3)]
+    return labels, {"matrix": fr[0], "grain": fr[1], "binder": fr[2]}
+
 
 def config_single_sphere_32():
     """32^3 cell, gamma 1.0 matrix, one ball of radius 8 centred at (16, 16, 16) with gamma 0.1."""

@@ -26,6 +26,14 @@ def test_bytes_per_voxel_of_one_pass():
     assert plane == pytest.approx(172.0, abs=0.1)     # the fused plane pass
     # FP64 doubles every figure
     assert bench.bytes_per_voxel("k_update", 8, 512) == 208
+    # stored-divergence schedule: the first pass reads a, b (8 B), the update also writes them
+    assert bench.bytes_per_voxel("k_div_rfft_z", 4, 512, True) == 8 + (257 / 512) * 8
+    assert bench.bytes_per_voxel("k_update", 4, 512, True) == 112
+    half = (257 / 512) * 8
+    step = sum(bench.bytes_per_voxel(k, 4, 512, True)
+               for k in ("k_div_rfft_z", "k_fft_y_fwd", "k_fft_x_solve", "k_fft_y_inv", "k_irfft_z", "k_update"))
+    assert abs(step - (8 + half + 6 * half + half + 4 + 112)) < 1e-9
+    assert bench.basis_bytes_per_voxel(4) == 132 and bench.basis_bytes_per_voxel(8) == 264
 
 
 def test_traffic_lines_in_profiles_parse_and_are_found():

@@ -140,3 +140,20 @@ def test_boolean_and_fibre_generators():
     ff = float((gf > 1.0).mean())
     cyl = np.pi * 2.0 ** 2 * 32.0 / 64 ** 3
     assert nf > 0 and 0.06 <= ff <= 0.06 + 1.5 * cyl
+
+
+def test_relaxed_and_infinite_contrast_generators():
+    """Relaxed balls do not overlap (periodic distances >= sum of radii); the porous cell hits
+    its porosity with gamma 0 in the pores; the sand-binder cell has the phase fractions of
+    Sec. 4.6 (grains 58.6 %, binder 1.3 %, the rest the third phase)."""
+    r = np.full(30, 4.0)
+    x = M.relaxed_spheres((32, 32, 32), r, seed=3)
+    d = x[:, None, :] - x[None, :, :]
+    d -= 32.0 * np.round(d / 32.0)
+    dist = np.sqrt(np.sum(d * d, axis=-1)) + np.eye(30) * 1e9
+    assert dist.min() >= 8.0 - 2e-3
+    g, por = M.porous_spheres((48, 48, 48), 20, 0.4, seed=2)
+    assert abs(por - 0.4) < 0.01 and g.min() == 0.0 and g.max() == 1.0
+    labels, fr = M.sand_binder((48, 48, 48), 6.0, 0.586, 0.013, seed=6)
+    assert abs(fr["grain"] - 0.586) < 0.02 and abs(fr["binder"] - 0.013) < 1e-3
+    assert abs(fr["matrix"] + fr["grain"] + fr["binder"] - 1.0) < 1e-12

@@ -149,7 +149,7 @@ def basis_bytes_per_voxel(esize):
 
 def bytes_per_voxel(kernel, esize, n3, stored_div=False):
     """Algorithmic DRAM bytes per voxel of one launch of each loop kernel. stored_div: the
-    stored-divergence schedule (update variants 8, 9), whose first pass reads the two
+    stored-divergence schedule (update variants 8 - 10), whose first pass reads the two
     divergences a, b and whose update pass also writes them."""
     half = (n3 // 2 + 1) / n3 * 2 * esize  # half-spectrum bytes per voxel
     return {
@@ -165,8 +165,8 @@ def bytes_per_voxel(kernel, esize, n3, stored_div=False):
 
 
 def plan_stored_div(plan):
-    """True when the plan's update variant is the stored-divergence schedule (8 or 9)."""
-    return int(plan.tuning()["update_variant"]) >= 8
+    """True when the plan's update variant is the stored-divergence schedule (8, 9 or 10)."""
+    return 8 <= int(plan.tuning()["update_variant"]) <= 10
 
 
 def load_traffic(kernel, workload, precision, with_source=False):

@@ -184,7 +184,8 @@ int ccmf_kernel_times(const ccmf_plan* plan, double* ms, long long* launches, co
 
 /*
  * Launch shape the plan chose, for tests and reports: out[0..7] = {update-pass
- * variant (0 registers, 1 TMA rows, 2..7 pipelined TMA, 8..10 stored divergences), plane pass fused (0 / 1),
+ * variant (0 registers, 1 TMA rows, 2..7 pipelined TMA, 8..10 stored divergences, 11, 12 narrower registers),
+ * plane pass fused (0 / 1),
  * blocks sharing one (x, y) plane (1 = one block, 2..16 = a thread-block cluster),
  * z-pass line pairs per block, y-pass lines per block, x-pass lines per block,
  * update-pass blocks per solve, graph branches}. Writes min(capacity, 8) entries and
@@ -207,7 +208,9 @@ typedef struct {
                                the 12 state components; 8: 8 warps per block, 9: 16 warps with half
                                the voxels per lane, 10: 8 warps with half the voxels per lane and two
                                blocks per SM; needs N3 a multiple of 128 / 64 / 64 (variant 8 / 9 / 10,
-                               FP32) or 64 / 32 / 32 (FP64) */
+                               FP32) or 64 / 32 / 32 (FP64); 11 register vectors as 0 with half the
+                               voxels per thread, two blocks per SM; 12 one voxel per thread, three
+                               blocks per SM */
     int plane_blocks;       /* y / x passes: 0 three strided passes, 1 one block per (x, y) plane,
                                2, 4, 8, 16 a thread-block cluster per plane */
     int z_pairs_per_block;  /* divergence + forward z pass: line pairs per block, power of two 1..16 */

@@ -28,6 +28,7 @@ template <typename T> int plane_cluster_capacity(int, size_t);
 template <typename T> int lines_blocks_per_sm(int, int, size_t);
 template <typename T> int wlines_blocks_per_sm(int, int, size_t);
 template <typename T> int update_vec_blocks_per_sm();
+template <typename T> int update_vec_half_blocks_per_sm(int);
 template <typename T> int ab_blocks_per_sm(int, size_t);
 template <typename T> void launch_init(const Ctx<T>&, cudaStream_t);
 template <typename T> void launch_iteration(const Ctx<T>&, cudaStream_t);
@@ -48,10 +49,10 @@ constexpr size_t kSmemBudget = 96 * 1024;
 constexpr size_t kSmemMax = 200 * 1024;   // dynamic shared memory of one block, at most
 constexpr int kMaxTimedIters = 2048;
 // update-pass variant per precision, from measurements on GB300: register vectors in
-// ticket-ordered chunks (variant 0) in both. FP32 is bandwidth-bound: 0.248 ms per
-// 128^3 x 3 step against 0.253-0.256 ms with the pipelined variants, 2.41 ms per 512^3
-// pass against 4.1 TB/s for the pipelines. FP64 is ALU-bound.
-constexpr int kDefaultUpdateVariantF32 = 0;
+// ticket-ordered chunks. FP32 is bandwidth-bound: with half the voxels per thread and two
+// blocks per SM (variant 11) a 512^3 pass takes 2.37 ms against 2.41 ms (variant 0) and
+// 4.1 TB/s for the pipelines; at 128^3 x 3, 0.1525 against 0.1538 ms. FP64 is ALU-bound.
+constexpr int kDefaultUpdateVariantF32 = 11;
 constexpr int kDefaultUpdateVariantF64 = 0;
 // the captured loop runs the solves of a batch as up to this many independent graph
 // branches, so that one branch's FFT pass (on-chip work) overlaps another branch's
@@ -255,6 +256,7 @@ int shape_for(const ccmf_plan* pl, const ccmf_tuning& t, LaunchShape* out, ccmf_
     if (gu > 608) gu = 608;
     sh.grid_update = (int)gu;
     sh.vec_resident = (f64 ? update_vec_blocks_per_sm<double>() : update_vec_blocks_per_sm<float>()) * sms;
+    sh.vec_resident_half = 0;
     // TMA-staged update: tiles of J z rows with J * N3 <= 512 (FP32) / 256 (FP64) voxels,
     // J a power of two dividing N2; two stages must fit the shared memory of a block
     const int tv_max = f64 ? 256 : 512;
@@ -281,7 +283,14 @@ int shape_for(const ccmf_plan* pl, const ccmf_tuning& t, LaunchShape* out, ccmf_
     }
     if (variant >= kNumUpdateVariants) return CCMF_ERR_UNSUPPORTED_SIZE;
     sh.upd_variant = 0;
-    if (variant >= 8) {
+    if ((variant == 11 || variant == 12) && n3 % W == 0) {
+        // the vector update with half the voxels per thread, two blocks per SM (11), or one voxel
+        // per thread, three blocks per SM (12)
+        sh.upd_variant = variant;
+        sh.vec_resident_half = (f64 ? update_vec_half_blocks_per_sm<double>(variant)
+                                    : update_vec_half_blocks_per_sm<float>(variant)) * sms;
+    }
+    if (variant >= 8 && variant <= 10) {
         // stored-divergence update: whole z rows in passes of 32 VW voxels, a block of NW warps
         // (NW - 2 interior rows); x segments sized so that the blocks of a launch fill the
         // resident slots of the GPU in whole waves as far as possible
@@ -353,9 +362,12 @@ int shape_for(const ccmf_plan* pl, const ccmf_tuning& t, LaunchShape* out, ccmf_
     r.update_variant = sh.upd_variant;
     sh.grid_partials = std::max(sh.grid_update, sh.grid_tma);
     if (sh.upd_variant >= 2 && sh.upd_variant <= 7) sh.grid_partials = std::max(sh.grid_partials, sh.grid_pipe);
-    if (sh.upd_variant >= 8) sh.grid_partials = std::max(sh.grid_partials, sh.ab.nq * sh.ab.nr);
+    if (is_ab_variant(sh.upd_variant)) sh.grid_partials = std::max(sh.grid_partials, sh.ab.nq * sh.ab.nr);
     // the vector update pass (variant 0 and every final evaluation) keeps one slot per chunk
     sh.grid_partials = (int)std::max<long long>(sh.grid_partials, vec_update_chunks(pl->g.N, f64 ? 2 : 4));
+    if (sh.upd_variant == 11 || sh.upd_variant == 12)
+        sh.grid_partials = (int)std::max<long long>(sh.grid_partials,
+                                                    vec_update_chunks(pl->g.N, sh.upd_variant == 12 ? 1 : (f64 ? 1 : 2)));
     // y / x passes: one block per k_z plane when the plane fits its shared memory, a
     // cluster of C blocks (C divides n1 and n2) sharing the plane through distributed
     // shared memory, or the three strided passes
@@ -570,7 +582,7 @@ Ctx<T> make_ctx(const ccmf_plan* pl, unsigned char* ws, const T* gamma, long lon
     c.p.ab = reinterpret_cast<T*>(ws + pl->off_ab);
     // the stored-divergence schedule needs the vector loads of gamma (a per-solve pointer
     // table is aligned by the batch API's allocations of whole fields)
-    c.use_ab = pl->sh.upd_variant >= 8 && c.vec_update;
+    c.use_ab = is_ab_variant(pl->sh.upd_variant) && c.vec_update;
     return c;
 }
 
@@ -846,7 +858,7 @@ int tune_descent(ccmf_plan* plan, const std::function<int(double*)>& measure, do
     std::vector<int> brs;
     for (int b = 1; b <= std::min(kMaxBranches, plan->batch); ++b) brs.push_back(b);
     const Knob knobs[] = {
-        {&ccmf_tuning::update_variant, {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10}},
+        {&ccmf_tuning::update_variant, {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12}},
         {&ccmf_tuning::plane_blocks, {0, 1, 2, 4, 8, 16}},
         {&ccmf_tuning::z_pairs_per_block, {1, 2, 4, 8, 16}},
         {&ccmf_tuning::y_lines_per_block, {1, 2, 4, 8, 16}},
@@ -1327,7 +1339,8 @@ int ccmf_tuning_import(const char* text) {
 int ccmf_plan_launch_info(const ccmf_plan* plan, int* out, int capacity, int* count) {
     if (!plan || !count || (capacity > 0 && !out)) return CCMF_ERR_INVALID_ARG;
     const LaunchShape& sh = plan->sh;
-    const int grid_upd = sh.upd_variant >= 8   ? sh.ab.nq * sh.ab.nr
+    const int grid_upd = is_ab_variant(sh.upd_variant) ? sh.ab.nq * sh.ab.nr
+                         : (sh.upd_variant == 11 || sh.upd_variant == 12) ? sh.vec_resident_half / std::max(1, plan->batch)
                          : sh.upd_variant >= 2 ? sh.grid_pipe
                          : sh.upd_variant == 1 ? sh.grid_tma
                                                : sh.grid_update;

@@ -8,6 +8,7 @@ template int plane_cluster_capacity<float>(int, size_t);
 template int lines_blocks_per_sm<float>(int, int, size_t);
 template int wlines_blocks_per_sm<float>(int, int, size_t);
 template int update_vec_blocks_per_sm<float>();
+template int update_vec_half_blocks_per_sm<float>(int);
 template int ab_blocks_per_sm<float>(int, size_t);
 template void launch_init<float>(const Ctx<float>&, cudaStream_t);
 template void launch_iteration<float>(const Ctx<float>&, cudaStream_t);

@@ -8,6 +8,7 @@ template int plane_cluster_capacity<double>(int, size_t);
 template int lines_blocks_per_sm<double>(int, int, size_t);
 template int wlines_blocks_per_sm<double>(int, int, size_t);
 template int update_vec_blocks_per_sm<double>();
+template int update_vec_half_blocks_per_sm<double>(int);
 template int ab_blocks_per_sm<double>(int, size_t);
 template void launch_init<double>(const Ctx<double>&, cudaStream_t);
 template void launch_iteration<double>(const Ctx<double>&, cudaStream_t);

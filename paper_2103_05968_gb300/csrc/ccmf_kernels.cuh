@@ -911,6 +911,7 @@ __global__ void __launch_bounds__(kThreads) k_div_rfft_wz(Geom g, Ptrs<T> p, con
     C* twl = reinterpret_cast<C*>(smem_raw);
     C* lines = twl + N;
     warp_tw_fill<C, N>(twl, tw);
+    __syncthreads();   // the twiddle table is filled by all threads of the block, then read by every warp
     const T irho = T(1) / (T)p.sc[s].rho;
     const T h = T(0.70710678118654752440084436210485);
     const long long Nv = g.N;
@@ -1461,12 +1462,51 @@ __global__ void __launch_bounds__(kThreads) k_update(Geom g, Ptrs<T> p, LoopConf
     update_epilogue<T, OUT>(g, p, cfg, S, s, rho_d, acc);
 }
 
+// VW consecutive elements of the field type with one aligned load / store.
+template <typename T, int VW> struct VecN;
+template <> struct VecN<float, 4> {
+    __device__ __forceinline__ static void ld(const float* __restrict__ p, float (&o)[4]) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+        o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+    }
+    __device__ __forceinline__ static void st(float* p, const float (&o)[4]) {
+        *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+};
+template <> struct VecN<float, 2> {
+    __device__ __forceinline__ static void ld(const float* __restrict__ p, float (&o)[2]) {
+        const float2 t = __ldg(reinterpret_cast<const float2*>(p));
+        o[0] = t.x; o[1] = t.y;
+    }
+    __device__ __forceinline__ static void st(float* p, const float (&o)[2]) {
+        *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
+    }
+};
+template <> struct VecN<float, 1> {
+    __device__ __forceinline__ static void ld(const float* __restrict__ p, float (&o)[1]) { o[0] = __ldg(p); }
+    __device__ __forceinline__ static void st(float* p, const float (&o)[1]) { p[0] = o[0]; }
+};
+template <> struct VecN<double, 2> {
+    __device__ __forceinline__ static void ld(const double* __restrict__ p, double (&o)[2]) {
+        const double2 t = __ldg(reinterpret_cast<const double2*>(p));
+        o[0] = t.x; o[1] = t.y;
+    }
+    __device__ __forceinline__ static void st(double* p, const double (&o)[2]) {
+        *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+    }
+};
+template <> struct VecN<double, 1> {
+    __device__ __forceinline__ static void ld(const double* __restrict__ p, double (&o)[1]) { o[0] = __ldg(p); }
+    __device__ __forceinline__ static void st(double* p, const double (&o)[1]) { p[0] = o[0]; }
+};
+
 // Vector version of the advancing update: W consecutive voxels of a z line per
-// thread, 16-byte loads and stores (N3 % W == 0, 16-byte aligned gamma).
-template <typename T, bool OUT>
-__global__ void __launch_bounds__(kThreads) k_update_vec(Geom g, Ptrs<T> p, LoopConfig cfg) {
-    constexpr int W = Vec16<T>::W;
-    using V = Vec16<T>;
+// thread, 16-byte loads and stores (N3 % W == 0, 16-byte aligned gamma). The
+// instantiation with half the voxels per thread (8-byte vectors in FP32) needs about
+// half the registers and runs two blocks per SM (update variant 11).
+template <typename T, bool OUT, int W = Vec16<T>::W, int MINB = 1>
+__global__ void __launch_bounds__(kThreads, MINB) k_update_vec(Geom g, Ptrs<T> p, LoopConfig cfg) {
+    using V = VecN<T, W>;
     const int s = blockIdx.y + p.s0;
     SolveScalars& S = p.sc[s];
     if (!OUT && !S.active) return;
@@ -1609,39 +1649,6 @@ __global__ void __launch_bounds__(kThreads) k_update_vec(Geom g, Ptrs<T> p, Loop
 // warps, the z terms between lanes (across the passes of a row, the first and last
 // voxels of a pass are completed by a fix-up in the next pass / at the end of the row).
 // ---------------------------------------------------------------------------
-template <typename T, int VW> struct VecN;
-template <> struct VecN<float, 4> {
-    __device__ __forceinline__ static void ld(const float* __restrict__ p, float (&o)[4]) {
-        const float4 t = __ldg(reinterpret_cast<const float4*>(p));
-        o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
-    }
-    __device__ __forceinline__ static void st(float* p, const float (&o)[4]) {
-        *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
-    }
-};
-template <> struct VecN<float, 2> {
-    __device__ __forceinline__ static void ld(const float* __restrict__ p, float (&o)[2]) {
-        const float2 t = __ldg(reinterpret_cast<const float2*>(p));
-        o[0] = t.x; o[1] = t.y;
-    }
-    __device__ __forceinline__ static void st(float* p, const float (&o)[2]) {
-        *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
-    }
-};
-template <> struct VecN<double, 2> {
-    __device__ __forceinline__ static void ld(const double* __restrict__ p, double (&o)[2]) {
-        const double2 t = __ldg(reinterpret_cast<const double2*>(p));
-        o[0] = t.x; o[1] = t.y;
-    }
-    __device__ __forceinline__ static void st(double* p, const double (&o)[2]) {
-        *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
-    }
-};
-template <> struct VecN<double, 1> {
-    __device__ __forceinline__ static void ld(const double* __restrict__ p, double (&o)[1]) { o[0] = __ldg(p); }
-    __device__ __forceinline__ static void st(double* p, const double (&o)[1]) { p[0] = o[0]; }
-};
-
 __host__ __device__ constexpr size_t ab_smem_elems(int tj, int n3, int nw, int vw) {
     return 4 * (size_t)tj * n3 + 2 * (size_t)nw * 4 * 32 * vw;
 }

@@ -188,6 +188,26 @@ int update_vec_blocks_per_sm() {
     return m < 1 ? 1 : m;
 }
 
+// Update variant 11: the vector update pass with half the voxels per thread, two blocks per SM.
+template <typename T>
+constexpr int kVecHalfW = Vec16<T>::W / 2;
+
+// Resident blocks per SM of update variant 11 (12: one voxel per thread, three blocks per SM),
+// at least 1.
+template <typename T>
+int update_vec_half_blocks_per_sm(int variant) {
+    int a = 0;
+    const cudaError_t e =
+        variant == 12
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_update_vec<T, false, 1, 3>, kThreads, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_update_vec<T, false, kVecHalfW<T>, 2>, kThreads, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return a < 1 ? 1 : a;
+}
+
 // Blocks per SM of a warp-per-line pass of length n (power of two 128 ... 1024), 0 on error.
 template <typename T>
 int wlines_blocks_per_sm(int mode, int n, size_t smem) {
@@ -287,7 +307,9 @@ cudaError_t configure_kernels(const LaunchShape& sh) {
         set((const void*)k_update_tma<T, 1>, sh.smem_tma);
         set((const void*)k_update_tma<T, 2>, sh.smem_tma);
     }
-    if (sh.upd_variant >= 8) { CCMF_DISPATCH_AB(sh.upd_variant, { set((const void*)k_update_ab<T, AV>, sh.smem_ab); }); }
+    if (is_ab_variant(sh.upd_variant)) {
+        CCMF_DISPATCH_AB(sh.upd_variant, { set((const void*)k_update_ab<T, AV>, sh.smem_ab); });
+    }
     if (sh.upd_variant >= 2 && sh.upd_variant <= 7) {
         CCMF_DISPATCH_PIPE(sh.upd_variant, {
             set((const void*)k_update_pipe<T, 0, ST, NTH>, sh.smem_pipe);
@@ -460,7 +482,14 @@ void launch_passes(const Ctx<T>& c, const Ptrs<T>& p, cudaStream_t st, F&& betwe
         else
             k_update_tma<T, 1><<<gt, kThreads, sh.smem_tma, st>>>(g, p, c.cfg, sh.tma_rows);
     }
-    else if (c.vec_update)
+    else if (c.vec_update && (sh.upd_variant == 11 || sh.upd_variant == 12)) {
+        const int vpb2 = sh.vec_resident_half > 0 ? sh.vec_resident_half / g.batch : sh.grid_update;
+        const dim3 gv2((unsigned)(vpb2 < 1 ? 1 : vpb2), (unsigned)g.batch);
+        if (sh.upd_variant == 12)
+            k_update_vec<T, false, 1, 3><<<gv2, kThreads, 0, st>>>(g, p, c.cfg);
+        else
+            k_update_vec<T, false, kVecHalfW<T>, 2><<<gv2, kThreads, 0, st>>>(g, p, c.cfg);
+    } else if (c.vec_update)
         k_update_vec<T, false><<<gv, kThreads, 0, st>>>(g, p, c.cfg);
     else
         k_update<T, false><<<gu, kThreads, 0, st>>>(g, p, c.cfg);

@@ -110,6 +110,7 @@ struct LaunchShape {
     int lpb_y, lpb_x;         // strided passes: lines per block
     int grid_update;          // blocks per solve of the voxel passes
     int vec_resident;         // resident blocks of the vector update pass on the whole GPU
+    int vec_resident_half;    // the same for update variants 11, 12 (fewer voxels per thread)
     size_t smem_z, smem_y, smem_x;
     int tma_rows;             // TMA-staged update: z rows per tile (0 = path not available)
     int grid_tma;             // blocks per solve of the TMA-staged update
@@ -144,6 +145,7 @@ template <> struct AbVariant<float, 10> { static constexpr int NW = 8, VW = 2, M
 template <> struct AbVariant<double, 8> { static constexpr int NW = 8, VW = 2, MINB = 1; };
 template <> struct AbVariant<double, 9> { static constexpr int NW = 16, VW = 1, MINB = 1; };
 template <> struct AbVariant<double, 10> { static constexpr int NW = 8, VW = 1, MINB = 2; };
-constexpr int kNumUpdateVariants = 11;
+constexpr int kNumUpdateVariants = 13;
+__host__ __device__ constexpr bool is_ab_variant(int v) { return v >= 8 && v <= 10; }
 
 }  // namespace ccmf

@@ -116,9 +116,30 @@ def test_fp32_stored_divergence_against_default_schedule(variant):
     assert np.abs(v1[2].cpu().numpy() - v_ref).max() <= 1e-5 * sc
 
 
+@pytest.mark.parametrize("variant", [8, 9, 10])
+def test_fp32_stored_divergence_warp_z_passes(variant):
+    """The first pass as one warp per line pair (z engine 2) reading the stored divergences,
+    N3 = 128 and 256: FP32 against the default update pass with the same FFT passes over
+    several iterations (gamma_eff within 1e-5, state within FP32 noise)."""
+    for shape in ((48, 40, 128), (30, 24, 256)):
+        gamma = M.boolean_spheres(shape, 3.0, 0.2, 0.3, 1.0, seed=43)[0]
+        out = []
+        for var in (0, variant):
+            plan = ccmf.Plan(shape, batch=1, precision=ccmf.CCMF_FP32_MIXED, device=DEV)
+            plan.set_tuning(update_variant=var, z_engine=2, line_engine=0, plane_blocks=0)
+            res, _, _ = plan.solve(torch.from_numpy(gamma.astype(np.float32)).to(DEV), [[0, 0, 1]],
+                                   ccmf.Params(fixed_iters=20))
+            e, _, _, _ = plan.state()
+            out.append((res[0]["gamma_eff"], e[0].cpu().numpy()))
+            plan.close()
+        assert np.isfinite(out[1][0])
+        assert abs(out[1][0] - out[0][0]) <= 1e-5 * abs(out[0][0])
+        assert np.abs(out[1][1] - out[0][1]).max() <= 1e-4 * np.abs(out[0][1]).max()
+
+
 def test_stored_divergence_unavailable_grids_are_rejected():
     plan = ccmf.Plan((16, 16, 48), batch=1, precision=ccmf.CCMF_FP32_MIXED, device=DEV)
-    for bad in (8, 9, 10, 11):   # N3 = 48 is not a multiple of 128 / 64; 11 is no variant
+    for bad in (8, 9, 10, 13):   # N3 = 48 is not a multiple of 128 / 64; 13 is no variant
         with pytest.raises(ccmf.CCMFError) as err:
             plan.set_tuning(update_variant=bad)
         assert err.value.code == ccmf.CCMF_ERR_UNSUPPORTED_SIZE

@@ -33,6 +33,9 @@ TUNINGS = [
     dict(update_variant=3, plane_blocks=2, z_pairs_per_block=4, radix_mode=2, branches=1),
     dict(update_variant=7, plane_blocks=4, branches=3, radix_mode=1),
     dict(update_variant=5, plane_blocks=0, y_lines_per_block=16, x_lines_per_block=1, radix_mode=2, branches=2),
+    dict(update_variant=11, plane_blocks=1, branches=3),
+    dict(update_variant=12, plane_blocks=0, branches=1),
+    dict(update_variant=9, plane_blocks=0, branches=2),
 ]
 
 
@@ -62,6 +65,7 @@ def test_infeasible_tuning_is_rejected_and_kept():
     plan = ccmf.Plan((40, 24, 12), batch=1, precision=ccmf.CCMF_FP32_MIXED, device=DEV)
     before = plan.tuning()
     for bad in (dict(plane_blocks=16), dict(plane_blocks=3), dict(z_pairs_per_block=3), dict(update_variant=9),
+                dict(update_variant=13),
                 dict(branches=5), dict(radix_mode=7)):
         with pytest.raises(ccmf.CCMFError) as err:
             plan.set_tuning(**bad)

@@ -165,8 +165,9 @@ def bytes_per_voxel(kernel, esize, n3, stored_div=False):
 
 
 def plan_stored_div(plan):
-    """True when the plan's update variant is the stored-divergence schedule (8, 9 or 10)."""
-    return 8 <= int(plan.tuning()["update_variant"]) <= 10
+    """True when the plan's update variant is the stored-divergence schedule (8 .. 10, 13 .. 15)."""
+    v = int(plan.tuning()["update_variant"])
+    return 8 <= v <= 10 or 13 <= v <= 15
 
 
 def load_traffic(kernel, workload, precision, with_source=False):

@@ -184,7 +184,8 @@ int ccmf_kernel_times(const ccmf_plan* plan, double* ms, long long* launches, co
 
 /*
  * Launch shape the plan chose, for tests and reports: out[0..7] = {update-pass
- * variant (0 registers, 1 TMA rows, 2..7 pipelined TMA, 8..10 stored divergences, 11, 12 narrower registers),
+ * variant (0 registers, 1 TMA rows, 2..7 pipelined TMA, 8..10 and 13..15 stored divergences, 11, 12
+ * narrower registers),
  * plane pass fused (0 / 1),
  * blocks sharing one (x, y) plane (1 = one block, 2..16 = a thread-block cluster),
  * z-pass line pairs per block, y-pass lines per block, x-pass lines per block,
@@ -210,7 +211,10 @@ typedef struct {
                                blocks per SM; needs N3 a multiple of 128 / 64 / 64 (variant 8 / 9 / 10,
                                FP32) or 64 / 32 / 32 (FP64); 11 register vectors as 0 with half the
                                voxels per thread, two blocks per SM; 12 one voxel per thread, three
-                               blocks per SM */
+                               blocks per SM; 13 .. 15 the stored-divergence schedule with independent warps
+                               (each walks 8 rows of one z segment of 32 VW voxels; 13: VW = 4 (FP32) /
+                               2 (FP64), two blocks per SM; 14, 15: VW = 2 / 1, four / three blocks per
+                               SM; needs N3 a multiple of 32 VW) */
     int plane_blocks;       /* y / x passes: 0 three strided passes, 1 one block per (x, y) plane,
                                2, 4, 8, 16 a thread-block cluster per plane */
     int z_pairs_per_block;  /* divergence + forward z pass: line pairs per block, power of two 1..16 */

@@ -290,6 +290,42 @@ int shape_for(const ccmf_plan* pl, const ccmf_tuning& t, LaunchShape* out, ccmf_
         sh.vec_resident_half = (f64 ? update_vec_half_blocks_per_sm<double>(variant)
                                     : update_vec_half_blocks_per_sm<float>(variant)) * sms;
     }
+    if (is_abw_variant(variant)) {
+        // warp-independent stored-divergence update: an item is tj rows of one z segment of 32 VW
+        // voxels over an x segment; x segments sized like those of variants 8 .. 10
+        const int vw = f64 ? (variant == 13 ? AbwVariant<double, 13>::VW : AbwVariant<double, 14>::VW)
+                           : (variant == 13 ? AbwVariant<float, 13>::VW : AbwVariant<float, 14>::VW);
+        static_assert(AbwVariant<float, 14>::VW == AbwVariant<float, 15>::VW &&
+                          AbwVariant<double, 14>::VW == AbwVariant<double, 15>::VW,
+                      "variants 14 and 15 differ in blocks per SM only");
+        const int kz = 32 * vw, tj = 8;
+        const size_t smem = (size_t)kAbwWarps * 4 * tj * kz * pl->esize;
+        if (n3 % kz == 0 && smem <= kSmemMax) {
+            const int nb = f64 ? ab_blocks_per_sm<double>(variant, smem) : ab_blocks_per_sm<float>(variant, smem);
+            if (nb > 0) {
+                AbShape& a = sh.ab;
+                a.tj = tj;
+                a.nq = (n2 + tj - 1) / tj;
+                a.npass = n3 / kz;
+                const long long slots = (long long)nb * kAbwWarps * sms;
+                double best = -1.0;
+                for (int nr = 1; nr <= n1; ++nr) {
+                    const int xs = (n1 + nr - 1) / nr;
+                    if ((long long)(nr - 1) * xs >= n1) continue;
+                    const long long items = (long long)a.nq * nr * a.npass * batch;
+                    const long long waves = (items + slots - 1) / slots;
+                    const double eff = (double)n1 / ((double)nr * (xs + 2)) * (double)items / (double)(waves * slots);
+                    if (eff > best + 1e-9) {
+                        best = eff;
+                        a.nr = nr;
+                        a.xs = xs;
+                    }
+                }
+                sh.upd_variant = variant;
+                sh.smem_ab = smem;
+            }
+        }
+    }
     if (variant >= 8 && variant <= 10) {
         // stored-divergence update: whole z rows in passes of 32 VW voxels, a block of NW warps
         // (NW - 2 interior rows); x segments sized so that the blocks of a launch fill the
@@ -362,7 +398,11 @@ int shape_for(const ccmf_plan* pl, const ccmf_tuning& t, LaunchShape* out, ccmf_
     r.update_variant = sh.upd_variant;
     sh.grid_partials = std::max(sh.grid_update, sh.grid_tma);
     if (sh.upd_variant >= 2 && sh.upd_variant <= 7) sh.grid_partials = std::max(sh.grid_partials, sh.grid_pipe);
-    if (is_ab_variant(sh.upd_variant)) sh.grid_partials = std::max(sh.grid_partials, sh.ab.nq * sh.ab.nr);
+    if (is_abw_variant(sh.upd_variant))
+        sh.grid_partials = std::max<int>(sh.grid_partials,
+                                         (int)ceil_div((long long)sh.ab.nq * sh.ab.nr * sh.ab.npass, kAbwWarps));
+    else if (is_ab_variant(sh.upd_variant))
+        sh.grid_partials = std::max(sh.grid_partials, sh.ab.nq * sh.ab.nr);
     // the vector update pass (variant 0 and every final evaluation) keeps one slot per chunk
     sh.grid_partials = (int)std::max<long long>(sh.grid_partials, vec_update_chunks(pl->g.N, f64 ? 2 : 4));
     if (sh.upd_variant == 11 || sh.upd_variant == 12)
@@ -858,7 +898,7 @@ int tune_descent(ccmf_plan* plan, const std::function<int(double*)>& measure, do
     std::vector<int> brs;
     for (int b = 1; b <= std::min(kMaxBranches, plan->batch); ++b) brs.push_back(b);
     const Knob knobs[] = {
-        {&ccmf_tuning::update_variant, {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12}},
+        {&ccmf_tuning::update_variant, {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15}},
         {&ccmf_tuning::plane_blocks, {0, 1, 2, 4, 8, 16}},
         {&ccmf_tuning::z_pairs_per_block, {1, 2, 4, 8, 16}},
         {&ccmf_tuning::y_lines_per_block, {1, 2, 4, 8, 16}},
@@ -1339,7 +1379,8 @@ int ccmf_tuning_import(const char* text) {
 int ccmf_plan_launch_info(const ccmf_plan* plan, int* out, int capacity, int* count) {
     if (!plan || !count || (capacity > 0 && !out)) return CCMF_ERR_INVALID_ARG;
     const LaunchShape& sh = plan->sh;
-    const int grid_upd = is_ab_variant(sh.upd_variant) ? sh.ab.nq * sh.ab.nr
+    const int grid_upd = is_abw_variant(sh.upd_variant) ? (int)ceil_div((long long)sh.ab.nq * sh.ab.nr * sh.ab.npass, kAbwWarps)
+                         : is_ab_variant(sh.upd_variant) ? sh.ab.nq * sh.ab.nr
                          : (sh.upd_variant == 11 || sh.upd_variant == 12) ? sh.vec_resident_half / std::max(1, plan->batch)
                          : sh.upd_variant >= 2 ? sh.grid_pipe
                          : sh.upd_variant == 1 ? sh.grid_tma

@@ -1884,6 +1884,232 @@ __global__ void __launch_bounds__(AbVariant<T, VAR>::NW * 32, AbVariant<T, VAR>:
         update_finish<T, false, NT, true>(g, p, cfg, S, s, rho_d, part, nblocks);
 }
 
+// Warp-independent stored-divergence update (update variant 13). Each warp owns one item: tj
+// consecutive y rows of one z segment of KZ = 32 VW voxels, over an x segment of slabs. It
+// walks the slabs and, within a slab, the rows (the row before and after the tile are
+// recomputed), so the y terms of the new state's divergence wait one row (in registers) and the
+// x terms one slab (in the warp's own shared-memory slots); no warp waits for another. A z
+// segment shorter than the row recomputes the update of the voxel just before and just after it
+// (lanes 0 and 31) for the z terms at its ends.
+constexpr int kAbwWarps = 4;   // warps (items) per block
+
+template <typename T, int VW>
+__device__ __forceinline__ void abw_halo_voxel(const StepConsts<T>& K, const T* __restrict__ e,
+                                               const T* __restrict__ v, const T* __restrict__ phi,
+                                               const T* __restrict__ gam, long long N, long long row, long long rxp,
+                                               long long rxm, long long ryp, long long rym, int kh, int n3,
+                                               T (&eo)[6], T (&vo)[6]) {
+    const int kp = (kh + 1 == n3) ? 0 : kh + 1, km = (kh == 0) ? n3 - 1 : kh - 1;
+    T ec[6], vc[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        ec[c] = __ldg(e + c * N + row + kh);
+        vc[c] = __ldg(v + c * N + row + kh);
+    }
+    const T php[3] = {__ldg(phi + rxp + kh), __ldg(phi + ryp + kh), __ldg(phi + row + kp)};
+    const T phm[3] = {__ldg(phi + rxm + kh), __ldg(phi + rym + kh), __ldg(phi + row + km)};
+    const T e2p[3] = {__ldg(e + 3 * N + rxp + kh), __ldg(e + 4 * N + ryp + kh), __ldg(e + 5 * N + row + kp)};
+    const T v2p[3] = {__ldg(v + 3 * N + rxp + kh), __ldg(v + 4 * N + ryp + kh), __ldg(v + 5 * N + row + kp)};
+    const T e1m[3] = {__ldg(e + 0 * N + rxm + kh), __ldg(e + 1 * N + rym + kh), __ldg(e + 2 * N + row + km)};
+    const T v1m[3] = {__ldg(v + 0 * N + rxm + kh), __ldg(v + 1 * N + rym + kh), __ldg(v + 2 * N + row + km)};
+    T acc[kNSum], fl[3];
+    voxel_step<T, false>(K, ec, vc, __ldg(gam + row + kh), __ldg(phi + row + kh), php, phm, e2p, v2p, e1m, v1m,
+                         acc, eo, vo, fl, nullptr, false);
+}
+
+template <typename T, int VW, int MINB>
+__global__ void __launch_bounds__(kAbwWarps * 32, MINB) k_update_abw(Geom g, Ptrs<T> p, LoopConfig cfg, AbShape ab) {
+    constexpr int NT = kAbwWarps * 32, KZ = 32 * VW;
+    using V = VecN<T, VW>;
+    const int s = blockIdx.y + p.s0;
+    SolveScalars& S = p.sc[s];
+    if (!S.active) return;
+    const long long N = g.N;
+    const int n1 = g.n1, n2 = g.n2, n3 = g.n3;
+    const double rho_d = S.rho;
+    const StepConsts<T> K = step_consts<T>(S, cfg);
+    const T h = K.h;
+    const int par = S.iters & 1;
+    const T* __restrict__ e = p.e + (long long)par * p.sstride + (long long)s * 6 * N;
+    const T* __restrict__ v = p.v + (long long)par * p.sstride + (long long)s * 6 * N;
+    T* __restrict__ e_out = p.e + (long long)(1 - par) * p.sstride + (long long)s * 6 * N;
+    T* __restrict__ v_out = p.v + (long long)(1 - par) * p.sstride + (long long)s * 6 * N;
+    const T* __restrict__ phi = p.phi + (size_t)s * N;
+    const T* __restrict__ gam = gamma_of(p, s);
+    T* __restrict__ a_out = p.ab + (size_t)s * 2 * N;
+    T* __restrict__ b_out = a_out + N;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int tj = ab.tj, npass = ab.npass;
+    // item = (x segment r, y tile q, z segment zs), z segments fastest, then y tiles
+    const long long item = (long long)blockIdx.x * kAbwWarps + w;
+    const int zs = (int)(item % npass);
+    const long long rest = item / npass;
+    const int q = (int)(rest % ab.nq), r = (int)(rest / ab.nq);
+    const bool have = r < ab.nr;   // warp-uniform
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // this warp's slots, [row][u][lane]: pending a and b of the current slab, the component 1x of
+    // e' and v' of the previous slab
+    T* pe = reinterpret_cast<T*>(smem_raw) + (size_t)w * 4 * tj * KZ;
+    T* pv = pe + (size_t)tj * KZ;
+    T* ex = pv + (size_t)tj * KZ;
+    T* vx = ex + (size_t)tj * KZ;
+    T acc[kNSum];
+#pragma unroll
+    for (int qq = 0; qq < kNSum; ++qq) acc[qq] = T(0);
+    if (have) {
+        const int j0 = q * tj, nint = min(tj, n2 - j0);
+        const int i0 = r * ab.xs, i1 = min(i0 + ab.xs, n1);
+        const int seg0 = zs * KZ, k0 = seg0 + lane * VW;
+        const int kp = (k0 + VW == n3) ? 0 : k0 + VW, km = (k0 == 0) ? n3 - 1 : k0 - 1;
+        const int khb = (seg0 == 0) ? n3 - 1 : seg0 - 1;            // halo voxel before the segment (lane 0)
+        const int kha = (seg0 + KZ == n3) ? 0 : seg0 + KZ;          // halo voxel after it (lane 31)
+        for (int i = i0 - 1; i <= i1; ++i) {
+            const bool ring_lo = (i == i0 - 1), ring_hi = (i == i1), inner = !ring_lo && !ring_hi;
+            const int ii = (i < 0) ? i + n1 : (i >= n1 ? i - n1 : i);
+            const int ip = (ii + 1 == n1) ? 0 : ii + 1, im = (ii == 0) ? n1 - 1 : ii - 1;
+            T y1e[VW], y1v[VW];   // e'1y, v'1y of the previous row
+#pragma unroll
+            for (int u = 0; u < VW; ++u) y1e[u] = y1v[u] = T(0);
+            const int jr_lo = inner ? -1 : 0, jr_hi = inner ? nint : nint - 1;
+            for (int jr = jr_lo; jr <= jr_hi; ++jr) {
+                int j = j0 + jr;
+                if (j < 0) j += n2;
+                if (j >= n2) j -= n2;
+                const int jp = (j + 1 == n2) ? 0 : j + 1, jm = (j == 0) ? n2 - 1 : j - 1;
+                const bool interior_row = jr >= 0 && jr < nint;
+                const bool count = inner && interior_row;
+                const long long row = ((long long)ii * n2 + j) * n3;
+                const long long rxp = ((long long)ip * n2 + j) * n3, rxm = ((long long)im * n2 + j) * n3;
+                const long long ryp = ((long long)ii * n2 + jp) * n3, rym = ((long long)ii * n2 + jm) * n3;
+                T eo[6][VW], vo[6][VW];
+                {
+                    T ec[6][VW], vc[6][VW];
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) {
+                        V::ld(e + c * N + row + k0, ec[c]);
+                        V::ld(v + c * N + row + k0, vc[c]);
+                    }
+                    T gm[VW], ph[VW];
+                    V::ld(gam + row + k0, gm);
+                    V::ld(phi + row + k0, ph);
+                    T e2x[VW], v2x[VW], e1x[VW], v1x[VW], e2y[VW], v2y[VW], e1y[VW], v1y[VW];
+                    T phxp[VW], phxm[VW], phyp[VW], phym[VW];
+                    V::ld(e + 3 * N + rxp + k0, e2x);
+                    V::ld(v + 3 * N + rxp + k0, v2x);
+                    V::ld(e + 0 * N + rxm + k0, e1x);
+                    V::ld(v + 0 * N + rxm + k0, v1x);
+                    V::ld(e + 4 * N + ryp + k0, e2y);
+                    V::ld(v + 4 * N + ryp + k0, v2y);
+                    V::ld(e + 1 * N + rym + k0, e1y);
+                    V::ld(v + 1 * N + rym + k0, v1y);
+                    V::ld(phi + rxp + k0, phxp);
+                    V::ld(phi + rxm + k0, phxm);
+                    V::ld(phi + ryp + k0, phyp);
+                    V::ld(phi + rym + k0, phym);
+                    const T e2z_after = __ldg(e + 5 * N + row + kp), v2z_after = __ldg(v + 5 * N + row + kp);
+                    const T e1z_before = __ldg(e + 2 * N + row + km), v1z_before = __ldg(v + 2 * N + row + km);
+                    const T ph_after = __ldg(phi + row + kp), ph_before = __ldg(phi + row + km);
+#pragma unroll
+                    for (int u = 0; u < VW; ++u) {
+                        T ecu[6], vcu[6];
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) {
+                            ecu[c] = ec[c][u];
+                            vcu[c] = vc[c][u];
+                        }
+                        const bool last = (u + 1 == VW), first = (u == 0);
+                        const T php[3] = {phxp[u], phyp[u], last ? ph_after : ph[(u + 1) % VW]};
+                        const T phm[3] = {phxm[u], phym[u], first ? ph_before : ph[(u + VW - 1) % VW]};
+                        const T e2p[3] = {e2x[u], e2y[u], last ? e2z_after : ec[5][(u + 1) % VW]};
+                        const T v2p[3] = {v2x[u], v2y[u], last ? v2z_after : vc[5][(u + 1) % VW]};
+                        const T e1m[3] = {e1x[u], e1y[u], first ? e1z_before : ec[2][(u + VW - 1) % VW]};
+                        const T v1m[3] = {v1x[u], v1y[u], first ? v1z_before : vc[2][(u + VW - 1) % VW]};
+                        T eou[6], vou[6], fl[3];
+                        voxel_step<T, false>(K, ecu, vcu, gm[u], ph[u], php, phm, e2p, v2p, e1m, v1m, acc, eou, vou,
+                                             fl, nullptr, count);
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) {
+                            eo[c][u] = eou[c];
+                            vo[c][u] = vou[c];
+                        }
+                    }
+                }
+                if (count) {
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) {
+                        V::st(e_out + c * N + row + k0, eo[c]);
+                        V::st(v_out + c * N + row + k0, vo[c]);
+                    }
+                }
+                // z neighbours of the voxels at the ends of the lane group: the neighbouring lanes, or at
+                // the ends of the segment the recomputed halo voxels (a whole row wraps within the warp)
+                T tme = __shfl_sync(0xffffffffu, eo[2][VW - 1], (lane + 31) & 31);
+                T tmv = __shfl_sync(0xffffffffu, vo[2][VW - 1], (lane + 31) & 31);
+                T tpe = __shfl_sync(0xffffffffu, eo[5][0], (lane + 1) & 31);
+                T tpv = __shfl_sync(0xffffffffu, vo[5][0], (lane + 1) & 31);
+                if (npass > 1 && count && (lane == 0 || lane == 31)) {
+                    T he[6], hv[6];
+                    abw_halo_voxel<T, VW>(K, e, v, phi, gam, N, row, rxp, rxm, ryp, rym, lane == 0 ? khb : kha, n3,
+                                          he, hv);
+                    if (lane == 0) {
+                        tme = he[2];
+                        tmv = hv[2];
+                    } else {
+                        tpe = he[5];
+                        tpv = hv[5];
+                    }
+                }
+                if (interior_row) {
+                    T fa[VW], fb[VW];
+#pragma unroll
+                    for (int u = 0; u < VW; ++u) {
+                        const size_t slot = (size_t)jr * KZ + u * 32 + lane;
+                        if (!ring_lo && i > i0) {   // a', b' of slab i - 1: its x+ terms are this slab's 2x
+                            fa[u] = pe[slot] + h * eo[3][u];
+                            fb[u] = pv[slot] + h * vo[3][u];
+                        }
+                        if (inner) {
+                            const T tm_e = (u > 0) ? eo[2][u - 1] : tme, tm_v = (u > 0) ? vo[2][u - 1] : tmv;
+                            const T tp_e = (u + 1 < VW) ? eo[5][u + 1] : tpe, tp_v = (u + 1 < VW) ? vo[5][u + 1] : tpv;
+                            const T la = (eo[0][u] + eo[1][u] + eo[2][u]) - (eo[3][u] + eo[4][u] + eo[5][u]);
+                            const T lb = (vo[0][u] + vo[1][u] + vo[2][u]) - (vo[3][u] + vo[4][u] + vo[5][u]);
+                            // pending until the next row (+2y) and the next slab (+2x)
+                            pe[slot] = h * (la + (tp_e - tm_e) - y1e[u] - ex[slot]);
+                            pv[slot] = h * (lb + (tp_v - tm_v) - y1v[u] - vx[slot]);
+                        }
+                        if (!ring_hi) {
+                            ex[slot] = eo[0][u];
+                            vx[slot] = vo[0][u];
+                        }
+                    }
+                    if (!ring_lo && i > i0) {
+                        const long long rprev = ((long long)im * n2 + j) * n3;
+                        V::st(a_out + rprev + k0, fa);
+                        V::st(b_out + rprev + k0, fb);
+                    }
+                }
+                if (inner && jr >= 1) {   // the previous (interior) row gets this row's 2y
+#pragma unroll
+                    for (int u = 0; u < VW; ++u) {
+                        const size_t slot = (size_t)(jr - 1) * KZ + u * 32 + lane;
+                        pe[slot] += h * eo[4][u];
+                        pv[slot] += h * vo[4][u];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < VW; ++u) {
+                    y1e[u] = eo[1][u];
+                    y1v[u] = vo[1][u];
+                }
+            }
+        }
+    }
+    const int nblocks = gridDim.x;
+    double* part = p.partial + (size_t)s * nblocks * kNSum;
+    if (block_partials<T, kNSum, NT>(acc, part, &S.counter, nblocks, blockIdx.x))
+        update_finish<T, false, NT, true>(g, p, cfg, S, s, rho_d, part, nblocks);
+}
+
 // The stored divergences a = div^- A* e, b = div^- A* v of the current state, for a
 // state that the stored-divergence update did not write (a new solve, an imported
 // state, a state advanced by another update pass). Skipped for solves whose stored

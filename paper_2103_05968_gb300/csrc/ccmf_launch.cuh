@@ -192,6 +192,20 @@ int update_vec_blocks_per_sm() {
 template <typename T>
 constexpr int kVecHalfW = Vec16<T>::W / 2;
 
+#define CCMF_DISPATCH_ABW(var, ...)                                                      \
+    do {                                                                                 \
+        if ((var) == 13) {                                                               \
+            using AW = AbwVariant<T, 13>;                                                \
+            __VA_ARGS__;                                                                 \
+        } else if ((var) == 14) {                                                        \
+            using AW = AbwVariant<T, 14>;                                                \
+            __VA_ARGS__;                                                                 \
+        } else {                                                                         \
+            using AW = AbwVariant<T, 15>;                                                \
+            __VA_ARGS__;                                                                 \
+        }                                                                                \
+    } while (0)
+
 // Resident blocks per SM of update variant 11 (12: one voxel per thread, three blocks per SM),
 // at least 1.
 template <typename T>
@@ -307,7 +321,9 @@ cudaError_t configure_kernels(const LaunchShape& sh) {
         set((const void*)k_update_tma<T, 1>, sh.smem_tma);
         set((const void*)k_update_tma<T, 2>, sh.smem_tma);
     }
-    if (is_ab_variant(sh.upd_variant)) {
+    if (is_abw_variant(sh.upd_variant)) {
+        CCMF_DISPATCH_ABW(sh.upd_variant, { set((const void*)k_update_abw<T, AW::VW, AW::MINB>, sh.smem_ab); });
+    } else if (is_ab_variant(sh.upd_variant)) {
         CCMF_DISPATCH_AB(sh.upd_variant, { set((const void*)k_update_ab<T, AV>, sh.smem_ab); });
     }
     if (sh.upd_variant >= 2 && sh.upd_variant <= 7) {
@@ -329,15 +345,20 @@ void launch_init(const Ctx<T>& c, cudaStream_t st) {
     if (c.use_ab) k_ab_init<T><<<grid, kThreads, 0, st>>>(c.g, c.p);
 }
 
-// Blocks per SM of the stored-divergence update variant 8, 9 or 10 (occupancy API), 0 on error.
+// Blocks per SM of the stored-divergence update variants 8 .. 10 and 13 .. 15 (occupancy API), 0 on error.
 template <typename T>
 int ab_blocks_per_sm(int variant, size_t smem) {
     const void* f = nullptr;
     int nt = 0;
-    CCMF_DISPATCH_AB(variant, {
-        f = (const void*)k_update_ab<T, AV>;
-        nt = 32 * AbVariant<T, AV>::NW;
-    });
+    if (is_abw_variant(variant)) {
+        CCMF_DISPATCH_ABW(variant, { f = (const void*)k_update_abw<T, AW::VW, AW::MINB>; });
+        nt = 32 * kAbwWarps;
+    } else {
+        CCMF_DISPATCH_AB(variant, {
+            f = (const void*)k_update_ab<T, AV>;
+            nt = 32 * AbVariant<T, AV>::NW;
+        });
+    }
     int nb = 0;
     if (raise_smem_limit(f, smem) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, nt, smem) != cudaSuccess) {
@@ -458,7 +479,13 @@ void launch_passes(const Ctx<T>& c, const Ptrs<T>& p, cudaStream_t st, F&& betwe
         k_update_vec<T, true><<<gv, kThreads, 0, st>>>(g, p, c.cfg);
     else if (OUT)
         k_update<T, true><<<gu, kThreads, 0, st>>>(g, p, c.cfg);
-    else if (ab) {
+    else if (ab && is_abw_variant(sh.upd_variant)) {
+        const long long items = (long long)sh.ab.nq * sh.ab.nr * sh.ab.npass;
+        const dim3 ga((unsigned)ceil_div(items, kAbwWarps), (unsigned)g.batch);
+        CCMF_DISPATCH_ABW(sh.upd_variant, {
+            k_update_abw<T, AW::VW, AW::MINB><<<ga, kAbwWarps * 32, sh.smem_ab, st>>>(g, p, c.cfg, sh.ab);
+        });
+    } else if (ab) {
         const dim3 ga((unsigned)(sh.ab.nq * sh.ab.nr), (unsigned)g.batch);
         CCMF_DISPATCH_AB(sh.upd_variant, {
             k_update_ab<T, AV><<<ga, AbVariant<T, AV>::NW * 32, sh.smem_ab, st>>>(g, p, c.cfg, sh.ab);

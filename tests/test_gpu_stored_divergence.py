@@ -1,4 +1,4 @@
-"""The stored-divergence schedule (update variants 8 and 9) against the oracle.
+"""The stored-divergence schedule (update variants 8, 9, 10 and 13 .. 15) against the oracle.
 
 The update pass writes a = div^- A* e and b = div^- A* v of the state it produces, and
 the first pass of the next iteration forms d = a - b / rho from them (Eq. 28, Eq. 30:
@@ -25,7 +25,7 @@ from paper_2103_05968_gb300 import microstructure as M  # noqa: E402
 DEV = "cuda:0"
 
 CASES = [
-    # (shape, normals): FP64 variant 8 runs 64-voxel z passes, variant 9 32-voxel passes
+    # (shape, normals): FP64 variants 8 and 13 run 64-voxel z passes, variants 9, 14, 15 32-voxel passes
     ((40, 24, 64), [[1, 0, 0], [0.36, 0.48, 0.8]]),
     ((20, 15, 128), [[0, 0, 1]]),
     ((9, 5, 256), [[0.6, 0.0, 0.8]]),
@@ -46,12 +46,12 @@ def _solve(gamma, normals, variant, params, precision=ccmf.CCMF_FP64):
     return plan, g, res, flow, cut, e, v, rho, iters
 
 
-@pytest.mark.parametrize("variant", [8, 9, 10])
+@pytest.mark.parametrize("variant", [8, 9, 10, 13, 14, 15])
 @pytest.mark.parametrize("case", range(len(CASES)))
 def test_fp64_stored_divergence_matches_oracle(variant, case):
     shape, normals = CASES[case]
-    if variant == 8 and shape[2] % 64:
-        pytest.skip("variant 8 needs N3 % 64 == 0 in FP64")
+    if variant in (8, 13) and shape[2] % 64:
+        pytest.skip("variants 8 and 13 need N3 % 64 == 0 in FP64")
     gamma = M.boolean_spheres(shape, 2.5, 0.2, 0.3, 1.0, seed=31 + case)[0]
     plan, g, res, flow, cut, e, v, rho, iters = _solve(gamma, normals, variant, ccmf.Params(fixed_iters=25))
     for s, n in enumerate(normals):
@@ -66,7 +66,7 @@ def test_fp64_stored_divergence_matches_oracle(variant, case):
     plan.close()
 
 
-@pytest.mark.parametrize("variant", [8, 9, 10])
+@pytest.mark.parametrize("variant", [8, 9, 10, 13, 14, 15])
 def test_stored_divergence_resume_and_import(variant):
     """Resume continues from the stored divergences bit for bit; an imported state gets its
     divergences recomputed and continues within rounding of the uninterrupted run."""
@@ -89,7 +89,7 @@ def test_stored_divergence_resume_and_import(variant):
     np.testing.assert_allclose(v2.cpu().numpy(), full[6].cpu().numpy(), rtol=0, atol=1e-12)
 
 
-@pytest.mark.parametrize("variant", [8, 9, 10])
+@pytest.mark.parametrize("variant", [8, 9, 10, 13, 14, 15])
 def test_fp32_stored_divergence_against_default_schedule(variant):
     """FP32-mixed 128^3 Boolean workload x 3 normals: the stored-divergence schedule against
     the default update at equal iterations (gamma_eff within 1e-5, fields within FP32
@@ -116,7 +116,7 @@ def test_fp32_stored_divergence_against_default_schedule(variant):
     assert np.abs(v1[2].cpu().numpy() - v_ref).max() <= 1e-5 * sc
 
 
-@pytest.mark.parametrize("variant", [8, 9, 10])
+@pytest.mark.parametrize("variant", [8, 9, 10, 13, 14, 15])
 def test_fp32_stored_divergence_warp_z_passes(variant):
     """The first pass as one warp per line pair (z engine 2) reading the stored divergences,
     N3 = 128 and 256: FP32 against the default update pass with the same FFT passes over
@@ -139,7 +139,7 @@ def test_fp32_stored_divergence_warp_z_passes(variant):
 
 def test_stored_divergence_unavailable_grids_are_rejected():
     plan = ccmf.Plan((16, 16, 48), batch=1, precision=ccmf.CCMF_FP32_MIXED, device=DEV)
-    for bad in (8, 9, 10, 13):   # N3 = 48 is not a multiple of 128 / 64; 13 is no variant
+    for bad in (8, 9, 10, 13, 14, 16):   # N3 = 48 is not a multiple of 128 / 64; 16 is no variant
         with pytest.raises(ccmf.CCMFError) as err:
             plan.set_tuning(update_variant=bad)
         assert err.value.code == ccmf.CCMF_ERR_UNSUPPORTED_SIZE

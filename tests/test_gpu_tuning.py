@@ -65,7 +65,7 @@ def test_infeasible_tuning_is_rejected_and_kept():
     plan = ccmf.Plan((40, 24, 12), batch=1, precision=ccmf.CCMF_FP32_MIXED, device=DEV)
     before = plan.tuning()
     for bad in (dict(plane_blocks=16), dict(plane_blocks=3), dict(z_pairs_per_block=3), dict(update_variant=9),
-                dict(update_variant=13),
+                dict(update_variant=13), dict(update_variant=16),
                 dict(branches=5), dict(radix_mode=7)):
         with pytest.raises(ccmf.CCMFError) as err:
             plan.set_tuning(**bad)

@@ -332,6 +332,14 @@ __device__ __forceinline__ void warp_tw_fill(C* twl, const C* __restrict__ tw) {
 // shared-memory round trip of the whole line.
 constexpr int kIoSmem = 0, kIoGlobal = 1, kIoReg = 2;
 
+// True for the layout the pass at sub-length NS reads when the passes before it were NS = 1 and 8,
+// both radix 8 (N >= 256): the NS = 8 pass stores that layout unpadded with an XOR swizzle (element p
+// at p ^ 8 when bit 6 of p is set) instead of at wpad(p).
+template <int N, int NS>
+__host__ __device__ constexpr bool warp_swizzled() {
+    return NS == 64 && N >= 256 && warp_radix<N, 1>() == 8 && warp_radix<N, 8>() == 8;
+}
+
 template <typename C, int N, int NS, int OFF, int IN = kIoSmem, int OUT = kIoSmem, bool CONJ = false>
 __device__ __forceinline__ void warp_stockham(C* x, const C* __restrict__ twl, int lane, C (&u)[N / 32],
                                               const C* gin = nullptr, C* gout = nullptr) {
@@ -359,6 +367,20 @@ __device__ __forceinline__ void warp_stockham(C* x, const C* __restrict__ twl, i
 #pragma unroll
                 for (int r = 0; r < R; ++r) v[b][r] = u[(32 * b + r * NB) / 32];
             }
+        } else if constexpr (warp_swizzled<N, NS>()) {
+            // the line as the NS = 8 pass left it: unpadded, position q + lane at (q + lane) ^ 8 when
+            // bit 6 of q is set (q = 32 b + r NB is a multiple of 32, so that bit is q's own)
+            const C* xl0 = x + lane;
+            const C* xl1 = x + (lane ^ 8);
+#pragma unroll
+            for (int b = 0; b < PER; ++b) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int q = 32 * b + r * NB;
+                    v[b][r] = ((q >> 6) & 1) ? xl1[q] : xl0[q];
+                }
+            }
+            __syncwarp();
         } else {
             const C* xl = x + wpad(lane);
 #pragma unroll
@@ -400,6 +422,24 @@ __device__ __forceinline__ void warp_stockham(C* x, const C* __restrict__ twl, i
                 for (int b = 0; b < PER; ++b) {
 #pragma unroll
                     for (int r = 0; r < R; ++r) xs[cpad(32 * b * R) + r] = v[b][r];
+                }
+            } else if constexpr (warp_swizzled<N, NS * R>()) {
+                // NS = 8, R = 8, read next by the NS = 64 pass: unpadded, element p at p ^ 8 when bit 6 of p
+                // is set. Here p = 64 (lane >> 3) + jm + 256 b + 8 r, so bit 6 is bit 3 of the lane: the
+                // lanes with it set write r ^ 1 in place of r. The 8-lane groups of a half-warp then use
+                // disjoint halves of the banks (the padded layout conflicts 2-way here).
+                const int jm = lane & 7, sw = (lane >> 3) & 1;
+                C* xe = x + (lane >> 3) * 64 + jm + 8 * sw;   // even r
+                C* xo = x + (lane >> 3) * 64 + jm - 8 * sw;   // odd r
+#pragma unroll
+                for (int b = 0; b < PER; ++b) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        if (r & 1)
+                            xo[256 * b + 8 * r] = v[b][r];
+                        else
+                            xe[256 * b + 8 * r] = v[b][r];
+                    }
                 }
             } else if constexpr (NS < 32) {
                 const int jm = lane & (NS - 1);

@@ -139,9 +139,7 @@ __global__ void __launch_bounds__(kThreads) k_init_stats(Geom g, Ptrs<T> p, Loop
     T tmin = T(INFINITY), tmax = T(-INFINITY), csum = T(0);
     double acc_sum = 0.0, acc_bad = 0.0;
     int cnt = 0;
-    const long long stride = (long long)gridDim.x * kThreads;
-    for (long long lin = (long long)blockIdx.x * kThreads + threadIdx.x; lin < g.N; lin += stride) {
-        const T x = gam[lin];
+    auto take = [&](T x) {
         if (!(x >= T(0)) || !isfinite(x)) {
             acc_bad += 1.0;
         } else {
@@ -154,6 +152,29 @@ __global__ void __launch_bounds__(kThreads) k_init_stats(Geom g, Ptrs<T> p, Loop
                 cnt = 0;
             }
         }
+    };
+    const long long stride = (long long)gridDim.x * kThreads;
+    const long long t0 = (long long)blockIdx.x * kThreads + threadIdx.x;
+    // 16-byte loads when gamma is 16-byte aligned and N a multiple of the vector width (every
+    // thread of the launch takes the same branch)
+    constexpr int W = 16 / (int)sizeof(T);
+    if (((uintptr_t)gam % 16) == 0 && g.N % W == 0) {
+        const long long nv = g.N / W;
+        for (long long q = t0; q < nv; q += stride) {
+            if constexpr (sizeof(T) == 4) {
+                const float4 x = __ldg(reinterpret_cast<const float4*>(gam) + q);
+                take(x.x);
+                take(x.y);
+                take(x.z);
+                take(x.w);
+            } else {
+                const double2 x = __ldg(reinterpret_cast<const double2*>(gam) + q);
+                take(x.x);
+                take(x.y);
+            }
+        }
+    } else {
+        for (long long lin = t0; lin < g.N; lin += stride) take(gam[lin]);
     }
     acc_sum += (double)csum;
     double acc_min = (double)tmin, acc_max = (double)tmax;
@@ -898,8 +919,17 @@ __global__ void __launch_bounds__(kPlaneClusterThreads, 1)
 // per k_z row, instead of a few lines per block. The divergence pass needs
 // N3 % 4 == 0 (FP32) / N3 % 2 == 0 (FP64) 16-byte groups, which power-of-two N3 >= 128 has.
 // ---------------------------------------------------------------------------
+// Blocks per SM the register budget of the divergence pass is sized for: four blocks of 256 threads
+// (64 registers; the pass's shared memory allows them too) up to N3 = 512 in FP32 and 256 in FP64, two
+// at 512 in FP64, one at 1024 (the register use of an unbounded build, so the bound only keeps it there).
+template <typename T, int N>
+constexpr int wz_min_blocks() {
+    return N >= 1024 ? 1 : (sizeof(T) == 4 || N <= 256) ? 4 : 2;
+}
+
 template <typename T, int N, bool AB = false>
-__global__ void __launch_bounds__(kThreads) k_div_rfft_wz(Geom g, Ptrs<T> p, const cx<T>* __restrict__ tw) {
+__global__ void __launch_bounds__(kThreads, wz_min_blocks<T, N>())
+    k_div_rfft_wz(Geom g, Ptrs<T> p, const cx<T>* __restrict__ tw) {
     using C = cx<T>;
     constexpr int NW = kThreads / 32;     // packed lines per block
     constexpr int RL = 2 * NW;            // real lines per block

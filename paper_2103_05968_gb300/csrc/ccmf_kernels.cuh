@@ -1914,7 +1914,7 @@ __global__ void __launch_bounds__(AbVariant<T, VAR>::NW * 32, AbVariant<T, VAR>:
         update_finish<T, false, NT, true>(g, p, cfg, S, s, rho_d, part, nblocks);
 }
 
-// Warp-independent stored-divergence update (update variant 13). Each warp owns one item: tj
+// Warp-independent stored-divergence update (update variants 13 .. 15). Each warp owns one item: tj
 // consecutive y rows of one z segment of KZ = 32 VW voxels, over an x segment of slabs. It
 // walks the slabs and, within a slab, the rows (the row before and after the tile are
 // recomputed), so the y terms of the new state's divergence wait one row (in registers) and the

@@ -434,6 +434,56 @@ def fibres512_record(args, dev):
             "l2": "inputs larger than L2: state 6.4 GB per step"}
 
 
+def batch192_record(args, dev):
+    """The batched workload (192 solves on grids of four shapes, one captured graph with one
+    branch per shape group) measured beside the default line: ms per step of a K-step call
+    (init, K iterations, final evaluation) and ms per iteration from the difference of a 2K-
+    and a K-step call, both on the 132 B/voxel basis over all voxels of the batch."""
+    import torch
+    from paper_2103_05968_gb300 import ccmf
+    t_set = time.perf_counter()
+    fields, index, normals, shapes = batch_inputs(np.float32)
+    dfields = [torch.from_numpy(f).to(dev) for f in fields]
+    del fields
+    gammas = [dfields[r] for r in index]
+    vox = sum(int(np.prod(sh)) for sh in shapes)
+    batch = ccmf.Batch(shapes, precision=ccmf.CCMF_FP32_MIXED, device=dev)
+    K = min(max(args.steps // 10, 20), 200)
+    batch.solve(gammas, normals, ccmf.Params(fixed_iters=args.warmup, check_every=args.warmup))
+    tune = None
+    if not args.no_autotune:   # every shape group's launch shape, timed on its own solves
+        ms_groups = batch.autotune(gammas, normals, iters=max(10, args.tune_iters // 4))
+        tune = {"ms_per_iter_groups": ms_groups, "iters_per_candidate": max(10, args.tune_iters // 4)}
+    setup_s = time.perf_counter() - t_set
+    stream = torch.cuda.current_stream(dev)
+
+    def timed_call(iters):
+        p = ccmf.Params(fixed_iters=iters, check_every=iters)
+        batch.solve(gammas, normals, p, want_results=False)   # captures the graph for this length
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        batch.solve(gammas, normals, p, want_results=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1)
+
+    t_k = timed_call(K)
+    t_2k = timed_call(2 * K)
+    peak, peak_kind = load_peaks()
+    basis = basis_bytes_per_voxel(4) * vox
+    ms_step, ms_iter = t_k / K, (t_2k - t_k) / K
+    buckets = batch.buckets()
+    batch.close()
+    return {"workload": WORKLOADS["batch192"]["desc"] + " FP32-mixed (FP64 reductions)", "solves": len(shapes),
+            "voxels_per_step": vox, "steps": K, "ms_per_step": ms_step, "value": vox * K / (t_k * 1e-3),
+            "unit": UNIT, "step_frac_132": basis / (ms_step * 1e-3) / 1e9 / peak, "ms_per_iter": ms_iter,
+            "iter_frac_132": basis / (ms_iter * 1e-3) / 1e9 / peak, "buckets": buckets,
+            "launch": "one captured graph, one branch per shape group (per-shape sub-plans)",
+            "peak": peak, "peak_kind": peak_kind, "autotune": tune, "setup_seconds": setup_s,
+            "l2": f"inputs larger than L2: state {48 * vox / 1e9:.1f} GB per step"}
+
+
 def cufft_yardstick(shape, B, dev, reps=20):
     """cuFFT (torch.fft) R2C + C2R of the same B scalar grids: a yardstick beside the
     solver's own FFT passes, not used by the solver."""
@@ -736,6 +786,9 @@ def run_gpu(args, world, rank, local):
     fib = None
     if rank == 0 and world == 1 and name == "boolean128" and not args.grid and not args.no_fibres512:
         fib = fibres512_record(args, dev)
+    b192 = None
+    if rank == 0 and world == 1 and name == "boolean128" and not args.grid and not args.no_batch192:
+        b192 = batch192_record(args, dev)
 
     # kernels launched in the timed region: per iteration one launch of each pass per graph
     # branch, plus setup and gamma statistics, plus the passes of the final evaluation
@@ -757,6 +810,7 @@ def run_gpu(args, world, rank, local):
                             "final evaluation, results D2H"},
                 "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
                 "fp32_vs_fp64": tta, "cufft_yardstick": yard, "autotune": tune, "fibres512": fib,
+                "batch192": b192,
                 "gamma_eff": [r["gamma_eff"] for r in res]}
         print(json.dumps(line), flush=True)
     plan.close()
@@ -780,6 +834,8 @@ def main():
     ap.add_argument("--grid", default=None, help="N1xN2xN3 corner block of the workload's field (profiling cases)")
     ap.add_argument("--no-fibres512", action="store_true",
                     help="skip the 512^3 short-fibre record beside the default workload")
+    ap.add_argument("--no-batch192", action="store_true",
+                    help="skip the 192-solve batched record beside the default workload")
     ap.add_argument("--no-speedup", action="store_true",
                     help="skip the FP32-mixed vs FP64 time-to-accuracy measurement")
     args = ap.parse_args()

@@ -212,9 +212,9 @@ typedef struct {
                                FP32) or 64 / 32 / 32 (FP64); 11 register vectors as 0 with half the
                                voxels per thread, two blocks per SM; 12 one voxel per thread, three
                                blocks per SM; 13 .. 15 the stored-divergence schedule with independent warps
-                               (each walks 8 rows of one z segment of 32 VW voxels; 13: VW = 4 (FP32) /
-                               2 (FP64), two blocks per SM; 14, 15: VW = 2 / 1, four / three blocks per
-                               SM; needs N3 a multiple of 32 VW) */
+                               (each walks tj = 8, 4, 6 rows of one z segment of 32 VW voxels, VW = 4
+                               (FP32) / 2 (FP64), two blocks of 4 warps per SM; needs N3 a multiple of
+                               32 VW) */
     int plane_blocks;       /* y / x passes: 0 three strided passes, 1 one block per (x, y) plane,
                                2, 4, 8, 16 a thread-block cluster per plane */
     int z_pairs_per_block;  /* divergence + forward z pass: line pairs per block, power of two 1..16 */

@@ -25,6 +25,21 @@ namespace ccmf {
 template <typename T> cudaError_t configure_kernels(const LaunchShape&);
 template <typename T> int pipe_blocks_per_sm(int, size_t);
 template <typename T> int plane_cluster_capacity(int, size_t);
+
+// Voxels per lane and rows per warp of the warp-independent stored-divergence update variant v.
+template <typename T>
+void abw_params(int v, int& vw, int& tj) {
+    if (v == 13) {
+        vw = AbwVariant<T, 13>::VW;
+        tj = AbwVariant<T, 13>::TJ;
+    } else if (v == 14) {
+        vw = AbwVariant<T, 14>::VW;
+        tj = AbwVariant<T, 14>::TJ;
+    } else {
+        vw = AbwVariant<T, 15>::VW;
+        tj = AbwVariant<T, 15>::TJ;
+    }
+}
 template <typename T> int lines_blocks_per_sm(int, int, size_t);
 template <typename T> int wlines_blocks_per_sm(int, int, size_t);
 template <typename T> int update_vec_blocks_per_sm();
@@ -293,12 +308,12 @@ int shape_for(const ccmf_plan* pl, const ccmf_tuning& t, LaunchShape* out, ccmf_
     if (is_abw_variant(variant)) {
         // warp-independent stored-divergence update: an item is tj rows of one z segment of 32 VW
         // voxels over an x segment; x segments sized like those of variants 8 .. 10
-        const int vw = f64 ? (variant == 13 ? AbwVariant<double, 13>::VW : AbwVariant<double, 14>::VW)
-                           : (variant == 13 ? AbwVariant<float, 13>::VW : AbwVariant<float, 14>::VW);
-        static_assert(AbwVariant<float, 14>::VW == AbwVariant<float, 15>::VW &&
-                          AbwVariant<double, 14>::VW == AbwVariant<double, 15>::VW,
-                      "variants 14 and 15 differ in blocks per SM only");
-        const int kz = 32 * vw, tj = 8;
+        int vw = 0, tj = 0;
+        if (f64)
+            abw_params<double>(variant, vw, tj);
+        else
+            abw_params<float>(variant, vw, tj);
+        const int kz = 32 * vw;
         const size_t smem = (size_t)kAbwWarps * 4 * tj * kz * pl->esize;
         if (n3 % kz == 0 && smem <= kSmemMax) {
             const int nb = f64 ? ab_blocks_per_sm<double>(variant, smem) : ab_blocks_per_sm<float>(variant, smem);

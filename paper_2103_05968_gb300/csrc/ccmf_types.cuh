@@ -145,15 +145,17 @@ template <> struct AbVariant<float, 10> { static constexpr int NW = 8, VW = 2, M
 template <> struct AbVariant<double, 8> { static constexpr int NW = 8, VW = 2, MINB = 1; };
 template <> struct AbVariant<double, 9> { static constexpr int NW = 16, VW = 1, MINB = 1; };
 template <> struct AbVariant<double, 10> { static constexpr int NW = 8, VW = 1, MINB = 2; };
-// Warp-independent stored-divergence update variants 13, 14, 15: voxels per lane and z pass,
-// blocks (of 4 warps) per SM the register budget is sized for.
+// Warp-independent stored-divergence update variants 13, 14, 15: voxels per lane and z pass, blocks
+// (of 4 warps) per SM the register budget is sized for, y rows per warp. Fewer rows per warp recompute
+// more ring rows but stream fewer bytes per slab step across the resident warps, which decides
+// whether the x-neighbour rows of one step are still in L2 at the next.
 template <typename T, int VAR> struct AbwVariant;
-template <> struct AbwVariant<float, 13> { static constexpr int VW = 4, MINB = 2; };
-template <> struct AbwVariant<float, 14> { static constexpr int VW = 2, MINB = 4; };
-template <> struct AbwVariant<float, 15> { static constexpr int VW = 2, MINB = 3; };
-template <> struct AbwVariant<double, 13> { static constexpr int VW = 2, MINB = 2; };
-template <> struct AbwVariant<double, 14> { static constexpr int VW = 1, MINB = 4; };
-template <> struct AbwVariant<double, 15> { static constexpr int VW = 1, MINB = 3; };
+template <> struct AbwVariant<float, 13> { static constexpr int VW = 4, MINB = 2, TJ = 8; };
+template <> struct AbwVariant<float, 14> { static constexpr int VW = 4, MINB = 2, TJ = 4; };
+template <> struct AbwVariant<float, 15> { static constexpr int VW = 4, MINB = 2, TJ = 6; };
+template <> struct AbwVariant<double, 13> { static constexpr int VW = 2, MINB = 2, TJ = 8; };
+template <> struct AbwVariant<double, 14> { static constexpr int VW = 2, MINB = 2, TJ = 4; };
+template <> struct AbwVariant<double, 15> { static constexpr int VW = 2, MINB = 2, TJ = 6; };
 constexpr int kNumUpdateVariants = 16;
 __host__ __device__ constexpr bool is_abw_variant(int v) { return v >= 13 && v <= 15; }
 // update variants that write the stored divergences: 8 .. 10 (block-cooperative), 13 .. 15 (warp-independent)

@@ -210,8 +210,8 @@ typedef struct {
                                the voxels per lane, 10: 8 warps with half the voxels per lane and two
                                blocks per SM; needs N3 a multiple of 128 / 64 / 64 (variant 8 / 9 / 10,
                                FP32) or 64 / 32 / 32 (FP64); 11 register vectors as 0 with half the
-                               voxels per thread, two blocks per SM; 12 one voxel per thread, three
-                               blocks per SM; 13 .. 15 the stored-divergence schedule with independent warps
+                               voxels per thread, two blocks per SM; 12 the same with three blocks
+                               per SM; 13 .. 15 the stored-divergence schedule with independent warps
                                (each walks tj = 8, 4, 6 rows of one z segment of 32 VW voxels, VW = 4
                                (FP32) / 2 (FP64), two blocks of 4 warps per SM; needs N3 a multiple of
                                32 VW) */

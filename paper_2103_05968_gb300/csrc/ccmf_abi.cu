@@ -299,8 +299,8 @@ int shape_for(const ccmf_plan* pl, const ccmf_tuning& t, LaunchShape* out, ccmf_
     if (variant >= kNumUpdateVariants) return CCMF_ERR_UNSUPPORTED_SIZE;
     sh.upd_variant = 0;
     if ((variant == 11 || variant == 12) && n3 % W == 0) {
-        // the vector update with half the voxels per thread, two blocks per SM (11), or one voxel
-        // per thread, three blocks per SM (12)
+        // the vector update with half the voxels per thread (8-byte vectors in FP32), two blocks per
+        // SM (11) or three (12)
         sh.upd_variant = variant;
         sh.vec_resident_half = (f64 ? update_vec_half_blocks_per_sm<double>(variant)
                                     : update_vec_half_blocks_per_sm<float>(variant)) * sms;
@@ -422,7 +422,7 @@ int shape_for(const ccmf_plan* pl, const ccmf_tuning& t, LaunchShape* out, ccmf_
     sh.grid_partials = (int)std::max<long long>(sh.grid_partials, vec_update_chunks(pl->g.N, f64 ? 2 : 4));
     if (sh.upd_variant == 11 || sh.upd_variant == 12)
         sh.grid_partials = (int)std::max<long long>(sh.grid_partials,
-                                                    vec_update_chunks(pl->g.N, sh.upd_variant == 12 ? 1 : (f64 ? 1 : 2)));
+                                                    vec_update_chunks(pl->g.N, f64 ? 1 : 2));
     // y / x passes: one block per k_z plane when the plane fits its shared memory, a
     // cluster of C blocks (C divides n1 and n2) sharing the plane through distributed
     // shared memory, or the three strided passes

@@ -206,14 +206,14 @@ constexpr int kVecHalfW = Vec16<T>::W / 2;
         }                                                                                \
     } while (0)
 
-// Resident blocks per SM of update variant 11 (12: one voxel per thread, three blocks per SM),
-// at least 1.
+// Resident blocks per SM of update variant 11 (12: the same vectors, three blocks per SM), at
+// least 1.
 template <typename T>
 int update_vec_half_blocks_per_sm(int variant) {
     int a = 0;
     const cudaError_t e =
         variant == 12
-            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_update_vec<T, false, 1, 3>, kThreads, 0)
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_update_vec<T, false, kVecHalfW<T>, 3>, kThreads, 0)
             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_update_vec<T, false, kVecHalfW<T>, 2>, kThreads, 0);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -513,7 +513,7 @@ void launch_passes(const Ctx<T>& c, const Ptrs<T>& p, cudaStream_t st, F&& betwe
         const int vpb2 = sh.vec_resident_half > 0 ? sh.vec_resident_half / g.batch : sh.grid_update;
         const dim3 gv2((unsigned)(vpb2 < 1 ? 1 : vpb2), (unsigned)g.batch);
         if (sh.upd_variant == 12)
-            k_update_vec<T, false, 1, 3><<<gv2, kThreads, 0, st>>>(g, p, c.cfg);
+            k_update_vec<T, false, kVecHalfW<T>, 3><<<gv2, kThreads, 0, st>>>(g, p, c.cfg);
         else
             k_update_vec<T, false, kVecHalfW<T>, 2><<<gv2, kThreads, 0, st>>>(g, p, c.cfg);
     } else if (c.vec_update)

@@ -97,8 +97,8 @@ def test_autotune_keeps_the_fastest_and_records_it():
     again.close()
 
 
-@pytest.mark.parametrize("shape", [(128, 256, 4), (128, 96, 6), (96, 128, 6)],
-                         ids=["warp_xy", "warp_x_generic_y", "generic_x_warp_y"])
+@pytest.mark.parametrize("shape", [(128, 256, 4), (128, 96, 6), (96, 128, 6), (512, 64, 4), (64, 512, 4)],
+                         ids=["warp_xy", "warp_x_generic_y", "generic_x_warp_y", "x_512", "y_512"])
 @pytest.mark.parametrize("engine", [1, 0], ids=["warp_lines", "block_lines"])
 def test_fp64_line_passes_against_oracle(shape, engine):
     """Strided y / x passes with one warp per power-of-two line (natural order) or in-place

@@ -471,6 +471,123 @@ __device__ __forceinline__ void warp_stockham(C* x, const C* __restrict__ twl, i
     }
 }
 
+// ---------------------------------------------------------------------------
+// Register-resident 512-point DFT of one warp's line (512 = 32 lanes x 16 registers), with one
+// exchange through shared memory per transform instead of the two of the radix-8 Stockham passes.
+// With x[m], m = l + 32 k, held as u[k] by lane l:
+//   1. a 16-point DFT over k in each lane, then the twiddle W_512^{l k'};
+//   2. an exchange: lane L receives, for k' = L >> 1, the values of the lanes l = (L & 1) + 2 j;
+//   3. a 16-point DFT over j, then the radix-2 step between lanes L and L ^ 1 (twiddle W_32^q),
+// which leaves X[f] with f = (L >> 1) + 16 q + 256 (L & 1) in register q of lane L. The DFT matrix
+// is symmetric, so the transposed steps in reverse order take a line held in that order back to
+// natural order (again a forward DFT). Exchange rows of 34 elements make both sides of the
+// exchange conflict-free.
+// ---------------------------------------------------------------------------
+
+// cos(2 pi m / 32) and sin(2 pi m / 32) for 0 <= m < 32, from the first quadrant by symmetry
+__host__ __device__ constexpr double cos32_q(int r) {
+    return r == 0 ? 1.0
+         : r == 1 ? 0.98078528040323044913
+         : r == 2 ? 0.92387953251128675613
+         : r == 3 ? 0.83146961230254523708
+         : r == 4 ? 0.70710678118654752440
+         : r == 5 ? 0.55557023301960222474
+         : r == 6 ? 0.38268343236508977173
+         : r == 7 ? 0.19509032201612826785
+                  : 0.0;
+}
+__host__ __device__ constexpr double cos32(int m) {
+    return m <= 8 ? cos32_q(m) : m <= 16 ? -cos32_q(16 - m) : m <= 24 ? -cos32_q(m - 16) : cos32_q(32 - m);
+}
+__host__ __device__ constexpr double sin32(int m) { return cos32((m + 24) % 32); }
+
+// W_32^m = exp(-2 pi i m / 32) (m a compile-time value after unrolling)
+template <typename C>
+__device__ __forceinline__ C w32c(int m) {
+    using R = decltype(C::x);
+    return cmake<C>(R(cos32(m)), R(-sin32(m)));
+}
+
+// 16-point forward DFT in registers, natural order in and out: 4-point DFTs of the stride-4
+// subsequences, twiddles W_16^{a b'}, 4-point DFTs across them.
+template <typename C>
+__device__ __forceinline__ void dft16(C (&v)[16]) {
+    C t[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        C q[4] = {v[a], v[a + 4], v[a + 8], v[a + 12]};
+        Dft<C, 4>::run(q);
+#pragma unroll
+        for (int bp = 0; bp < 4; ++bp) t[a][bp] = (a * bp == 0) ? q[bp] : cmul(q[bp], w32c<C>(2 * a * bp));
+    }
+#pragma unroll
+    for (int bp = 0; bp < 4; ++bp) {
+        C q[4] = {t[0][bp], t[1][bp], t[2][bp], t[3][bp]};
+        Dft<C, 4>::run(q);
+#pragma unroll
+        for (int ap = 0; ap < 4; ++ap) v[bp + 4 * ap] = q[ap];
+    }
+}
+
+template <typename C>
+__device__ __forceinline__ C shfl_xor_cx(C a, int m) {
+    return cmake<C>(__shfl_xor_sync(0xffffffffu, a.x, m), __shfl_xor_sync(0xffffffffu, a.y, m));
+}
+
+constexpr int kReg512Row = 34;   // exchange row stride (16 rows: 544 elements of scratch per warp)
+
+// Natural order in (u[k] = x[lane + 32 k]), permuted order out (u[q] = X[(lane >> 1) + 16 q +
+// 256 (lane & 1)]). tw[k'] = W_512^{lane k'} (tw[0] unused). s: the warp's scratch; the caller has
+// finished its own reads of s before the call.
+template <typename C>
+__device__ __forceinline__ void fft512_to_perm(C (&u)[16], C* s, const C (&tw)[16], int lane) {
+    dft16(u);
+#pragma unroll
+    for (int kp = 1; kp < 16; ++kp) u[kp] = cmul(u[kp], tw[kp]);
+    __syncwarp();
+#pragma unroll
+    for (int kp = 0; kp < 16; ++kp) s[kp * kReg512Row + lane] = u[kp];
+    __syncwarp();
+    const C* sr = s + (lane >> 1) * kReg512Row + (lane & 1);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) u[j] = sr[2 * j];
+    dft16(u);
+    const bool odd = (lane & 1) != 0;
+    using R = decltype(C::x);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        // odd lanes hold O[q]: scale by W_32^q; then E + W O (even lane) and E - W O (odd lane)
+        const C w = odd ? w32c<C>(q) : cmake<C>(R(1), R(0));
+        const C mine = cmul(u[q], w);
+        const C other = shfl_xor_cx(mine, 1);
+        u[q] = odd ? csub(other, mine) : cadd(mine, other);
+    }
+}
+
+// Permuted order in (as fft512_to_perm leaves it), natural order out: the forward DFT of the
+// line, u[k] = Y[lane + 32 k]. The caller reads s only after a __syncwarp.
+template <typename C>
+__device__ __forceinline__ void fft512_from_perm(C (&u)[16], C* s, const C (&tw)[16], int lane) {
+    const bool odd = (lane & 1) != 0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        // even lane (a = X[k' + 16 q]): a + b; odd lane (b = X[k' + 16 (q + 16)]): W_32^q (a - b)
+        const C other = shfl_xor_cx(u[q], 1);
+        u[q] = odd ? cmul(csub(other, u[q]), w32c<C>(q)) : cadd(u[q], other);
+    }
+    dft16(u);
+    __syncwarp();
+    C* sw = s + (lane >> 1) * kReg512Row + (lane & 1);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) sw[2 * j] = u[j];
+    __syncwarp();
+#pragma unroll
+    for (int kp = 0; kp < 16; ++kp) u[kp] = s[kp * kReg512Row + lane];
+#pragma unroll
+    for (int kp = 1; kp < 16; ++kp) u[kp] = cmul(u[kp], tw[kp]);
+    dft16(u);
+}
+
 template <int N>
 __host__ __device__ constexpr bool warp_fft_ok() {
     return N >= 128 && N <= 1024 && (N & (N - 1)) == 0 && warp_tw_count<N>() <= N;

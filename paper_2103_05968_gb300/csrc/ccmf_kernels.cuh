@@ -660,6 +660,17 @@ __global__ void __launch_bounds__(kThreads, wlines_min_blocks<T, MODE, N>())
         C* const buf0 = twl + N;
         C* const buf1 = buf0 + (size_t)L * LS;
         const long long plane = (long long)g.n1 * g.n2;
+        // FP32 at N = 512: per-lane twiddles W_512^{lane k'} and the x symbol in the permuted order of
+        // fft512_to_perm, loaded once for all tiles
+        constexpr bool kReg512 = sizeof(T) == 4 && N == 512;
+        C tw512[16];
+        T xs512[16];
+        if constexpr (kReg512) {
+#pragma unroll
+            for (int kp = 0; kp < 16; ++kp) tw512[kp] = tw[(lane * kp) & (N - 1)];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) xs512[q] = xsym[(lane >> 1) + 16 * q + 256 * (lane & 1)];
+        }
         const long long nlines = (long long)g.n3h * g.n2;
         const long long ntiles = (nlines + L - 1) / L;
         // thread (cl, m0) moves elements m0 + 32 i of line cl of a tile (64-byte row
@@ -697,11 +708,6 @@ __global__ void __launch_bounds__(kThreads, wlines_min_blocks<T, MODE, N>())
             __syncthreads();
             const long long l0 = t * L;
             C* x = b + warp * LS;
-            // forward x FFT into registers (u[k] = X[lane + 32 k]), the Poisson gain,
-            // then the inverse from the same registers: the spectrum line does not
-            // go through shared memory in between
-            C u[N / 32];
-            warp_fft_to_regs<C, N>(x, twl, lane, u);
             const long long lw = l0 + warp;
             const bool valid = lw < nlines;
             int kz = 0, k2 = 0;
@@ -710,13 +716,37 @@ __global__ void __launch_bounds__(kThreads, wlines_min_blocks<T, MODE, N>())
                 k2 = (int)(lw - (long long)kz * g.n2);
             }
             const T lam23 = valid ? ysym[k2] + sym3[kz] : T(0);
+            if constexpr (kReg512) {
+                // the 512-point transforms in registers with one exchange each (fft512_to_perm /
+                // fft512_from_perm); the gain in the permuted order, symbol values per lane preloaded
+                C u[16];
 #pragma unroll
-            for (int k = 0; k < N / 32; ++k) {
-                const T lam = xsym[lane + 32 * k] + lam23;
-                const T gk = (valid && lam > T(0)) ? poisson_gain(inv_n, lam) : T(0);
-                u[k] = cmake<C>(u[k].x * gk, -u[k].y * gk);   // conj: the inverse runs as conj(FFT(conj(.)))
+                for (int k = 0; k < 16; ++k) u[k] = x[wpad(lane) + cpad(32 * k)];
+                fft512_to_perm(u, x, tw512, lane);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const T lam = xs512[q] + lam23;
+                    const T gk = (valid && lam > T(0)) ? poisson_gain(inv_n, lam) : T(0);
+                    u[q] = cmake<C>(u[q].x * gk, -u[q].y * gk);   // conj: the inverse runs as conj(FFT(conj(.)))
+                }
+                fft512_from_perm(u, x, tw512, lane);
+                __syncwarp();
+#pragma unroll
+                for (int k = 0; k < 16; ++k) x[wpad(lane) + cpad(32 * k)] = u[k];
+            } else {
+                // forward x FFT into registers (u[k] = X[lane + 32 k]), the Poisson gain,
+                // then the inverse from the same registers: the spectrum line does not
+                // go through shared memory in between
+                C u[N / 32];
+                warp_fft_to_regs<C, N>(x, twl, lane, u);
+#pragma unroll
+                for (int k = 0; k < N / 32; ++k) {
+                    const T lam = xsym[lane + 32 * k] + lam23;
+                    const T gk = (valid && lam > T(0)) ? poisson_gain(inv_n, lam) : T(0);
+                    u[k] = cmake<C>(u[k].x * gk, -u[k].y * gk);   // conj: the inverse runs as conj(FFT(conj(.)))
+                }
+                warp_fft_from_regs<C, N>(x, twl, lane, u);
             }
-            warp_fft_from_regs<C, N>(x, twl, lane, u);
             __syncthreads();
             const long long l = l0 + cl;
             if (l < nlines) {

@@ -91,6 +91,20 @@ def test_fp32_fibre_corner_block_one_step_512_tuning():
     print("512x512x128 FP32 one-step relative max errors (e, v):", worst)
 
 
+def test_fp32_x_lines_512_three_normals():
+    """FP32 x passes of length 512 (in FP32 the 512-point transforms of the x pass run in
+    registers with one shared-memory exchange each) on a 512 x 24 x 16 two-phase cell with
+    three normals, strided line passes: one step after 20 iterations against the oracle."""
+    gamma = M.random_two_phase((512, 24, 16), 0.3, 0.25, 1.0, 29)
+    normals = [[1, 0, 0], [0.36, 0.48, 0.8], [0, 0, 1]]
+    plan = ccmf.Plan(gamma.shape, batch=3, precision=ccmf.CCMF_FP32_MIXED, device=DEV)
+    plan.set_tuning(plane_blocks=0, line_engine=1)
+    assert plan.tuning()["plane_blocks"] == 0 and plan.tuning()["line_engine"] == 1
+    worst = one_step_against_oracle(gamma, normals, plan, 20, (0, 1, 2))
+    plan.close()
+    print("512x24x16 FP32 one-step relative max errors (e, v):", worst)
+
+
 def _one_weakest_layer():
     layers = np.array([1.0, 0.9, 1.2, 0.6, 1.1, 0.7, 1.4, 0.8] * 8)
     layers[37] = 0.4

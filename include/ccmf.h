@@ -353,6 +353,27 @@ int ccmf_batch_workspace_bytes(const ccmf_batch* batch, size_t* bytes);
 int ccmf_batch_autotune(ccmf_batch* batch, const void* const* gammas, const double* xi_bar, void* workspace,
                         size_t workspace_bytes, int iters, double* ms, void* stream);
 
+/*
+ * Launch mode of ccmf_batch_solve (spec batching pattern; the paper has no batched
+ * solver: each solve is the iteration of Eq. 30 with the stopping test of Eq. 31).
+ *   enable = 0 (default): one captured graph with one branch of per-shape sub-plan
+ *            passes per shape group (the launch shapes ccmf_batch_autotune picks);
+ *   enable = 1: one persistent kernel launch per iteration for the whole batch. Its
+ *            work items (pass, solve, tile) of the six passes of Eq. 28 / Eq. 30 (z
+ *            forward FFT with the divergence, y, x with the Poisson gain, y inverse, z
+ *            inverse, the update) sit in one device queue in pass-major order; resident
+ *            blocks take them in order, and an item waits (bounded) until the previous
+ *            pass of its solve has completed. A wait that runs out sets that solve's
+ *            status to CCMF_ERR_TIMEOUT and retires it. The FFT stages are the in-place /
+ *            Stockham block stages for every axis length, so results differ from the
+ *            graph mode by rounding only. Axes longer than 512 (FP32) / 256 (FP64) use
+ *            narrower tiles; a batch whose tiles do not fit shared memory returns
+ *            CCMF_ERR_UNSUPPORTED_SIZE from ccmf_batch_solve.
+ * The next ccmf_batch_solve captures its graph again. Returns CCMF_ERR_INVALID_ARG for
+ * a NULL batch or enable not in {0, 1}.
+ */
+int ccmf_batch_set_persistent(ccmf_batch* batch, int enable);
+
 /* Number of shape groups (sub-plans) of the batch. */
 int ccmf_batch_buckets(const ccmf_batch* batch, int* buckets);
 

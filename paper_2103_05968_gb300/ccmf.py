@@ -136,6 +136,7 @@ _SIGNATURES = {
     "ccmf_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "ccmf_batch_workspace_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     "ccmf_batch_buckets": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "ccmf_batch_set_persistent": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "ccmf_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
                                             ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_size_t,
                                             ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
@@ -341,6 +342,10 @@ def ccmf_batch_workspace_bytes(batch):
     b = ctypes.c_size_t()
     code = load_library().ccmf_batch_workspace_bytes(batch, ctypes.byref(b))
     return code, b.value
+
+
+def ccmf_batch_set_persistent(batch, enable):
+    return load_library().ccmf_batch_set_persistent(batch, int(enable))
 
 
 def ccmf_batch_buckets(batch):
@@ -599,6 +604,10 @@ class Batch:
             self.workspace_bytes = nbytes
             self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
         self.ws_ptr = (self.workspace.data_ptr() + 255) // 256 * 256
+
+    def set_persistent(self, enable=True):
+        """One persistent launch per iteration for the whole batch (ccmf_batch_set_persistent)."""
+        _check(ccmf_batch_set_persistent(self.handle, 1 if enable else 0), "ccmf_batch_set_persistent")
 
     def buckets(self):
         code, n = ccmf_batch_buckets(self.handle)

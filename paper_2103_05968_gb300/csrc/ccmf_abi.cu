@@ -55,6 +55,11 @@ template <typename T> void launch_adj_seed(const Ctx<T>&, T*, T*, SolveScalars*,
 template <typename T>
 void launch_adj_step(const Ctx<T>&, const T*, T*, T*, T*, T*, T*, const T*, SolveScalars*, T*, const double*, int, int,
                      cudaStream_t, const unsigned*);
+// the persistent batch kernel is instantiated in ccmf_f32.cu / ccmf_f64.cu only
+extern template int batch_persist_blocks_per_sm<float>(int, size_t);
+extern template int batch_persist_blocks_per_sm<double>(int, size_t);
+extern template void launch_batch_persist<float>(const PersistArgs<float>&, int, int, size_t, cudaStream_t);
+extern template void launch_batch_persist<double>(const PersistArgs<double>&, int, int, size_t, cudaStream_t);
 }  // namespace ccmf
 
 namespace {
@@ -1451,6 +1456,10 @@ struct ccmf_batch {
     bool have_graph;
     GraphKey gkey;
     int* h_active;                           // pinned, one counter per bucket
+    // the persistent launch (ccmf_batch_set_persistent): its tables in the workspace
+    int persistent;                          // 1: one k_batch_persist launch per iteration
+    size_t pers_groups_off, pers_map_off, pers_base_off, pers_done_off, pers_part_off;
+    std::vector<size_t> pers_part_b;         // each bucket's chunk partial slots (from pers_part_off)
 };
 
 namespace {
@@ -1464,6 +1473,116 @@ void batch_free(ccmf_batch* b) {
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     if (b->h_active) cudaFreeHost(b->h_active);
     delete b;
+}
+
+// The persistent launch of a batch: uploads the work-queue tables (group descriptors,
+// solve map, first item of every (pass, solve)) into the workspace and, when the key
+// changed, captures the loop graph: per iteration one memset of the queue counters and one
+// k_batch_persist launch over every solve of every shape group.
+template <typename T>
+int batch_persist_capture(ccmf_batch* bt, const std::vector<Ctx<T>>& ctx, unsigned char* ws, bool aligned,
+                          const GraphKey& key, const LoopConfig& cfg, cudaStream_t st) {
+    const int nb = (int)bt->plans.size();
+    const int ns = bt->count;
+    // tile shapes: the wider tiles unless some group's axis is too long for them
+    size_t smem = 0;
+    int variant = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        variant = pass;
+        smem = 0;
+        for (ccmf_plan* pl : bt->plans)
+            smem = std::max(smem, persist_smem_bytes<T>(pl->n1, pl->n2, pl->n3, kPersistTiles[variant][0],
+                                                        kPersistTiles[variant][1]));
+        if (smem <= 110 * 1024) break;
+    }
+    if (smem > 220 * 1024) return CCMF_ERR_UNSUPPORTED_SIZE;
+    const int P = kPersistTiles[variant][0], L = kPersistTiles[variant][1];
+    std::vector<PersistGroup<T>> groups(nb);
+    std::vector<int> sgroup, slocal;
+    for (int b = 0; b < nb; ++b) {
+        ccmf_plan* pl = bt->plans[b];
+        const Ctx<T>& c = ctx[b];
+        PersistGroup<T>& G = groups[b];
+        memset(&G, 0, sizeof(G));
+        G.g = c.g;
+        G.p = c.p;
+        G.p.s0 = 0;
+        G.p.run_all = 0;
+        G.p.partial = reinterpret_cast<double*>(ws + bt->pers_part_off + bt->pers_part_b[b]);
+        for (int a = 0; a < 3; ++a) {
+            G.ax[a] = c.ax[a];
+            G.tw[a] = c.tw[a];
+        }
+        G.rsym_x = c.rsym[0];
+        G.rsym_y = c.rsym[1];
+        G.sym_z = c.sym[2];
+        G.div_l = make_fastdiv((unsigned)L);
+        G.inv_n = (T)(1.0 / (double)c.g.N);
+        G.vec_div = c.vec_div ? 1 : 0;
+        G.upd_w = (sizeof(T) == 4 && aligned && pl->n3 % 2 == 0) ? 2 : 1;
+        G.nchunks = vec_update_chunks(c.g.N, G.upd_w);
+        const long long pairs = ceil_div((long long)pl->n1 * pl->n2, 2);
+        G.ntiles[0] = (int)ceil_div(pairs, P);
+        G.ntiles[1] = (int)ceil_div((long long)pl->n3h * pl->n1, L);
+        G.ntiles[2] = (int)ceil_div((long long)pl->n3h * pl->n2, L);
+        G.ntiles[3] = G.ntiles[1];
+        G.ntiles[4] = G.ntiles[0];
+        G.ntiles[5] = (int)G.nchunks;
+        for (int q = 0; q < pl->batch; ++q) {
+            sgroup.push_back(b);
+            slocal.push_back(q);
+        }
+    }
+    // first queue item of every (pass, solve), pass-major
+    std::vector<long long> base((size_t)kPersistPasses * ns + 1);
+    long long acc = 0;
+    for (int pass = 0; pass < kPersistPasses; ++pass)
+        for (int j = 0; j < ns; ++j) {
+            base[(size_t)pass * ns + j] = acc;
+            acc += groups[sgroup[j]].ntiles[pass];
+        }
+    base[(size_t)kPersistPasses * ns] = acc;
+    if (acc >= (1ll << 32) - (1ll << 24)) return CCMF_ERR_UNSUPPORTED_SIZE;   // the 32-bit ticket
+    if (cudaMemcpyAsync(ws + bt->pers_groups_off, groups.data(), sizeof(PersistGroup<T>) * nb, cudaMemcpyHostToDevice,
+                        st) != cudaSuccess ||
+        cudaMemcpyAsync(ws + bt->pers_map_off, sgroup.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(ws + bt->pers_map_off + sizeof(int) * ns, slocal.data(), sizeof(int) * ns,
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(ws + bt->pers_base_off, base.data(), sizeof(long long) * base.size(), cudaMemcpyHostToDevice,
+                        st) != cudaSuccess)
+        return CCMF_ERR_CUDA;
+    if (bt->have_graph && memcmp(&bt->gkey, &key, sizeof(key)) == 0) return CCMF_OK;
+    if (bt->have_graph) cudaGraphExecDestroy(bt->gexec);
+    bt->have_graph = false;
+    const int per_sm = batch_persist_blocks_per_sm<T>(variant, smem);
+    if (per_sm < 1) return CCMF_ERR_UNSUPPORTED_SIZE;
+    PersistArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    a.groups = reinterpret_cast<const PersistGroup<T>*>(ws + bt->pers_groups_off);
+    a.sgroup = reinterpret_cast<const int*>(ws + bt->pers_map_off);
+    a.slocal = a.sgroup + ns;
+    a.base = reinterpret_cast<const long long*>(ws + bt->pers_base_off);
+    a.done = reinterpret_cast<unsigned*>(ws + bt->pers_done_off);
+    a.head = a.done + (size_t)ns * kPersistPasses;
+    a.nsolve = ns;
+    a.cfg = cfg;
+    const size_t counters = sizeof(unsigned) * ((size_t)ns * kPersistPasses + 1);
+    const int grid = per_sm * bt->plans[0]->sms;
+    cudaGraph_t graph;
+    if (cudaStreamBeginCapture(bt->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CCMF_ERR_CUDA;
+    for (int it = 0; it < key.chunk; ++it) {
+        cudaMemsetAsync(a.done, 0, counters, bt->cap_stream);
+        launch_batch_persist<T>(a, variant, grid, smem, bt->cap_stream);
+    }
+    cudaError_t err = cudaStreamEndCapture(bt->cap_stream, &graph);
+    if (err != cudaSuccess) return CCMF_ERR_CUDA;
+    err = cudaGraphInstantiate(&bt->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (err != cudaSuccess) return CCMF_ERR_CUDA;
+    bt->gkey = key;
+    bt->have_graph = true;
+    return CCMF_OK;
 }
 
 template <typename T>
@@ -1482,6 +1601,10 @@ int batch_solve_impl(ccmf_batch* bt, const void* const* gammas, const double* xi
     cfg.rho_rule = prm->rho_rule;
     cfg.hist_len = prm->history_len;
     cfg.resume = 0;
+    {
+        const char* env = getenv("CCMF_DEBUG_SPIN_LIMIT");
+        cfg.spin_limit = env ? (unsigned)strtoul(env, nullptr, 10) + 1u : 0u;
+    }
     std::vector<Ctx<T>> ctx(nb);
     bool aligned = true;
     for (int b = 0; b < nb; ++b) {
@@ -1520,10 +1643,13 @@ int batch_solve_impl(ccmf_batch* bt, const void* const* gammas, const double* xi
     GraphKey key;
     memset(&key, 0, sizeof(key));
     key.chunk = chunk;
-    key.timed = aligned ? 2 : 3;   // records the alignment the captured kernels assume
+    key.timed = (bt->persistent ? 4 : 2) + (aligned ? 0 : 1);   // launch mode and the alignment assumed
     key.ws = ws;
     key.cfg = cfg;
-    if (!(bt->have_graph && memcmp(&bt->gkey, &key, sizeof(key)) == 0)) {
+    if (bt->persistent) {
+        const int rc = batch_persist_capture<T>(bt, ctx, ws, aligned, key, cfg, st);
+        if (rc != CCMF_OK) return rc;
+    } else if (!(bt->have_graph && memcmp(&bt->gkey, &key, sizeof(key)) == 0)) {
         if (bt->have_graph) cudaGraphExecDestroy(bt->gexec);
         bt->have_graph = false;
         cudaGraph_t graph;
@@ -1728,6 +1854,25 @@ int ccmf_batch_create(int count, const int* shapes, int precision, ccmf_batch** 
         bt->gp_off.push_back(off);
         off = align_up(off + sizeof(void*) * bt->members[b].size());
     }
+    // tables of the persistent launch (sized for either precision) and its chunk partial slots
+    // (one per chunk of kVecChunkGroups x kThreads voxels, the narrowest update vectors)
+    bt->pers_groups_off = off;
+    off = align_up(off + sizeof(PersistGroup<double>) * keys.size());
+    bt->pers_map_off = off;
+    off = align_up(off + 2 * sizeof(int) * (size_t)count);
+    bt->pers_base_off = off;
+    off = align_up(off + sizeof(long long) * ((size_t)kPersistPasses * count + 1));
+    bt->pers_done_off = off;
+    off = align_up(off + sizeof(unsigned) * ((size_t)kPersistPasses * count + 1));
+    bt->pers_part_off = off;
+    {
+        size_t po = 0;
+        for (ccmf_plan* pl : bt->plans) {
+            bt->pers_part_b.push_back(po);
+            po = align_up(po + sizeof(double) * kNSum * (size_t)pl->batch * (size_t)vec_update_chunks(pl->g.N, 1));
+        }
+        off = align_up(off + po);
+    }
     bt->total = off;
     int nev = 0;
     // join events for the largest branch count any tuning of the buckets may choose
@@ -1811,6 +1956,16 @@ int ccmf_batch_autotune(ccmf_batch* batch, const void* const* gammas, const doub
     unsigned char* ws = reinterpret_cast<unsigned char*>(workspace);
     if (batch->prec == CCMF_FP64) return batch_autotune_impl<double>(batch, gammas, xi_bar, ws, iters, ms, st);
     return batch_autotune_impl<float>(batch, gammas, xi_bar, ws, iters, ms, st);
+}
+
+int ccmf_batch_set_persistent(ccmf_batch* batch, int enable) {
+    if (!batch || (enable != 0 && enable != 1)) return CCMF_ERR_INVALID_ARG;
+    if (batch->persistent != enable) {
+        if (batch->have_graph) cudaGraphExecDestroy(batch->gexec);
+        batch->have_graph = false;
+        batch->persistent = enable;
+    }
+    return CCMF_OK;
 }
 
 int ccmf_batch_buckets(const ccmf_batch* batch, int* buckets) {

@@ -19,4 +19,6 @@ template void launch_adj_restore<float>(const Ctx<float>&, int, const double*, i
 template void launch_adj_seed<float>(const Ctx<float>&, float*, float*, SolveScalars*, cudaStream_t);
 template void launch_adj_step<float>(const Ctx<float>&, const float*, float*, float*, float*, float*, float*, const float*, SolveScalars*, float*,
                                    const double*, int, int, cudaStream_t, const unsigned*);
+template int batch_persist_blocks_per_sm<float>(int, size_t);
+template void launch_batch_persist<float>(const PersistArgs<float>&, int, int, size_t, cudaStream_t);
 }  // namespace ccmf

@@ -19,4 +19,6 @@ template void launch_adj_restore<double>(const Ctx<double>&, int, const double*,
 template void launch_adj_seed<double>(const Ctx<double>&, double*, double*, SolveScalars*, cudaStream_t);
 template void launch_adj_step<double>(const Ctx<double>&, const double*, double*, double*, double*, double*, double*, const double*, SolveScalars*, double*,
                                    const double*, int, int, cudaStream_t, const unsigned*);
+template int batch_persist_blocks_per_sm<double>(int, size_t);
+template void launch_batch_persist<double>(const PersistArgs<double>&, int, int, size_t, cudaStream_t);
 }  // namespace ccmf

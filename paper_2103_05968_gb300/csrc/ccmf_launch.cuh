@@ -2,6 +2,7 @@
 #pragma once
 
 #include "ccmf_kernels.cuh"
+#include "ccmf_persist.cuh"
 
 namespace ccmf {
 
@@ -612,6 +613,36 @@ void launch_adj_step(const Ctx<T>& c, const T* zk, T* ebar, T* vbar, T* zbar, T*
     cm.p.zout = nullptr;
     launch_final<T>(cm, st, my, nullptr);
     k_adj_post<T><<<grid, kThreads, 0, st>>>(c.g, zbar, my, sched, sched_len, k, b, ebar, vbar);
+}
+
+// Tile shapes of the batched persistent kernel: {z line pairs, y / x lines} per item.
+// Variant 0 for short axes, variant 1 where variant 0's tiles do not fit shared memory.
+constexpr int kPersistTiles[2][2] = {{8, 16}, {2, 4}};
+
+// Resident blocks per SM of k_batch_persist variant `variant` with `smem` bytes of dynamic
+// shared memory (raises the kernel's limit first), 0 on error.
+template <typename T>
+int batch_persist_blocks_per_sm(int variant, size_t smem) {
+    int nb = 0;
+    const void* f = variant == 0 ? (const void*)k_batch_persist<T, 8, 16> : (const void*)k_batch_persist<T, 2, 4>;
+    cudaError_t err = raise_smem_limit(f, smem);
+    if (err == cudaSuccess)
+        err = variant == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_persist<T, 8, 16>, kThreads, smem)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_persist<T, 2, 4>, kThreads, smem);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+// One persistent launch: every pass of one iteration of every solve of the batch.
+template <typename T>
+void launch_batch_persist(const PersistArgs<T>& a, int variant, int grid, size_t smem, cudaStream_t st) {
+    if (variant == 0)
+        k_batch_persist<T, 8, 16><<<grid, kThreads, smem, st>>>(a);
+    else
+        k_batch_persist<T, 2, 4><<<grid, kThreads, smem, st>>>(a);
 }
 
 }  // namespace ccmf

@@ -61,18 +61,21 @@ def make_gamma(name, dtype):
     raise ValueError(name)
 
 
-def batch_inputs(dtype, seed=2103):
-    """The 64 realisations of the batched workload: (fields, per-solve field index, normals, shapes)."""
+def batch_inputs(dtype, seed=2103, solves=192):
+    """The 64 realisations of the batched workload: (fields, per-solve field index, normals, shapes).
+    With solves < 192 only the first solves (and the realisations they use) are made."""
     from paper_2103_05968_gb300 import microstructure as M
     rng = np.random.default_rng(seed)
     fields = []
-    for r in range(64):
+    nreal = min(64, (solves + 2) // 3)
+    for r in range(nreal):
         n = int(rng.choice([64, 96, 128, 160]))
         vf = float(rng.uniform(0.10, 0.30))
         g, _ = M.boolean_spheres((n, n, n), 4.0, vf, 0.2, 1.0, seed=seed + 1 + r, radius_max=8.0, dtype=dtype)
         fields.append(g)
-    index = [r for r in range(64) for _ in range(3)]
-    normals = np.array([nv for _ in range(64) for nv in WORKLOADS["batch192"]["normals"]], dtype=np.float64)
+    index = [r for r in range(nreal) for _ in range(3)][:solves]
+    normals = np.array([nv for _ in range(nreal) for nv in WORKLOADS["batch192"]["normals"]],
+                       dtype=np.float64)[:solves]
     shapes = [fields[r].shape for r in index]
     return fields, index, normals, shapes
 
@@ -90,11 +93,13 @@ def run_batch(args, world, rank, local):
     prec = ccmf.CCMF_FP64 if args.precision == "fp64" else ccmf.CCMF_FP32_MIXED
     np_dtype = np.float64 if prec == ccmf.CCMF_FP64 else np.float32
     esize = 8 if prec == ccmf.CCMF_FP64 else 4
-    fields, index, normals, shapes = batch_inputs(np_dtype)
+    fields, index, normals, shapes = batch_inputs(np_dtype, solves=args.batch_solves)
     dfields = [torch.from_numpy(f).to(dev) for f in fields]
     gammas = [dfields[r] for r in index]
     vox = sum(int(np.prod(sh)) for sh in shapes)
     batch = ccmf.Batch(shapes, precision=prec, device=dev)
+    if args.batch_launch == "persistent":
+        batch.set_persistent(True)
     K, W = args.steps, args.warmup
     p = ccmf.Params(fixed_iters=K, check_every=K)
     tune = None
@@ -125,9 +130,10 @@ def run_batch(args, world, rank, local):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
                 "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if esize == 8 else "f32", "data": "synthetic",
-                "config": {"workload": WORKLOADS["batch192"]["desc"], "solves": len(shapes),
+                "config": {"workload": WORKLOADS["batch192"]["desc"] + (
+                               "" if len(shapes) == 192 else f" (first {len(shapes)} solves)"), "solves": len(shapes),
                            "voxels_per_step": vox, "buckets": batch.buckets(), "precision": args.precision,
-                           "l2": "inputs larger than L2"},
+                           "launch": args.batch_launch, "l2": "inputs larger than L2"},
                 "roofline": {"bound": "hbm", "achieved": step_bytes / (t_ms / K * 1e-3) / 1e9, "peak": peak,
                              "unit": "GB/s", "frac": step_bytes / (t_ms / K * 1e-3) / 1e9 / peak,
                              "traffic": None,
@@ -474,12 +480,22 @@ def batch192_record(args, dev):
     basis = basis_bytes_per_voxel(4) * vox
     ms_step, ms_iter = t_k / K, (t_2k - t_k) / K
     buckets = batch.buckets()
+    # the same solves in one persistent launch per iteration (one device work queue)
+    batch.set_persistent(True)
+    tp_k = timed_call(K)
+    tp_2k = timed_call(2 * K)
+    pms_step, pms_iter = tp_k / K, (tp_2k - tp_k) / K
+    persistent = {"launch": "one k_batch_persist launch per iteration: (pass, solve, tile) items of every "
+                            "solve from one device queue", "ms_per_step": pms_step,
+                  "value": vox * K / (tp_k * 1e-3), "step_frac_132": basis / (pms_step * 1e-3) / 1e9 / peak,
+                  "ms_per_iter": pms_iter, "iter_frac_132": basis / (pms_iter * 1e-3) / 1e9 / peak}
     batch.close()
     return {"workload": WORKLOADS["batch192"]["desc"] + " FP32-mixed (FP64 reductions)", "solves": len(shapes),
             "voxels_per_step": vox, "steps": K, "ms_per_step": ms_step, "value": vox * K / (t_k * 1e-3),
             "unit": UNIT, "step_frac_132": basis / (ms_step * 1e-3) / 1e9 / peak, "ms_per_iter": ms_iter,
             "iter_frac_132": basis / (ms_iter * 1e-3) / 1e9 / peak, "buckets": buckets,
             "launch": "one captured graph, one branch per shape group (per-shape sub-plans)",
+            "persistent": persistent,
             "peak": peak, "peak_kind": peak_kind, "autotune": tune, "setup_seconds": setup_s,
             "l2": f"inputs larger than L2: state {48 * vox / 1e9:.1f} GB per step"}
 
@@ -834,6 +850,11 @@ def main():
     ap.add_argument("--grid", default=None, help="N1xN2xN3 corner block of the workload's field (profiling cases)")
     ap.add_argument("--no-fibres512", action="store_true",
                     help="skip the 512^3 short-fibre record beside the default workload")
+    ap.add_argument("--batch-launch", default="graph", choices=["graph", "persistent"],
+                    help="--workload batch192: the branched graph of per-shape passes, or one persistent launch "
+                         "per iteration")
+    ap.add_argument("--batch-solves", type=int, default=192,
+                    help="--workload batch192: the first N solves only (small profiling cases)")
     ap.add_argument("--no-batch192", action="store_true",
                     help="skip the 192-solve batched record beside the default workload")
     ap.add_argument("--no-speedup", action="store_true",

@@ -1484,21 +1484,28 @@ int batch_persist_capture(ccmf_batch* bt, const std::vector<Ctx<T>>& ctx, unsign
                           const GraphKey& key, const LoopConfig& cfg, cudaStream_t st) {
     const int nb = (int)bt->plans.size();
     const int ns = bt->count;
-    // tile shapes: the wider tiles unless some group's axis is too long for them
+    // tile shapes: the wider tiles unless some group's axis is too long for them. Dynamic shared
+    // memory: the queue tables, the twiddle table of the longest axis, the largest tile buffers.
+    int maxn = 1;
+    for (ccmf_plan* pl : bt->plans) maxn = std::max(maxn, std::max(pl->n1, std::max(pl->n2, pl->n3)));
+    const size_t tw_off = persist_table_bytes(nb);
+    const size_t work_off = tw_off + align_up(sizeof(cx<T>) * (size_t)maxn, 16);
     size_t smem = 0;
     int variant = 0;
     for (int pass = 0; pass < 2; ++pass) {
         variant = pass;
-        smem = 0;
+        size_t wmax = 0;
         for (ccmf_plan* pl : bt->plans)
-            smem = std::max(smem, persist_smem_bytes<T>(pl->n1, pl->n2, pl->n3, kPersistTiles[variant][0],
+            wmax = std::max(wmax, persist_work_bytes<T>(pl->n1, pl->n2, pl->n3, kPersistTiles[variant][0],
                                                         kPersistTiles[variant][1]));
+        smem = work_off + wmax;
         if (smem <= 110 * 1024) break;
     }
     if (smem > 220 * 1024) return CCMF_ERR_UNSUPPORTED_SIZE;
     const int P = kPersistTiles[variant][0], L = kPersistTiles[variant][1];
     std::vector<PersistGroup<T>> groups(nb);
-    std::vector<int> sgroup, slocal;
+    std::vector<int> gstart(nb);
+    int first = 0;
     for (int b = 0; b < nb; ++b) {
         ccmf_plan* pl = bt->plans[b];
         const Ctx<T>& c = ctx[b];
@@ -1522,53 +1529,70 @@ int batch_persist_capture(ccmf_batch* bt, const std::vector<Ctx<T>>& ctx, unsign
         G.upd_w = (sizeof(T) == 4 && aligned && pl->n3 % 2 == 0) ? 2 : 1;
         G.nchunks = vec_update_chunks(c.g.N, G.upd_w);
         const long long pairs = ceil_div((long long)pl->n1 * pl->n2, 2);
-        G.ntiles[0] = (int)ceil_div(pairs, P);
-        G.ntiles[1] = (int)ceil_div((long long)pl->n3h * pl->n1, L);
-        G.ntiles[2] = (int)ceil_div((long long)pl->n3h * pl->n2, L);
-        G.ntiles[3] = G.ntiles[1];
-        G.ntiles[4] = G.ntiles[0];
-        G.ntiles[5] = (int)G.nchunks;
-        for (int q = 0; q < pl->batch; ++q) {
-            sgroup.push_back(b);
-            slocal.push_back(q);
+        G.tiles[0] = (int)ceil_div(pairs, P);
+        G.tiles[1] = (int)ceil_div((long long)pl->n3h * pl->n1, L);
+        G.tiles[2] = (int)ceil_div((long long)pl->n3h * pl->n2, L);
+        G.tiles[3] = G.tiles[1];
+        G.tiles[4] = G.tiles[0];
+        G.tiles[5] = (int)G.nchunks;
+        // bytes one tile of each pass moves (FP32 fields; FP64 doubles them): items of about
+        // 256 KB keep the per-item cost (ticket, barriers, release) small against the tile work
+        const double es = (double)sizeof(T) / 4.0;
+        const double tile_bytes[kPersistPasses] = {2.0 * P * pl->n3 * 52.0 * es, (double)L * pl->n2 * 16.0 * es,
+                                                   (double)L * pl->n1 * 16.0 * es, (double)L * pl->n2 * 16.0 * es,
+                                                   2.0 * P * pl->n3 * 8.0 * es, 1.0};
+        for (int q = 0; q < kPersistPasses; ++q)
+            G.tpi[q] = q == kPersistPasses - 1 ? 1 : std::max(1, (int)(256.0 * 1024.0 / tile_bytes[q]));
+        gstart[b] = first;   // solves are numbered group by group (the done counters' index j)
+        first += pl->batch;
+    }
+    const int per_sm = batch_persist_blocks_per_sm<T>(variant, smem);
+    if (per_sm < 1) return CCMF_ERR_UNSUPPORTED_SIZE;
+    const int grid = per_sm * bt->plans[0]->sms;
+    for (int q = 0; q < kPersistPasses; ++q) {
+        long long tiles = 0;
+        for (int b = 0; b < nb; ++b) tiles += (long long)groups[b].tiles[q] * bt->plans[b]->batch;
+        const int cap = (int)std::max<long long>(1, tiles / (4ll * grid));
+        for (int b = 0; b < nb; ++b) {
+            PersistGroup<T>& G = groups[b];
+            G.tpi[q] = std::min(G.tpi[q], cap);
+            G.ntiles[q] = (int)ceil_div(G.tiles[q], G.tpi[q]);
         }
     }
-    // first queue item of every (pass, solve), pass-major
-    std::vector<long long> base((size_t)kPersistPasses * ns + 1);
+    // first queue item of every (pass, group), pass-major; inside (pass, group) the group's
+    // solves follow one another with ntiles items each
+    std::vector<long long> pg_base((size_t)kPersistPasses * nb + 1);
     long long acc = 0;
     for (int pass = 0; pass < kPersistPasses; ++pass)
-        for (int j = 0; j < ns; ++j) {
-            base[(size_t)pass * ns + j] = acc;
-            acc += groups[sgroup[j]].ntiles[pass];
+        for (int b = 0; b < nb; ++b) {
+            pg_base[(size_t)pass * nb + b] = acc;
+            acc += (long long)groups[b].ntiles[pass] * bt->plans[b]->batch;
         }
-    base[(size_t)kPersistPasses * ns] = acc;
+    pg_base[(size_t)kPersistPasses * nb] = acc;
     if (acc >= (1ll << 32) - (1ll << 24)) return CCMF_ERR_UNSUPPORTED_SIZE;   // the 32-bit ticket
     if (cudaMemcpyAsync(ws + bt->pers_groups_off, groups.data(), sizeof(PersistGroup<T>) * nb, cudaMemcpyHostToDevice,
                         st) != cudaSuccess ||
-        cudaMemcpyAsync(ws + bt->pers_map_off, sgroup.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st) !=
+        cudaMemcpyAsync(ws + bt->pers_map_off, gstart.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st) !=
             cudaSuccess ||
-        cudaMemcpyAsync(ws + bt->pers_map_off + sizeof(int) * ns, slocal.data(), sizeof(int) * ns,
-                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(ws + bt->pers_base_off, base.data(), sizeof(long long) * base.size(), cudaMemcpyHostToDevice,
-                        st) != cudaSuccess)
+        cudaMemcpyAsync(ws + bt->pers_base_off, pg_base.data(), sizeof(long long) * pg_base.size(),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess)
         return CCMF_ERR_CUDA;
     if (bt->have_graph && memcmp(&bt->gkey, &key, sizeof(key)) == 0) return CCMF_OK;
     if (bt->have_graph) cudaGraphExecDestroy(bt->gexec);
     bt->have_graph = false;
-    const int per_sm = batch_persist_blocks_per_sm<T>(variant, smem);
-    if (per_sm < 1) return CCMF_ERR_UNSUPPORTED_SIZE;
     PersistArgs<T> a;
     memset(&a, 0, sizeof(a));
     a.groups = reinterpret_cast<const PersistGroup<T>*>(ws + bt->pers_groups_off);
-    a.sgroup = reinterpret_cast<const int*>(ws + bt->pers_map_off);
-    a.slocal = a.sgroup + ns;
-    a.base = reinterpret_cast<const long long*>(ws + bt->pers_base_off);
+    a.pg_base = reinterpret_cast<const long long*>(ws + bt->pers_base_off);
+    a.gstart = reinterpret_cast<const int*>(ws + bt->pers_map_off);
     a.done = reinterpret_cast<unsigned*>(ws + bt->pers_done_off);
     a.head = a.done + (size_t)ns * kPersistPasses;
+    a.ngroups = nb;
     a.nsolve = ns;
+    a.tw_off = (int)tw_off;
+    a.work_off = (int)work_off;
     a.cfg = cfg;
     const size_t counters = sizeof(unsigned) * ((size_t)ns * kPersistPasses + 1);
-    const int grid = per_sm * bt->plans[0]->sms;
     cudaGraph_t graph;
     if (cudaStreamBeginCapture(bt->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CCMF_ERR_CUDA;
     for (int it = 0; it < key.chunk; ++it) {

@@ -34,6 +34,13 @@
 namespace ccmf {
 
 constexpr int kPersistPasses = 6;
+// Blocks per SM the persistent kernel's register budget is sized for (a build-time knob): three
+// blocks (80 registers, a few spilled bytes in the update body) ran the 192-solve batch in
+// 14.5 ms per iteration on GB300 against 16.6 ms with two (128 registers, no spills).
+#ifndef CCMF_PERSIST_MIN_BLOCKS
+#define CCMF_PERSIST_MIN_BLOCKS 3
+#endif
+constexpr int kPersistMinBlocks = CCMF_PERSIST_MIN_BLOCKS;
 
 // One shape group of the batch (a sub-plan's grid, workspace slice and tables).
 template <typename T>
@@ -50,18 +57,21 @@ struct PersistGroup {
     int vec_div;                // pass 0 reads 16-byte vectors (n3 % (16 / sizeof(T)) == 0)
     int upd_w;                  // voxels per thread group of pass 5 (vector width)
     long long nchunks;          // pass-5 chunks per solve
-    int ntiles[kPersistPasses]; // items per solve of each pass
+    int tiles[kPersistPasses];  // tiles per solve of each pass (pass 5: chunks)
+    int tpi[kPersistPasses];    // consecutive tiles per work item (1 for pass 5: one partial slot per chunk)
+    int ntiles[kPersistPasses]; // items per solve of each pass: ceil(tiles / tpi)
 };
 
 template <typename T>
 struct PersistArgs {
     const PersistGroup<T>* groups;
-    const int* sgroup;          // [nsolve] group of solve j
-    const int* slocal;          // [nsolve] index of solve j inside its group
-    const long long* base;      // [kPersistPasses * nsolve + 1] first item of (pass, solve j), pass-major
+    const long long* pg_base;   // [kPersistPasses * ngroups + 1] first item of (pass, group), pass-major;
+                                // inside (pass, group) the group's solves follow one another, ntiles each
+    const int* gstart;          // [ngroups] index j of each group's first solve (solves numbered group by group)
     unsigned* done;             // [nsolve][kPersistPasses] completed items (zeroed before each launch)
     unsigned* head;             // next item of the queue (zeroed before each launch)
-    int nsolve;
+    int ngroups, nsolve;
+    int tw_off, work_off;       // byte offsets of the twiddle table and the tile buffers in dynamic shared memory
     LoopConfig cfg;
 };
 
@@ -89,12 +99,23 @@ template <> struct VecCg<double, 1> {
     __device__ __forceinline__ static void ld(const double* p, double (&o)[1]) { o[0] = __ldcg(p); }
 };
 
-// Shared memory (bytes) of one block of k_batch_persist for a group of this shape.
+// Dynamic shared memory of k_batch_persist, in three parts: the queue tables (first item of
+// every (pass, group), each group's scalar slots, first solve and tiles per pass), the
+// twiddle table of the current axis (kept while consecutive items use the same one) and
+// the tile buffers.
+__host__ __device__ inline size_t persist_off_sc(int ng) {
+    return ((size_t)(kPersistPasses * ng + 1) * 8 + 15) / 16 * 16;
+}
+__host__ __device__ inline size_t persist_off_start(int ng) { return persist_off_sc(ng) + (size_t)ng * 8; }
+__host__ __device__ inline size_t persist_table_bytes(int ng) {
+    return (persist_off_start(ng) + (size_t)ng * 4 * (1 + kPersistPasses) + 15) / 16 * 16;
+}
+// Tile buffers (bytes) of a group of this shape.
 template <typename T>
-__host__ __device__ inline size_t persist_smem_bytes(int n1, int n2, int n3, int P, int L) {
-    const size_t z = (size_t)n3 + 2 * (size_t)n3 * (P + 1);
-    const size_t y = (size_t)n2 + (size_t)n2 * (L + 1);
-    const size_t x = (size_t)n1 + (size_t)n1 * (L + 1);
+__host__ __device__ inline size_t persist_work_bytes(int n1, int n2, int n3, int P, int L) {
+    const size_t z = 2 * (size_t)n3 * (P + 1);
+    const size_t y = (size_t)n2 * (L + 1);
+    const size_t x = (size_t)n1 * (L + 1);
     size_t m = z > y ? z : y;
     m = m > x ? m : x;
     return m * sizeof(cx<T>);
@@ -103,16 +124,15 @@ __host__ __device__ inline size_t persist_smem_bytes(int n1, int n2, int n3, int
 // Pass 0 on tile t: line pairs (2q, 2q + 1), q in [t P, t P + P), packed as the real and
 // imaginary parts of one complex line (as k_div_rfft_z).
 template <typename T, int P, bool VEC>
-__device__ void persist_div_rfft_z(const PersistGroup<T>& G, int s, long long t, unsigned char* smem) {
+__device__ void persist_div_rfft_z(const PersistGroup<T>& G, int s, long long t, const cx<T>* twl,
+                                   unsigned char* work) {
     using C = cx<T>;
     constexpr int stride = P + 1;
     constexpr int W = VEC ? Vec16<T>::W : 1;
     const Geom& g = G.g;
     const Ptrs<T>& p = G.p;
-    C* twl = reinterpret_cast<C*>(smem);
-    C* A = twl + g.n3;
+    C* A = reinterpret_cast<C*>(work);
     C* B = A + (size_t)g.n3 * stride;
-    for (int i = threadIdx.x; i < g.n3; i += kThreads) twl[i] = G.tw[2][i];
     const T irho = T(1) / (T)p.sc[s].rho;
     const T h = T(0.70710678118654752440084436210485);
     const long long N = g.N;
@@ -206,14 +226,12 @@ __device__ void persist_div_rfft_z(const PersistGroup<T>& G, int s, long long t,
 // MODE 0: forward (DIF, leaves digit-reversed y order). MODE 2: inverse of the
 // conjugated data that pass 2 stores (DIT, natural order), conjugated on store.
 template <typename T, int MODE, int L>
-__device__ void persist_y_lines(const PersistGroup<T>& G, int s, long long t, unsigned char* smem) {
+__device__ void persist_y_lines(const PersistGroup<T>& G, int s, long long t, const cx<T>* twl, unsigned char* work) {
     using C = cx<T>;
     constexpr int stride = L + 1;
     const Geom& g = G.g;
     const int n = g.n2;
-    C* twl = reinterpret_cast<C*>(smem);
-    C* b = twl + n;
-    for (int i = threadIdx.x; i < n; i += kThreads) twl[i] = G.tw[1][i];
+    C* b = reinterpret_cast<C*>(work);
     const long long nlines = (long long)g.n3h * g.n1;
     C* spec = G.p.spec + (size_t)s * g.Nh;
     const long long l0 = t * L;
@@ -241,7 +259,7 @@ __device__ void persist_y_lines(const PersistGroup<T>& G, int s, long long t, un
 // Poisson gain from the digit-reversed x and y symbols, inverse as conj(DIT(conj(.)));
 // the result is stored conjugated (pass 3 undoes it).
 template <typename T, int L>
-__device__ void persist_x_lines(const PersistGroup<T>& G, int s, long long t, unsigned char* smem) {
+__device__ void persist_x_lines(const PersistGroup<T>& G, int s, long long t, const cx<T>* twl, unsigned char* work) {
     using C = cx<T>;
     constexpr int stride = L + 1;
     constexpr int lsh = (L >= 16) ? 4 : (L >= 8) ? 3 : (L >= 4) ? 2 : (L >= 2) ? 1 : 0;
@@ -249,9 +267,7 @@ __device__ void persist_x_lines(const PersistGroup<T>& G, int s, long long t, un
     constexpr int mstep = kThreads / L;
     const Geom& g = G.g;
     const int n = g.n1;
-    C* twl = reinterpret_cast<C*>(smem);
-    C* b = twl + n;
-    for (int i = threadIdx.x; i < n; i += kThreads) twl[i] = G.tw[0][i];
+    C* b = reinterpret_cast<C*>(work);
     const long long plane = (long long)g.n1 * g.n2;
     const long long nlines = (long long)g.n3h * g.n2;
     C* spec = G.p.spec + (size_t)s * g.Nh;
@@ -285,14 +301,12 @@ __device__ void persist_x_lines(const PersistGroup<T>& G, int s, long long t, un
 // Pass 4 on tile t: the packed C2R along z of line pairs (2q, 2q + 1), q in [t P, t P + P)
 // (as k_irfft_z), writing phi.
 template <typename T, int P>
-__device__ void persist_irfft_z(const PersistGroup<T>& G, int s, long long t, unsigned char* smem) {
+__device__ void persist_irfft_z(const PersistGroup<T>& G, int s, long long t, const cx<T>* twl, unsigned char* work) {
     using C = cx<T>;
     constexpr int stride = P + 1;
     const Geom& g = G.g;
-    C* twl = reinterpret_cast<C*>(smem);
-    C* A = twl + g.n3;
+    C* A = reinterpret_cast<C*>(work);
     C* B = A + (size_t)g.n3 * stride;
-    for (int i = threadIdx.x; i < g.n3; i += kThreads) twl[i] = G.tw[2][i];
     const long long Lp = (long long)g.n1 * g.n2;
     const long long l0 = t * 2 * P;
     const C* spec = G.p.spec + (size_t)s * g.Nh;
@@ -444,48 +458,75 @@ __device__ __forceinline__ bool persist_wait(const unsigned* ctr, unsigned need,
 }
 
 // The persistent kernel: P line pairs per z tile, L lines per y / x tile.
+// Thread 0 of a block takes the tickets: it fetches the next one while the current item
+// runs (a block holds at most one item that has not started, so the earliest unfinished
+// item is always running or about to start), decodes an item from the (pass, group) table
+// in shared memory, and remembers which (solve, pass) dependency it has already seen
+// complete and the active flag of the last solve it decoded.
 template <typename T, int P, int L>
-__global__ void __launch_bounds__(kThreads, 2) k_batch_persist(PersistArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, kPersistMinBlocks) k_batch_persist(PersistArgs<T> a) {
+    using C = cx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(16) PersistGroup<T> sg;   // the current item's group, copied from global memory
     __shared__ long long s_tile;
-    __shared__ int s_pass, s_j, s_group, s_local, s_run, s_last, s_loaded;
+    __shared__ int s_pass, s_j, s_group, s_local, s_run, s_last, s_loaded, s_twkey;
     static_assert(sizeof(PersistGroup<T>) % 4 == 0, "group copy by words");
-    if (threadIdx.x == 0) s_loaded = -1;
-    const int nq = kPersistPasses * a.nsolve;
-    const long long total = a.base[nq];
+    const int ng = a.ngroups;
+    long long* t_base = reinterpret_cast<long long*>(smem_raw);
+    SolveScalars** t_sc = reinterpret_cast<SolveScalars**>(smem_raw + persist_off_sc(ng));
+    int* t_start = reinterpret_cast<int*>(smem_raw + persist_off_start(ng));
+    int* t_tiles = t_start + ng;
+    C* twl = reinterpret_cast<C*>(smem_raw + a.tw_off);
+    unsigned char* work = smem_raw + a.work_off;
+    for (int i = threadIdx.x; i <= kPersistPasses * ng; i += kThreads) t_base[i] = a.pg_base[i];
+    for (int b = threadIdx.x; b < ng; b += kThreads) {
+        t_sc[b] = a.groups[b].p.sc;
+        t_start[b] = a.gstart[b];
+    }
+    for (int i = threadIdx.x; i < ng * kPersistPasses; i += kThreads)
+        t_tiles[i] = a.groups[i / kPersistPasses].ntiles[i % kPersistPasses];
     const unsigned budget = a.cfg.spin_limit ? a.cfg.spin_limit - 1 : kSpinLimit;
+    long long next = 0;
+    int ok_j = -1, ok_p = -1, act_j = -1, act_v = 0;   // thread 0's caches
+    if (threadIdx.x == 0) {
+        s_loaded = -1;
+        s_twkey = -1;
+        next = (long long)atomicAdd(a.head, 1u);
+    }
     for (;;) {
-        __syncthreads();   // every thread is done with the previous item's shared values
+        __syncthreads();   // tables ready; every thread is done with the previous item's shared values
         if (threadIdx.x == 0) {
-            const long long item = (long long)atomicAdd(a.head, 1u);
+            const long long item = next;
+            const long long total = t_base[kPersistPasses * ng];
             int pass = -1, j = 0, grp = 0, loc = 0, run = 0;
             long long tile = 0;
             if (item < total) {
-                int lo = 0, hi = nq;   // base[lo] <= item < base[hi]
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (a.base[mid] <= item)
-                        lo = mid;
-                    else
-                        hi = mid;
-                }
-                pass = lo / a.nsolve;
-                j = lo - pass * a.nsolve;
-                tile = item - a.base[lo];
-                grp = a.sgroup[j];
-                loc = a.slocal[j];
-                const PersistGroup<T>& G = a.groups[grp];
+                next = (long long)atomicAdd(a.head, 1u);   // the following ticket, while this item runs
+                pass = 0;
+                while (pass + 1 < kPersistPasses && item >= t_base[(pass + 1) * ng]) ++pass;
+                while (grp + 1 < ng && item >= t_base[pass * ng + grp + 1]) ++grp;
+                const long long off = item - t_base[pass * ng + grp];
+                const long long nt = t_tiles[grp * kPersistPasses + pass];
+                const long long q = off / nt;
+                tile = off - q * nt;
+                loc = (int)q;
+                j = t_start[grp] + loc;
                 // a solve's active flag changes only when its last pass-5 item completes, after
                 // every other item of the solve in this launch
-                run = G.p.sc[loc].active ? 1 : 0;
-                if (run && pass > 0) {
+                if (j != act_j) {
+                    act_j = j;
+                    act_v = t_sc[grp][loc].active;
+                }
+                run = act_v ? 1 : 0;
+                if (run && pass > 0 && !(j == ok_j && pass == ok_p)) {
                     const unsigned* ctr = a.done + (size_t)j * kPersistPasses + (pass - 1);
-                    if (!persist_wait(ctr, (unsigned)G.ntiles[pass - 1], budget)) {
-                        atomicCAS(&G.p.sc[loc].status, 0, 6);   // CCMF_ERR_TIMEOUT; the solve retires
-                        run = 2;                                // at its pass-5 completion
+                    if (persist_wait(ctr, (unsigned)t_tiles[grp * kPersistPasses + pass - 1], budget)) {
+                        ok_j = j;
+                        ok_p = pass;
+                    } else {
+                        atomicCAS(&t_sc[grp][loc].status, 0, 6);   // CCMF_ERR_TIMEOUT; the solve retires
+                        run = 2;                                    // at its pass-5 completion
                     }
-                    __threadfence();
                 }
             }
             s_pass = pass;
@@ -502,25 +543,47 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_persist(PersistArgs<T> a)
         if (run == 0) continue;   // a retired solve: its items are skipped
         const int j = s_j, grp = s_group, s = s_local;
         const long long tile = s_tile;
-        if (grp != s_loaded) {    // the same decision in every thread (s_loaded is written below only)
+        const int axis = (pass == 2) ? 0 : (pass == 1 || pass == 3) ? 1 : 2;
+        const int twkey = grp * 3 + axis;
+        // both decisions are taken before thread 0 updates s_loaded / s_twkey below
+        const bool new_group = grp != s_loaded;
+        const bool new_tw = run == 1 && pass < kPersistPasses - 1 && twkey != s_twkey;
+        if (new_group) {
             const int* src = reinterpret_cast<const int*>(a.groups + grp);
             int* dst = reinterpret_cast<int*>(&sg);
             for (int w = threadIdx.x; w < (int)(sizeof(PersistGroup<T>) / 4); w += kThreads) dst[w] = src[w];
-            __syncthreads();
-            if (threadIdx.x == 0) s_loaded = grp;
         }
-        if (run == 1) {
+        if (new_group || new_tw) __syncthreads();
+        if (new_tw) {
+            const int n = axis == 0 ? sg.g.n1 : axis == 1 ? sg.g.n2 : sg.g.n3;
+            for (int i = threadIdx.x; i < n; i += kThreads) twl[i] = sg.tw[axis][i];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            s_loaded = grp;
+            if (new_tw) s_twkey = twkey;
+        }
+        if (run == 1 && pass < kPersistPasses - 1) {
+            // an item covers tpi consecutive tiles of its pass
+            const long long t0 = tile * sg.tpi[pass];
+            const long long t1 = min(t0 + sg.tpi[pass], (long long)sg.tiles[pass]);
+            for (long long t = t0; t < t1; ++t) {
+                if (t > t0) __syncthreads();   // the previous tile's buffers have been stored
+                switch (pass) {
+                    case 0:
+                        if (sg.vec_div)
+                            persist_div_rfft_z<T, P, true>(sg, s, t, twl, work);
+                        else
+                            persist_div_rfft_z<T, P, false>(sg, s, t, twl, work);
+                        break;
+                    case 1: persist_y_lines<T, 0, L>(sg, s, t, twl, work); break;
+                    case 2: persist_x_lines<T, L>(sg, s, t, twl, work); break;
+                    case 3: persist_y_lines<T, 2, L>(sg, s, t, twl, work); break;
+                    default: persist_irfft_z<T, P>(sg, s, t, twl, work); break;
+                }
+            }
+        } else if (run == 1) {
             switch (pass) {
-                case 0:
-                    if (sg.vec_div)
-                        persist_div_rfft_z<T, P, true>(sg, s, tile, smem_raw);
-                    else
-                        persist_div_rfft_z<T, P, false>(sg, s, tile, smem_raw);
-                    break;
-                case 1: persist_y_lines<T, 0, L>(sg, s, tile, smem_raw); break;
-                case 2: persist_x_lines<T, L>(sg, s, tile, smem_raw); break;
-                case 3: persist_y_lines<T, 2, L>(sg, s, tile, smem_raw); break;
-                case 4: persist_irfft_z<T, P>(sg, s, tile, smem_raw); break;
                 default:
                     if constexpr (sizeof(T) == 4) {
                         if (sg.upd_w == 2)
@@ -533,11 +596,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_persist(PersistArgs<T> a)
                     break;
             }
         }
-        __threadfence();   // this item's writes before its completion count
-        __syncthreads();
+        __syncthreads();   // every thread's writes of this item precede thread 0's release below
         if (threadIdx.x == 0) {
+            __threadfence();
             const unsigned old = atomicAdd(a.done + (size_t)j * kPersistPasses + pass, 1u);
-            s_last = (pass == kPersistPasses - 1) && (old + 1 == (unsigned)sg.ntiles[pass]);
+            s_last = (pass == kPersistPasses - 1) && (old + 1 == (unsigned)t_tiles[grp * kPersistPasses + pass]);
             if (s_last) __threadfence();
         }
         __syncthreads();

@@ -225,7 +225,10 @@ typedef struct {
                                1 as 0 but radix 4s in place of a radix 8 + 2 tail; 2 radix 4 at most */
     int zinv_pairs_per_block; /* inverse z pass: line pairs per block, power of two 1..16 */
     int line_engine;        /* strided y / x passes: 0 in-place radix stages per block (any length),
-                               1 one warp per line for power-of-two lengths 128..1024 */
+                               1 one warp per line for power-of-two lengths 128..1024, 2 as 1 with
+                               the x pass's tiles of 8 lines moved between the half spectrum and
+                               shared memory by TMA (cp.async.bulk.tensor loads and stores;
+                               FP32, N1 = 512, N2 a multiple of 8) */
     int z_engine;           /* z passes: 0 Stockham stages over tiles of line pairs (any N3);
                                one warp per line pair for power-of-two N3 128..1024 in the
                                inverse pass (1) or in both passes (2) */

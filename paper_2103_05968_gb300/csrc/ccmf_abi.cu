@@ -56,6 +56,8 @@ template <typename T>
 void launch_adj_step(const Ctx<T>&, const T*, T*, T*, T*, T*, T*, const T*, SolveScalars*, T*, const double*, int, int,
                      cudaStream_t, const unsigned*);
 // the persistent batch kernel is instantiated in ccmf_f32.cu / ccmf_f64.cu only
+template <typename T> int wx_tma_blocks_per_sm();
+extern template int wx_tma_blocks_per_sm<float>();
 extern template int batch_persist_blocks_per_sm<float>(int, size_t);
 extern template int batch_persist_blocks_per_sm<double>(int, size_t);
 extern template void launch_batch_persist<float>(const PersistArgs<float>&, int, int, size_t, cudaStream_t);
@@ -473,6 +475,7 @@ int shape_for(const ccmf_plan* pl, const ccmf_tuning& t, LaunchShape* out, ccmf_
     // strided line passes: one warp per line for power-of-two lengths 128 ... 1024
     // (line_engine 1), else in-place radix stages over tiles of lines
     int le = r.line_engine;
+    const bool le_auto = le < 0 && !getenv("CCMF_LINE_ENGINE");
     if (le < 0) {
         // warp per line by default (GB300, 512^2 planes: y passes 0.29 ms against 0.37 ms
         // for the block stages, x pass 0.62 against 0.64 ms); the autotuner tries both
@@ -480,11 +483,12 @@ int shape_for(const ccmf_plan* pl, const ccmf_tuning& t, LaunchShape* out, ccmf_
         le = env ? atoi(env) : 1;
         if (le < 0 || le > 1) le = 1;
     }
-    if (le > 1) return CCMF_ERR_UNSUPPORTED_SIZE;
+    if (le > 2) return CCMF_ERR_UNSUPPORTED_SIZE;
     r.line_engine = le;
     auto warp_len_ok = [](int n) { return n >= 128 && n <= 1024 && (n & (n - 1)) == 0; };
     sh.wl_y = sh.wl_x = 0;
-    if (!sh.plane_fused && le == 1) {
+    sh.x_tma = 0;
+    if (!sh.plane_fused && le >= 1) {
         // y: twiddles + one padded line per warp; x: twiddles + two tiles of 8 lines
         const size_t swy = ((size_t)n2 + 8 * (size_t)(n2 + n2 / 16)) * cs;
         const size_t swx = ((size_t)n1 + 2 * 8 * (size_t)(n1 + n1 / 16 + 2)) * cs;
@@ -496,6 +500,19 @@ int shape_for(const ccmf_plan* pl, const ccmf_tuning& t, LaunchShape* out, ccmf_
             sh.wl_x = n1;
             sh.smem_wx = swx;
         }
+        // line engine 2: the x pass with its tiles moved by TMA (FP32, n1 = 512, n2 % 8 == 0); the
+        // built-in choice where it applies (GB300, 512^3: 0.218 against 0.339 ms per x pass)
+        if (le_auto && le == 1 && !f64 && sh.wl_x == kTmaXN && x_tma_shape_ok(n1, n2, pl->n3h, batch)) {
+            le = 2;
+            r.line_engine = 2;
+        }
+        if (le == 2) {
+            if (f64 || sh.wl_x != kTmaXN || !x_tma_shape_ok(n1, n2, pl->n3h, batch))
+                return CCMF_ERR_UNSUPPORTED_SIZE;
+            sh.x_tma = 1;
+        }
+    } else if (le == 2) {
+        return CCMF_ERR_UNSUPPORTED_SIZE;
     }
     // z passes: one warp per line pair for power-of-two N3 128 ... 1024: z_engine 1 the
     // inverse pass only, 2 both passes (the divergence pass's stencil loads favour the
@@ -532,10 +549,11 @@ int shape_for(const ccmf_plan* pl, const ccmf_tuning& t, LaunchShape* out, ccmf_
                                       : wlines_blocks_per_sm<float>(0, n2, sh.smem_wy))
                                : (f64 ? lines_blocks_per_sm<double>(0, sh.lpb_y, sh.smem_y)
                                       : lines_blocks_per_sm<float>(0, sh.lpb_y, sh.smem_y));
-        const int bx = sh.wl_x ? (f64 ? wlines_blocks_per_sm<double>(1, n1, sh.smem_wx)
-                                      : wlines_blocks_per_sm<float>(1, n1, sh.smem_wx))
-                               : (f64 ? lines_blocks_per_sm<double>(1, sh.lpb_x, sh.smem_x)
-                                      : lines_blocks_per_sm<float>(1, sh.lpb_x, sh.smem_x));
+        const int bx = sh.x_tma  ? wx_tma_blocks_per_sm<float>()
+                       : sh.wl_x ? (f64 ? wlines_blocks_per_sm<double>(1, n1, sh.smem_wx)
+                                        : wlines_blocks_per_sm<float>(1, n1, sh.smem_wx))
+                                 : (f64 ? lines_blocks_per_sm<double>(1, sh.lpb_x, sh.smem_x)
+                                        : lines_blocks_per_sm<float>(1, sh.lpb_x, sh.smem_x));
         if (by < 1 || bx < 1) return CCMF_ERR_UNSUPPORTED_SIZE;
         sh.grid_y = (int)std::max(1LL, ((long long)by * sms + batch - 1) / batch);
         sh.grid_x = (int)std::max(1LL, ((long long)bx * sms + batch - 1) / batch);
@@ -926,7 +944,7 @@ int tune_descent(ccmf_plan* plan, const std::function<int(double*)>& measure, do
         {&ccmf_tuning::branches, brs},
         {&ccmf_tuning::radix_mode, {0, 1, 2}},
         {&ccmf_tuning::zinv_pairs_per_block, {1, 2, 4, 8, 16}},
-        {&ccmf_tuning::line_engine, {0, 1}},
+        {&ccmf_tuning::line_engine, {0, 1, 2}},
         {&ccmf_tuning::z_engine, {0, 1, 2}},
     };
     for (const Knob& k : knobs) {

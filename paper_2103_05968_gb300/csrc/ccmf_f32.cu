@@ -21,4 +21,5 @@ template void launch_adj_step<float>(const Ctx<float>&, const float*, float*, fl
                                    const double*, int, int, cudaStream_t, const unsigned*);
 template int batch_persist_blocks_per_sm<float>(int, size_t);
 template void launch_batch_persist<float>(const PersistArgs<float>&, int, int, size_t, cudaStream_t);
+template int wx_tma_blocks_per_sm<float>();
 }  // namespace ccmf

@@ -3,6 +3,7 @@
 
 #include "ccmf_kernels.cuh"
 #include "ccmf_persist.cuh"
+#include "ccmf_tma_x.cuh"
 
 namespace ccmf {
 
@@ -241,6 +242,24 @@ int wlines_blocks_per_sm(int mode, int n, size_t smem) {
     return nb;
 }
 
+// Blocks per SM of the TMA-staged x pass (FP32 only), 0 on error.
+template <typename T>
+int wx_tma_blocks_per_sm() {
+    if constexpr (sizeof(T) != 4) {
+        return 0;
+    } else {
+        int nb = 0;
+        cudaError_t err = raise_smem_limit((const void*)k_fft_wx_tma<kTmaXN>, kTmaXSmem);
+        if (err == cudaSuccess)
+            err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fft_wx_tma<kTmaXN>, kThreads, kTmaXSmem);
+        if (err != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return nb;
+    }
+}
+
 // Sets the launch attributes of the cluster plane pass and returns how many of its
 // clusters can be resident at once (0: this cluster size cannot be launched).
 template <typename T, int CL>
@@ -313,6 +332,9 @@ cudaError_t configure_kernels(const LaunchShape& sh) {
         });
     }
     if (sh.wl_x) { CCMF_DISPATCH_N(sh.wl_x, { set((const void*)k_fft_wlines<T, 1, NN>, sh.smem_wx); }); }
+    if constexpr (sizeof(T) == 4) {
+        if (sh.x_tma) set((const void*)k_fft_wx_tma<kTmaXN>, kTmaXSmem);
+    }
     if (sh.plane_fused && sh.plane_cluster <= 1) set((const void*)k_fft_plane<T>, sh.smem_plane);
     if (sh.plane_fused && sh.plane_cluster > 1 && err == cudaSuccess &&
         plane_cluster_capacity<T>(sh.plane_cluster, sh.smem_plane) < 1)
@@ -443,7 +465,22 @@ void launch_passes(const Ctx<T>& c, const Ptrs<T>& p, cudaStream_t st, F&& betwe
             });
         }
         between(kKFftYFwd);
-        if (sh.wl_x) {
+        bool x_done = false;
+        if constexpr (sizeof(T) == 4) {
+            if (sh.x_tma) {
+                // the tensor map covers the planes of the solves this launch touches; the plan's
+                // launch rules checked the shape, so a failed encoding leaves no valid launch
+                alignas(64) CUtensorMap xmap;
+                if (encode_x_tensor_map(&xmap, p.spec, g.n1, g.n2, (long long)g.n3h * (p.s0 + g.batch)))
+                    k_fft_wx_tma<kTmaXN><<<gwx, kThreads, kTmaXSmem, st>>>(xmap, g, p, c.tw[0], c.sym[0], ysym,
+                                                                          c.sym[2], inv_n, c.cfg.spin_limit);
+                else
+                    k_launch_failed<0><<<1, 32, 0, st>>>(p.sc, p.s0, g.batch);
+                x_done = true;
+            }
+        }
+        if (x_done) {
+        } else if (sh.wl_x) {
             CCMF_DISPATCH_N(sh.wl_x, {
                 k_fft_wlines<T, 1, NN><<<gwx, kThreads, sh.smem_wx, st>>>(g, p, c.tw[0], c.sym[0], ysym, c.sym[2],
                                                                           inv_n);

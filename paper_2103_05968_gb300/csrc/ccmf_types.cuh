@@ -125,6 +125,7 @@ struct LaunchShape {
     int plane_cluster;        // blocks sharing one plane: 1 = k_fft_plane, 2..16 = k_fft_plane_cluster
     int grid_y, grid_x;       // persistent blocks per solve of the y / x line passes (0: one tile per block)
     int wl_y, wl_x;           // > 0: the y / x line passes run one warp per line (k_fft_wlines); the line length
+    int x_tma;                // 1: the x pass is k_fft_wx_tma (tiles moved by TMA; FP32, n1 = 512)
     size_t smem_wy, smem_wx;  // their dynamic shared memory
     int wz, wzd;              // > 0: the inverse / divergence z pass runs one warp per line pair; N3
     size_t smem_wzd, smem_wzi;

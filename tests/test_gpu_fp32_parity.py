@@ -105,6 +105,78 @@ def test_fp32_x_lines_512_three_normals():
     print("512x24x16 FP32 one-step relative max errors (e, v):", worst)
 
 
+def test_fp32_x_lines_512_tma_tiles():
+    """The x pass with its 8-line tiles moved by TMA (line engine 2: cp.async.bulk.tensor into a
+    64-byte swizzled buffer and back) does the same arithmetic as the warp engine's copy loop
+    (line engine 1): states bit-identical after 20 iterations on the 512 x 24 x 16 cell with
+    three normals in three graph branches, and one step against the oracle."""
+    gamma = M.random_two_phase((512, 24, 16), 0.3, 0.25, 1.0, 29)
+    normals = [[1, 0, 0], [0.36, 0.48, 0.8], [0, 0, 1]]
+    g = torch.from_numpy(gamma.astype(np.float32)).to(DEV)
+    states = []
+    for le in (1, 2):
+        plan = ccmf.Plan(gamma.shape, batch=3, precision=ccmf.CCMF_FP32_MIXED, device=DEV)
+        plan.set_tuning(plane_blocks=0, line_engine=le, branches=3)
+        assert plan.tuning()["line_engine"] == le
+        res, _, _ = plan.solve(g, normals, ccmf.Params(fixed_iters=20))
+        e, v, rho, _ = plan.state()
+        states.append((e.cpu().numpy(), v.cpu().numpy(), list(rho), [r["gamma_eff"] for r in res]))
+        plan.close()
+    (e1, v1, r1, g1), (e2, v2, r2, g2) = states
+    assert np.array_equal(e1, e2) and np.array_equal(v1, v2) and r1 == r2 and g1 == g2
+    plan = ccmf.Plan(gamma.shape, batch=3, precision=ccmf.CCMF_FP32_MIXED, device=DEV)
+    plan.set_tuning(plane_blocks=0, line_engine=2)
+    worst = one_step_against_oracle(gamma, normals, plan, 20, (0, 1, 2))
+    plan.close()
+    print("512x24x16 FP32 TMA x tiles, one-step relative max errors (e, v):", worst)
+
+
+def test_fp32_fibre_block_tma_x_tiles_equal_warp_engine():
+    """512 x 512 x 64 corner block of the 512^3 fibre field in the 512^3 launch shape: the TMA
+    x pass leaves the state bit-identical to the warp engine's after 6 iterations."""
+    full, _ = M.config_short_fibres_512(dtype=np.float32)
+    gamma = np.ascontiguousarray(full[:, :, :64])
+    del full
+    g = torch.from_numpy(gamma).to(DEV)
+    out = []
+    for le in (1, 2):
+        plan = ccmf.Plan(gamma.shape, batch=1, precision=ccmf.CCMF_FP32_MIXED, device=DEV)
+        plan.set_tuning(update_variant=11, plane_blocks=0, line_engine=le, z_engine=1)
+        res, _, _ = plan.solve(g, [[0, 0, 1]], ccmf.Params(fixed_iters=6))
+        e, v, rho, _ = plan.state()
+        out.append((e.cpu().numpy(), v.cpu().numpy(), rho[0], res[0]["gamma_eff"]))
+        plan.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2] and out[0][3] == out[1][3]
+
+
+def test_tma_x_tiles_wait_timeout_reported(monkeypatch):
+    """The TMA x pass's bounded mbarrier wait: with the zero-poll debug budget it gives up,
+    drains its loads in flight, and the solve reports CCMF_ERR_TIMEOUT; the next call is healthy."""
+    gamma = M.random_two_phase((512, 16, 8), 0.3, 0.25, 1.0, 31)
+    g = torch.from_numpy(gamma.astype(np.float32)).to(DEV)
+    plan = ccmf.Plan(gamma.shape, batch=1, precision=ccmf.CCMF_FP32_MIXED, device=DEV)
+    plan.set_tuning(plane_blocks=0, line_engine=2, update_variant=0)
+    monkeypatch.setenv("CCMF_DEBUG_SPIN_LIMIT", "0")
+    res, _, _ = plan.solve(g, [[0, 0, 1]], ccmf.Params(fixed_iters=3))
+    assert res[0]["status"] == ccmf.CCMF_ERR_TIMEOUT
+    monkeypatch.delenv("CCMF_DEBUG_SPIN_LIMIT")
+    res, _, _ = plan.solve(g, [[0, 0, 1]], ccmf.Params(fixed_iters=3))
+    assert res[0]["status"] == 0 and res[0]["iters"] == 3 and np.isfinite(res[0]["gamma_eff"])
+    plan.close()
+
+
+def test_tma_x_tiles_rejected_where_not_applicable():
+    """Line engine 2 needs FP32, N1 = 512 and N2 a multiple of 8."""
+    for shape, prec in (((512, 12, 8), ccmf.CCMF_FP32_MIXED), ((256, 16, 8), ccmf.CCMF_FP32_MIXED),
+                        ((512, 16, 8), ccmf.CCMF_FP64)):
+        plan = ccmf.Plan(shape, batch=1, precision=prec, device=DEV)
+        with pytest.raises(ccmf.CCMFError) as ei:
+            plan.set_tuning(plane_blocks=0, line_engine=2)
+        assert ei.value.code == ccmf.CCMF_ERR_UNSUPPORTED_SIZE
+        plan.close()
+
+
 def _one_weakest_layer():
     layers = np.array([1.0, 0.9, 1.2, 0.6, 1.1, 0.7, 1.4, 0.8] * 8)
     layers[37] = 0.4

@@ -369,8 +369,8 @@ int ccmf_batch_autotune(ccmf_batch* batch, const void* const* gammas, const doub
  *            pass of its solve has completed. A wait that runs out sets that solve's
  *            status to CCMF_ERR_TIMEOUT and retires it. The FFT stages are the in-place /
  *            Stockham block stages for every axis length, so results differ from the
- *            graph mode by rounding only. Axes longer than 512 (FP32) / 256 (FP64) use
- *            narrower tiles; a batch whose tiles do not fit shared memory returns
+ *            graph mode by rounding only. Axes longer than about 400 (FP32) / 200 (FP64)
+ *            use narrower tiles; a batch whose tiles do not fit shared memory returns
  *            CCMF_ERR_UNSUPPORTED_SIZE from ccmf_batch_solve.
  * The next ccmf_batch_solve captures its graph again. Returns CCMF_ERR_INVALID_ARG for
  * a NULL batch or enable not in {0, 1}.

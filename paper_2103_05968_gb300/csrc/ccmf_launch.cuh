@@ -652,20 +652,28 @@ void launch_adj_step(const Ctx<T>& c, const T* zk, T* ebar, T* vbar, T* zbar, T*
     k_adj_post<T><<<grid, kThreads, 0, st>>>(c.g, zbar, my, sched, sched_len, k, b, ebar, vbar);
 }
 
-// Tile shapes of the batched persistent kernel: {z line pairs, y / x lines} per item.
-// Variant 0 for short axes, variant 1 where variant 0's tiles do not fit shared memory.
-constexpr int kPersistTiles[2][2] = {{8, 16}, {2, 4}};
+// Tile shapes of the batched persistent kernel: {z line pairs, y / x lines} per tile.
+// Variant 0 unless its tiles do not fit 110 KB of shared memory (axes beyond about 400 in FP32,
+// 200 in FP64), variant 1 then. On the 192-solve workload 16 line pairs per z tile ran 13.57 ms
+// per iteration against 14.57 ms with 8 (a build-time knob).
+#ifndef CCMF_PERSIST_ZPAIRS
+#define CCMF_PERSIST_ZPAIRS 16
+#endif
+constexpr int kPersistZPairs = CCMF_PERSIST_ZPAIRS;
+constexpr int kPersistTiles[2][2] = {{kPersistZPairs, 16}, {4, 8}};
 
 // Resident blocks per SM of k_batch_persist variant `variant` with `smem` bytes of dynamic
 // shared memory (raises the kernel's limit first), 0 on error.
 template <typename T>
 int batch_persist_blocks_per_sm(int variant, size_t smem) {
     int nb = 0;
-    const void* f = variant == 0 ? (const void*)k_batch_persist<T, 8, 16> : (const void*)k_batch_persist<T, 2, 4>;
+    const void* f = variant == 0 ? (const void*)k_batch_persist<T, kPersistZPairs, 16>
+                                 : (const void*)k_batch_persist<T, 4, 8>;
     cudaError_t err = raise_smem_limit(f, smem);
     if (err == cudaSuccess)
-        err = variant == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_persist<T, 8, 16>, kThreads, smem)
-                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_persist<T, 2, 4>, kThreads, smem);
+        err = variant == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_persist<T, kPersistZPairs, 16>,
+                                                                           kThreads, smem)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_persist<T, 4, 8>, kThreads, smem);
     if (err != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -677,9 +685,9 @@ int batch_persist_blocks_per_sm(int variant, size_t smem) {
 template <typename T>
 void launch_batch_persist(const PersistArgs<T>& a, int variant, int grid, size_t smem, cudaStream_t st) {
     if (variant == 0)
-        k_batch_persist<T, 8, 16><<<grid, kThreads, smem, st>>>(a);
+        k_batch_persist<T, kPersistZPairs, 16><<<grid, kThreads, smem, st>>>(a);
     else
-        k_batch_persist<T, 2, 4><<<grid, kThreads, smem, st>>>(a);
+        k_batch_persist<T, 4, 8><<<grid, kThreads, smem, st>>>(a);
 }
 
 }  // namespace ccmf

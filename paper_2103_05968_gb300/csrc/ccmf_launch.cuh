@@ -655,23 +655,29 @@ void launch_adj_step(const Ctx<T>& c, const T* zk, T* ebar, T* vbar, T* zbar, T*
 // Tile shapes of the batched persistent kernel: {z line pairs, y / x lines} per tile.
 // Variant 0 unless its tiles do not fit 110 KB of shared memory (axes beyond about 400 in FP32,
 // 200 in FP64), variant 1 then. On the 192-solve workload 16 line pairs per z tile ran 13.57 ms
-// per iteration against 14.57 ms with 8 (a build-time knob).
+// per iteration against 14.57 ms with 8, and 32 lines per y / x tile 13.13 ms against 13.57 ms
+// with 16: the line passes are bound by their stage barriers, and wider tiles give each barrier
+// more butterflies (build-time knobs).
 #ifndef CCMF_PERSIST_ZPAIRS
 #define CCMF_PERSIST_ZPAIRS 16
 #endif
+#ifndef CCMF_PERSIST_LINES
+#define CCMF_PERSIST_LINES 32
+#endif
 constexpr int kPersistZPairs = CCMF_PERSIST_ZPAIRS;
-constexpr int kPersistTiles[2][2] = {{kPersistZPairs, 16}, {4, 8}};
+constexpr int kPersistLines = CCMF_PERSIST_LINES;
+constexpr int kPersistTiles[2][2] = {{kPersistZPairs, kPersistLines}, {4, 8}};
 
 // Resident blocks per SM of k_batch_persist variant `variant` with `smem` bytes of dynamic
 // shared memory (raises the kernel's limit first), 0 on error.
 template <typename T>
 int batch_persist_blocks_per_sm(int variant, size_t smem) {
     int nb = 0;
-    const void* f = variant == 0 ? (const void*)k_batch_persist<T, kPersistZPairs, 16>
+    const void* f = variant == 0 ? (const void*)k_batch_persist<T, kPersistZPairs, kPersistLines>
                                  : (const void*)k_batch_persist<T, 4, 8>;
     cudaError_t err = raise_smem_limit(f, smem);
     if (err == cudaSuccess)
-        err = variant == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_persist<T, kPersistZPairs, 16>,
+        err = variant == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_persist<T, kPersistZPairs, kPersistLines>,
                                                                            kThreads, smem)
                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_persist<T, 4, 8>, kThreads, smem);
     if (err != cudaSuccess) {
@@ -685,7 +691,7 @@ int batch_persist_blocks_per_sm(int variant, size_t smem) {
 template <typename T>
 void launch_batch_persist(const PersistArgs<T>& a, int variant, int grid, size_t smem, cudaStream_t st) {
     if (variant == 0)
-        k_batch_persist<T, kPersistZPairs, 16><<<grid, kThreads, smem, st>>>(a);
+        k_batch_persist<T, kPersistZPairs, kPersistLines><<<grid, kThreads, smem, st>>>(a);
     else
         k_batch_persist<T, 4, 8><<<grid, kThreads, smem, st>>>(a);
 }

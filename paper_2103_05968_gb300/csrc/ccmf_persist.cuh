@@ -262,8 +262,8 @@ template <typename T, int L>
 __device__ void persist_x_lines(const PersistGroup<T>& G, int s, long long t, const cx<T>* twl, unsigned char* work) {
     using C = cx<T>;
     constexpr int stride = L + 1;
-    constexpr int lsh = (L >= 16) ? 4 : (L >= 8) ? 3 : (L >= 4) ? 2 : (L >= 2) ? 1 : 0;
-    static_assert((1 << lsh) == L, "L must be a power of two <= 16");
+    constexpr int lsh = (L >= 32) ? 5 : (L >= 16) ? 4 : (L >= 8) ? 3 : (L >= 4) ? 2 : (L >= 2) ? 1 : 0;
+    static_assert((1 << lsh) == L, "L must be a power of two <= 32");
     constexpr int mstep = kThreads / L;
     const Geom& g = G.g;
     const int n = g.n1;

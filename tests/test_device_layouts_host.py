@@ -82,7 +82,7 @@ def test_tile_coordinates_follow_the_tma_rules(n2, n3, batch):
 # Work queue of the batched persistent launch
 # ---------------------------------------------------------------------------
 PASSES = 6
-P, L = 16, 16                # line pairs per z tile, lines per y / x tile (variant 0)
+P, L = 16, 32                # line pairs per z tile, lines per y / x tile (variant 0)
 CHUNK = 256 * 16             # thread groups per update chunk
 
 

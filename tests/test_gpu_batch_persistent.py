@@ -140,3 +140,36 @@ def test_persistent_device_wait_timeout_reported(monkeypatch):
     res = batch.solve(gammas, normals, ccmf.Params(fixed_iters=3))
     assert all(r["status"] == 0 and r["iters"] == 3 and np.isfinite(r["gamma_eff"]) for r in res)
     batch.close()
+
+
+def test_persistent_narrow_tiles_for_long_axes():
+    """A batch with an axis too long for the wide tiles (beyond about 400 points in FP32, 200 in
+    FP64) runs the narrow-tile instantiation (4 line pairs, 8 lines) for all its groups: FP64
+    against the oracle at equal iterations, FP32 against the graph mode."""
+    f64 = [M.random_two_phase((6, 10, 256), 0.3, 0.25, 1.0, 41), M.uniform_random((8, 8, 8), 0.5, 1.5, 42)]
+    plan = [(0, [0, 0, 1]), (1, [0.36, 0.48, 0.8]), (0, [1, 0, 0])]
+    dev = [torch.from_numpy(f).to(DEV) for f in f64]
+    batch = ccmf.Batch([f64[f].shape for f, _ in plan], precision=ccmf.CCMF_FP64, device=DEV)
+    batch.set_persistent(True)
+    res = batch.solve([dev[f] for f, _ in plan], np.array([n for _, n in plan], dtype=np.float64),
+                      ccmf.Params(fixed_iters=20))
+    for s, (f, n) in enumerate(plan):
+        ref = O.solve(f64[f], n, O.Params(fixed_iters=20), record_history=False)
+        assert res[s]["status"] == 0 and res[s]["iters"] == 20
+        for key, rk in (("gamma_eff", ref.gamma_eff), ("gamma_primal", ref.gamma_primal), ("rho", ref.rho),
+                        ("residual", ref.residual)):
+            assert abs(res[s][key] - rk) <= 1e-10 * abs(rk), (s, key, res[s][key], rk)
+    batch.close()
+    f32 = [M.random_two_phase((8, 8, 512), 0.3, 0.25, 1.0, 43).astype(np.float32),
+           M.boolean_spheres((16, 12, 10), 2.0, 0.2, 0.3, 1.0, 44)[0].astype(np.float32)]
+    gam = [torch.from_numpy(f).to(DEV) for f in f32]
+    normals = np.array([[0, 0, 1], [1, 0, 0]], dtype=np.float64)
+    out = []
+    for persistent in (False, True):
+        b = ccmf.Batch([f.shape for f in f32], precision=ccmf.CCMF_FP32_MIXED, device=DEV)
+        b.set_persistent(persistent)
+        out.append(b.solve(gam, normals, ccmf.Params(fixed_iters=30)))
+        b.close()
+    for a, r in zip(out[1], out[0]):
+        assert a["status"] == 0 and a["iters"] == 30
+        assert abs(a["gamma_eff"] - r["gamma_eff"]) <= 1e-5 * abs(r["gamma_eff"])

@@ -425,8 +425,9 @@ int ccmf_batch_solve(ccmf_batch* batch, const void* const* gammas, const double*
  *
  * The first call on a device looks up the device address of the scratch area
  * (cudaGetSymbolAddress) with that device current, once per device (thread-safe);
- * the address belongs to the device's primary context, so the entry point must not
- * be used on a device after a cudaDeviceReset of it. Kernels are launched directly
+ * make that first call before any stream capture begins. The address belongs to the
+ * device's primary context, so the entry point must not be used on a device after a
+ * cudaDeviceReset of it. Kernels are launched directly
  * on `stream` (no graph). The call copies the unit normal from host memory with
  * cudaMemcpyAsync; with a tolerance (fixed_iters = 0) the host reads a counter from
  * the device every check_every updates, and with a non-NULL result it synchronises

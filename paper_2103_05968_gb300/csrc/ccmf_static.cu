@@ -128,9 +128,10 @@ int lines_for(int n, size_t cs) {
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
 // One-time set-up per device, with that device current: the device address of
-// the scratch array (host code cannot use the array's name as an address). The
-// address belongs to the device's primary context; a cudaDeviceReset ends that
-// context, and ccmf_solve_static must not be called on the device afterwards.
+// the scratch array (host code cannot use the array's name as an address). It runs
+// in the first call on the device, which should come before any stream capture
+// begins. The address belongs to the device's primary context; a cudaDeviceReset
+// ends that context, and ccmf_solve_static must not be called on the device afterwards.
 int static_setup(int dev, unsigned char** base) {
     if (dev < 0 || dev >= kMaxDevices) return CCMF_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(g_scratch_mutex);

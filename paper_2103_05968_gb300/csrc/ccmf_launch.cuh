@@ -446,7 +446,7 @@ void launch_passes(const Ctx<T>& c, const Ptrs<T>& p, cudaStream_t st, F&& betwe
         launch_plane_cluster<T>(g, p, c, inv_n, st);
         between(kKFftPlane);
     } else if (sh.plane_fused) {
-        k_fft_plane<T><<<dim3((unsigned)g.n3h, (unsigned)g.batch), kPlaneThreads, sh.smem_plane, st>>>(
+        k_fft_plane<T><<<dim3((unsigned)g.n3h, (unsigned)g.batch), plane_threads<T>(), sh.smem_plane, st>>>(
             g, p, c.ax[0], c.ax[1], c.tw[0], c.tw[1], c.rsym[0], c.rsym[1], c.sym[2], inv_n);
         between(kKFftPlane);
     } else {

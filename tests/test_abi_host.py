@@ -77,6 +77,9 @@ def test_null_arguments_rejected(lib):
     assert lib.ccmf_plan_destroy(None) == ccmf.CCMF_OK
     assert lib.ccmf_solve(None, None, 0, None, None, None, 0, None, None, None, None) == ccmf.CCMF_ERR_INVALID_ARG
     assert lib.ccmf_set_kernel_timing(None, 1) == ccmf.CCMF_ERR_INVALID_ARG
+    assert lib.ccmf_batch_set_persistent(None, 1) == ccmf.CCMF_ERR_INVALID_ARG
+    assert lib.ccmf_batch_solve(None, None, None, None, None, 0, None, None) == ccmf.CCMF_ERR_INVALID_ARG
+    assert lib.ccmf_batch_destroy(None) == ccmf.CCMF_OK
 
 
 def test_binding_fails_loudly_without_library(tmp_path):
